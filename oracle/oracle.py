@@ -1,0 +1,244 @@
+"""ctypes wrapper of the FP64 C oracle (test infrastructure only).
+
+Arrays are numpy; positions are uint32 fractional coordinates of shape (N, 3) on the
+2^-32 grid (r = s * L / 2^32). Each function cites the equation of arXiv 2609.02694 it
+evaluates; the C source states the definition term by term.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_dp = ct.POINTER(ct.c_double)
+
+
+def lib():
+    """Load (building if needed) the oracle shared library."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_kdim_M.argtypes = [ct.c_double, ct.c_double]
+        L.orc_kdim_M.restype = ct.c_int
+        L.orc_kdim_table.argtypes = [ct.c_double, ct.c_double, ct.c_int, _u64p, _dp]
+        L.orc_sample_k.argtypes = [ct.c_uint64, ct.c_uint64, ct.c_uint32, _f64p, ct.c_double,
+                                   ct.c_int, _i32p, _dp]
+        L.orc_rho.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, ct.c_int, _i32p, _f64p]
+        L.orc_rbe_kspace.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, ct.c_double, ct.c_double,
+                                     ct.c_int, _i32p, ct.c_double, _f64p, _dp, _dp]
+        L.orc_ewald_kspace.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, ct.c_double,
+                                       ct.c_double, _f64p, _dp, _dp]
+        L.orc_self_energy.argtypes = [ct.c_int64, _f64p, ct.c_double, ct.c_double]
+        L.orc_self_energy.restype = ct.c_double
+        L.orc_min_image_r2.argtypes = [_u32p, _u32p, _f64p, _f64p]
+        L.orc_min_image_r2.restype = ct.c_double
+        L.orc_real_space.argtypes = [ct.c_int64, _u32p, _f64p, _i32p, _f64p, ct.c_double,
+                                     ct.c_double, ct.c_double, ct.c_int, _f64p, _f64p,
+                                     ct.c_void_p, ct.c_int64, _f64p, _dp, _dp, _dp, _dp,
+                                     ct.c_void_p]
+        L.orc_cells.argtypes = [ct.c_int64, _u32p, _i32p, _i32p, _i64p, _i64p]
+        L.orc_rbl.argtypes = [ct.c_int64, _u32p, _f64p, _i32p, _f64p, ct.c_double, ct.c_double,
+                              ct.c_double, ct.c_int, ct.c_uint64, ct.c_uint64, ct.c_uint32,
+                              ct.c_double, ct.c_int, _f64p, _f64p, _f64p, _dp, _dp, _dp, _dp,
+                              ct.c_void_p, ct.c_void_p, ct.c_void_p]
+        L.orc_brute_coulomb.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, ct.c_double, ct.c_int,
+                                        _f64p, _dp]
+        L.orc_vv_drift.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, _f64p, _f64p, ct.c_double,
+                                   ct.c_double]
+        L.orc_vv_kick.argtypes = [ct.c_int64, _f64p, _f64p, _f64p, ct.c_double, ct.c_double]
+        L.orc_num_threads.restype = ct.c_int
+        for name in ("orc_kdim_table", "orc_sample_k", "orc_rho", "orc_rbe_kspace",
+                     "orc_ewald_kspace", "orc_real_space", "orc_cells", "orc_rbl",
+                     "orc_brute_coulomb", "orc_vv_drift", "orc_vv_kick"):
+            getattr(L, name).restype = ct.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def _s(s):
+    return np.ascontiguousarray(s, dtype=np.uint32).reshape(-1, 3)
+
+
+def _f(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def num_threads():
+    return lib().orc_num_threads()
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block (Salmon et al., SC'11)."""
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def kdim_M(L, alpha):
+    return lib().orc_kdim_M(float(L), float(alpha))
+
+
+def kdim_table(L, alpha, M=None):
+    """Per-axis cumulative thresholds and normaliser of exp(-k^2/4 alpha) (Eq. F_long_RBE)."""
+    M = kdim_M(L, alpha) if M is None else M
+    T = np.zeros(2 * M + 1, np.uint64)
+    Z = ct.c_double()
+    _check(lib().orc_kdim_table(float(L), float(alpha), int(M), T, ct.byref(Z)), "kdim_table")
+    return T, Z.value
+
+
+def sample_k(seed, step, replica, box, alpha, P):
+    """P importance-sampled modes m (P, 3) and the normaliser S (Eq. F_long_RBE)."""
+    m = np.zeros((P, 3), np.int32)
+    S = ct.c_double()
+    _check(lib().orc_sample_k(int(seed), int(step), int(replica), _f(box), float(alpha),
+                              int(P), m, ct.byref(S)), "sample_k")
+    return m, S.value
+
+
+def rho(s, q, box, m):
+    """Structure factor rho(k) = sum_j q_j exp(i k.r_j) as complex128 (Eq. U_Coul_Fourier)."""
+    s = _s(s)
+    m = np.ascontiguousarray(m, np.int32).reshape(-1, 3)
+    out = np.zeros(2 * len(m), np.float64)
+    _check(lib().orc_rho(len(s), s, _f(q), _f(box), len(m), m, out), "rho")
+    return out[0::2] + 1j * out[1::2]
+
+
+def rbe_kspace(s, q, box, alpha, C, m, S):
+    """RBE k-space force (N, 3), energy and virial on a fixed mode set (Eq. F_long_RBE)."""
+    s = _s(s)
+    m = np.ascontiguousarray(m, np.int32).reshape(-1, 3)
+    F = np.zeros((len(s), 3), np.float64)
+    U, W = ct.c_double(), ct.c_double()
+    _check(lib().orc_rbe_kspace(len(s), s, _f(q), _f(box), float(alpha), float(C), len(m), m,
+                                float(S), F, ct.byref(U), ct.byref(W)), "rbe_kspace")
+    return F, U.value, W.value
+
+
+def ewald_kspace(s, q, box, alpha, C):
+    """Full Ewald k-space force, energy and virial (Eqs. U_Coul_Fourier, F_i)."""
+    s = _s(s)
+    F = np.zeros((len(s), 3), np.float64)
+    U, W = ct.c_double(), ct.c_double()
+    _check(lib().orc_ewald_kspace(len(s), s, _f(q), _f(box), float(alpha), float(C), F,
+                                  ct.byref(U), ct.byref(W)), "ewald_kspace")
+    return F, U.value, W.value
+
+
+def self_energy(q, alpha, C):
+    q = _f(q)
+    return lib().orc_self_energy(len(q), q, float(alpha), float(C))
+
+
+def min_image_r2(si, sj, box):
+    d = np.zeros(3, np.float64)
+    r2 = lib().orc_min_image_r2(np.asarray(si, np.uint32), np.asarray(sj, np.uint32), _f(box), d)
+    return r2, d
+
+
+def lj_tables(eps, sig, ntypes=None):
+    eps = np.atleast_1d(np.asarray(eps, np.float64))
+    sig = np.atleast_1d(np.asarray(sig, np.float64))
+    if ntypes is None:
+        ntypes = int(round(np.sqrt(eps.size)))
+    return _f(eps.reshape(-1)), _f(sig.reshape(-1)), ntypes
+
+
+def real_space(s, q, types, box, alpha, rc, C, eps, sig, i_list=None):
+    """Real-space erfc Coulomb + LJ forces and energies (Eqs. F_i, G_short, LJ)."""
+    s = _s(s)
+    N = len(s)
+    eps, sig, nt = lj_tables(eps, sig)
+    F = np.zeros((N, 3), np.float64)
+    nbr = np.zeros(N, np.int32)
+    vals = [ct.c_double() for _ in range(4)]
+    if i_list is not None:
+        il = np.ascontiguousarray(i_list, np.int64)
+        ilp, nl = il.ctypes.data, len(il)
+    else:
+        il, ilp, nl = None, None, 0
+    _check(lib().orc_real_space(N, s, _f(q), np.ascontiguousarray(types, np.int32), _f(box),
+                                float(alpha), float(rc), float(C), nt, eps, sig, ilp, nl, F,
+                                *[ct.byref(v) for v in vals], nbr.ctypes.data), "real_space")
+    return dict(F=F, U_real=vals[0].value, U_lj=vals[1].value, W_real=vals[2].value,
+                W_lj=vals[3].value, nbr=nbr)
+
+
+def cells(s, n):
+    """Linked cells: cell of each particle, cell_start (ncell+1), ids in (cell, id) order."""
+    s = _s(s)
+    n = np.ascontiguousarray(n, np.int32)
+    ncell = int(np.prod(n.astype(np.int64)))
+    cell_of = np.zeros(len(s), np.int32)
+    cell_start = np.zeros(ncell + 1, np.int64)
+    sorted_ids = np.zeros(len(s), np.int64)
+    _check(lib().orc_cells(len(s), s, n, cell_of, cell_start, sorted_ids), "cells")
+    return cell_of, cell_start, sorted_ids
+
+
+def rbl(s, q, types, box, alpha, r_core, r_s, p, seed, step, replica, C, eps, sig):
+    """Random batch list short-range force with the mean-force correction (Eqs. RBL, F_corr)."""
+    s = _s(s)
+    N = len(s)
+    eps, sig, nt = lj_tables(eps, sig)
+    F = np.zeros((N, 3), np.float64)
+    nc = np.zeros(N, np.int32)
+    ns = np.zeros(N, np.int32)
+    partners = np.zeros((N, p), np.int32)
+    vals = [ct.c_double() for _ in range(4)]
+    _check(lib().orc_rbl(N, s, _f(q), np.ascontiguousarray(types, np.int32), _f(box),
+                         float(alpha), float(r_core), float(r_s), int(p), int(seed), int(step),
+                         int(replica), float(C), nt, eps, sig, F,
+                         *[ct.byref(v) for v in vals], nc.ctypes.data, ns.ctypes.data,
+                         partners.ctypes.data), "rbl")
+    return dict(F=F, U_real=vals[0].value, U_lj=vals[1].value, W_real=vals[2].value,
+                W_lj=vals[3].value, n_core=nc, n_shell=ns, partners=partners)
+
+
+def brute_coulomb(s, q, box, C, R):
+    """Image-cell sum of Eq. Coul_potential for |n| <= R, in tin-foil convention."""
+    s = _s(s)
+    F = np.zeros((len(s), 3), np.float64)
+    U = ct.c_double()
+    _check(lib().orc_brute_coulomb(len(s), s, _f(q), _f(box), float(C), int(R), F,
+                                   ct.byref(U)), "brute_coulomb")
+    return F, U.value
+
+
+def vv_drift(s, v, F, mass, box, dt, kappa):
+    """First half of velocity Verlet on the fixed-point grid; updates s and v in place."""
+    _check(lib().orc_vv_drift(len(s), s, v, _f(F), _f(mass), _f(box), float(dt),
+                              float(kappa)), "vv_drift")
+
+
+def vv_kick(v, F, mass, dt, kappa):
+    _check(lib().orc_vv_kick(len(v), v, _f(F), _f(mass), float(dt), float(kappa)), "vv_kick")
+
+
+def total_forces(s, q, types, box, alpha, rc, C, eps, sig, m, S):
+    """Total nonbonded force and energies with RBE on the given mode set (Sec. 2.1)."""
+    rs = real_space(s, q, types, box, alpha, rc, C, eps, sig)
+    Fk, Uk, Wk = rbe_kspace(s, q, box, alpha, C, m, S)
+    Us = self_energy(q, alpha, C)
+    return dict(F=rs["F"] + Fk, U_real=rs["U_real"], U_lj=rs["U_lj"], U_k=Uk, U_self=Us,
+                U_total=rs["U_real"] + rs["U_lj"] + Uk - Us, W_real=rs["W_real"],
+                W_lj=rs["W_lj"], W_k=Wk, nbr=rs["nbr"])
+
+
+__all__ = [n for n in dir() if not n.startswith("_") and n not in ("ct", "os", "np")]
