@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of the RBE force path on GB300: particle-steps/s of full velocity-Verlet steps.
+
+Workload (one GPU, inputs resident in HBM): 1,048,576 particles at number density
+0.1 / A^3 (L = 218.88 A), 10% charged (+/-1 e), single LJ type (eps 0.1 kcal/mol,
+sigma 3 A), alpha = 0.09 / A^2 (sqrt(alpha) = 0.3 / A), r_c = 10 A, P = 200 modes,
+FP32-compensated form, NVE velocity Verlet, dt = 1 fs. Each step runs every stage of
+the path: kick + drift, cell binning and sort, Philox mode sampling, structure factor,
+real-space pair forces, k-space gather, kick and energy totals.
+
+Output: one JSON line (rank 0). --impl reference times the FP64 CPU oracle instead.
+Under torchrun each rank advances its own replica of the same workload (weak scaling,
+no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RBE force particle-steps/s on 1 GB300, FP32-comp vs FP64 form at stated force error"
+UNIT = "particle-steps/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+PAIR_FLOPS = 20.0  # FP32 flops per unique pair (LJ), the per-unit figure of the roofline
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=1 << 20)
+    ap.add_argument("--P", type=int, default=200)
+    ap.add_argument("--precision", default="fp32_comp")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 form, e2e, error and CPU legs (profiling runs)")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2609_02694_gb300 import synth
+    sy = synth.make_system(args.N, density=0.1, frac_charged=0.1, seed=2)
+    desc = (f"N={args.N} charged LJ, 10% +/-1e, density 0.1/A^3, L={sy.box[0]:.3f} A, "
+            f"alpha=0.09/A^2, r_c=10 A, P={args.P}, NVE velocity Verlet dt=1 fs")
+    return sy, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd[1:1] = ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_steps(h, stream, flush_buf, K, profile_phase=None):
+    """Sum of per-step device times (CUDA events on the library's stream), L2 flushed
+    between steps; returns (total_ms, summed phase ms)."""
+    import torch
+    total = 0.0
+    phases = None
+    for _ in range(K):
+        flush_buf.zero_()  # 256 MiB write evicts the 129 MB L2
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        h.step(1)
+        end.record(stream)
+        end.synchronize()
+        total += start.elapsed_time(end)
+        if profile_phase:
+            ph, _ = h.profile()
+            phases = ph if phases is None else {k: phases[k] + ph[k] for k in ph}
+    return total, phases
+
+
+def sampled_error(orc, sy, F, m, S, n=32, seed=0):
+    """Force rel-L2 on n sampled particles against the oracle on the same modes."""
+    from paper_2609_02694_gb300 import synth
+    rng = np.random.default_rng(seed)
+    charged = np.flatnonzero(sy.q != 0)
+    idx = np.unique(np.concatenate([rng.choice(sy.n, n, replace=False), charged[: n // 2]]))
+    rs = orc.real_space(sy.s, sy.q, sy.types, sy.box, synth.ALPHA, synth.R_CUT,
+                        synth.COULOMB_C, sy.eps, sy.sig, i_list=idx)
+    rho = orc.rho(sy.s, sy.q, sy.box, m)
+    k = 2 * np.pi * m / sy.box
+    k2 = (k * k).sum(1)
+    th = sy.positions()[idx] @ k.T
+    im = rho.imag[None, :] * np.cos(th) - rho.real[None, :] * np.sin(th)
+    c = (S / len(m)) * 4 * np.pi * synth.COULOMB_C / (np.prod(sy.box) * k2)
+    Fk = -(sy.q[idx][:, None, None] * (c * im)[:, :, None] * k[None, :, :]).sum(1)
+    Fo = rs["F"][idx] + Fk
+    return float(np.linalg.norm(F[idx] - Fo) / np.linalg.norm(Fo)), len(idx)
+
+
+def cpu_oracle_step(orc, sy, P, n_sample, seed=0):
+    """One oracle force evaluation of the workload, sampled: the structure factor and
+    the k-space forces in full, the O(N) real-space sums for n_sample particles; returns
+    (extrapolated seconds per full step, seconds spent)."""
+    from paper_2609_02694_gb300 import synth
+    m, S = orc.sample_k(1, 0, 0, sy.box, synth.ALPHA, P)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(sy.n, n_sample, replace=False))
+    t0 = time.perf_counter()
+    orc.rbe_kspace(sy.s, sy.q, sy.box, synth.ALPHA, synth.COULOMB_C, m, S)
+    t1 = time.perf_counter()
+    orc.real_space(sy.s, sy.q, sy.types, sy.box, synth.ALPHA, synth.R_CUT, synth.COULOMB_C,
+                   sy.eps, sy.sig, i_list=idx)
+    t2 = time.perf_counter()
+    return (t1 - t0) + (t2 - t1) * sy.n / n_sample, t2 - t0
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    sy, desc = workload(args)
+    orc = oracle
+    orc.lib()
+    n_sample = 256
+    for _ in range(args.warmup):
+        cpu_oracle_step(orc, sy, args.P, 64)
+    tot = spent = 0.0
+    for k in range(args.steps):
+        t, s = cpu_oracle_step(orc, sy, args.P, n_sample, seed=k)
+        tot += t
+        spent += s
+    value = sy.n * args.steps / tot
+    sample = (f"per step: full structure factor and k-space forces, O(N) real-space sums of "
+              f"{n_sample} sampled particles, extrapolated to all {sy.n}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc + ", FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "measured_seconds": spent}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2609_02694_gb300 import binding, build, synth
+    build.build()
+    binding.lib()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    sy, desc = workload(args)
+    mk = dict(P=args.P, alpha=synth.ALPHA, r_c=synth.R_CUT, coulomb_C=synth.COULOMB_C,
+              dt=1.0, kappa=synth.ACCEL_KAPPA, replica=rank, stream=stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    h = binding.from_system(sy, precision=args.precision, **mk)
+    h.set_profiling(True)
+    # exact unique-pair count of step 0 (the roofline's units) and the force sample
+    F0, E0, _ = h.forces_f64(0)
+    nbr, _ = h.neighbor_counts()
+    pairs = float(nbr.astype(np.int64).sum()) / 2.0
+    m0, S0 = h.sample_k(0)
+    for _ in range(args.warmup):
+        h.step(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:  # noqa: BLE001
+        pass
+    with ClockSampler(uuid) as clk:
+        total_ms, phases = time_steps(h, stream, flush, args.steps, profile_phase=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    kps = h.kernels_per_step()
+    E1, _ = h.energies()
+    value = sy.n * args.steps * ws / (total_ms / 1e3)
+    pair_ms = phases["pair"] / args.steps
+    achieved = pairs * PAIR_FLOPS / (pair_ms / 1e3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": desc + f", {args.precision} form",
+                       "l2": "flushed between timed steps (256 MiB write); per-step CUDA events",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "gpu_launches": kps * args.steps,
+            "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+            "roofline": {"bound": "alu", "kernel": "pair_kernel (cell-list LJ)",
+                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "units": f"{pairs:.0f} unique pairs x {PAIR_FLOPS:.0f} flops",
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"},
+            "clocks": clk.summary(),
+            "energy": {"total_step0": E0["total"], "total_after": E1["total"],
+                       "kinetic_after": E1["kinetic"]}}
+    if rank == 0 and not args.no_extras:
+        import oracle
+        orc = oracle
+        orc.lib()
+        err32, ns = sampled_error(orc, sy, F0, m0, S0)
+        line["force_error"] = {"rel_l2_vs_oracle_same_modes": err32,
+                               "sample": f"{ns} particles (step 0)"}
+        # FP64 form on the same workload
+        h64 = binding.from_system(sy, precision="fp64", **mk)
+        h64.set_profiling(True)
+        F64, _, _ = h64.forces_f64(0)
+        for _ in range(2):
+            h64.step(1)
+        ms64, ph64 = time_steps(h64, stream, flush, args.fp64_steps, profile_phase=True)
+        err64, _ = sampled_error(orc, sy, F64, m0, S0)
+        line["fp64_form"] = {"value": sy.n * args.fp64_steps / (ms64 / 1e3), "unit": UNIT,
+                             "ms_per_step": ms64 / args.fp64_steps,
+                             "rel_l2_vs_oracle_same_modes": err64,
+                             "phases_ms_per_step": {k: v / args.fp64_steps for k, v in ph64.items()}}
+        h64.close()
+        # end to end through the C ABI with pinned host buffers
+        pos_h = torch.from_numpy(sy.positions()).pin_memory()
+        F_h = torch.empty((sy.n, 3), dtype=torch.float32).pin_memory()
+        h.set_profiling(False)
+        for k in range(2):
+            h.set_positions(pos_h)
+            h.forces(k, out=F_h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            h.set_positions(pos_h)
+            h.forces(k, out=F_h)
+        t1 = time.perf_counter()
+        line["e2e"] = {"value": sy.n * args.steps / (t1 - t0), "unit": UNIT,
+                       "h2d_bytes_per_step": sy.n * 3 * 8,
+                       "d2h_bytes_per_step": sy.n * 3 * 4 + 8 * (6 + 4) + 4,
+                       "call": "rbe_set_positions(host f64) + rbe_forces(host f32 F, energies)"}
+        # CPU baseline: the oracle on a bounded sample of the same workload
+        t_ext, spent = cpu_oracle_step(orc, sy, args.P, 512)
+        line["cpu_baseline"] = {"value": sy.n / t_ext, "unit": UNIT, "cores": orc.num_threads(),
+                                "kind": "oracle",
+                                "sample": "one step 0 force evaluation: full structure factor and "
+                                          "k-space forces, O(N) real-space sums of 512 sampled "
+                                          f"particles extrapolated to {sy.n} "
+                                          f"({spent:.1f} s measured)"}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * rbe.h -- C ABI of the GB300-native improved random batch Ewald (RBE) force path.
+ *
+ * The library evaluates the nonbonded force of RBMD 2.0 (arXiv 2609.02694, Sec. 2.1) for
+ * point charges with Lennard-Jones interactions in an orthorhombic periodic box:
+ *   F_i = F_i^N + F_i^F                                   (Eq. F_i)
+ * where F^N is the erfc-screened Coulomb + LJ pair force inside the cutoff (Eqs. F_i,
+ * G_short, LJ), evaluated over linked cells or by the random batch list (Eqs. Ci_Si, RBL,
+ * F_corr), and F^F is the importance-sampled k-space estimator (Eq. F_long_RBE) on P modes
+ * drawn from P(k) ~ exp(-k^2 / 4 alpha), k != 0.
+ *
+ * Conventions
+ *  - Units are the caller's. The Coulomb constant, the force-to-acceleration factor and
+ *    the time step are parameters. Real units (Angstrom, fs, amu, kcal/mol, e) use
+ *    coulomb_C = 332.06371 and kappa = 4.184e-4.
+ *  - alpha is the paper's Ewald parameter, in length^-2 (Eq. Ewald: erfc(sqrt(alpha) r)).
+ *  - Positions are stored on the 2^-32 fractional grid: s_d = round(r_d / L_d * 2^32) mod
+ *    2^32. Positions that are already on that grid are kept exactly.
+ *  - Arrays of N x 3 values are row-major per particle (x, y, z) and indexed by the
+ *    caller's particle id 0..N-1. The library reorders particles internally by cell and
+ *    translates back on every output.
+ *  - Every call returns RBE_OK (0) or a negative RBE_ERR_* code. rbe_error_string() gives
+ *    a message. A failed call leaves the handle usable unless it returns RBE_ERR_CUDA.
+ *  - Calls are asynchronous on the stream given to rbe_init, except those that return
+ *    host data. Those synchronise that stream before they return.
+ *  - The library owns every device buffer it allocates and frees them in rbe_destroy.
+ *    Caller buffers are never retained after a call returns.
+ */
+#ifndef RBE_H
+#define RBE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbe_ctx *rbe_handle;
+
+enum {
+  RBE_OK = 0,
+  RBE_ERR_INVALID = -1,     /* a NULL handle or pointer, or a value out of range */
+  RBE_ERR_NONNEUTRAL = -2,  /* |sum q| > 1e-9 * max(1, sum |q|) (charge neutrality, Sec. 2.1) */
+  RBE_ERR_CUTOFF = -3,      /* r_c >= L/2 on some axis (minimum image not unique) */
+  RBE_ERR_CELLS = -4,       /* fewer cells per axis than the stencil needs */
+  RBE_ERR_OOM = -5,         /* device allocation failed */
+  RBE_ERR_CUDA = -6,        /* a CUDA runtime error; the handle should be destroyed */
+  RBE_ERR_SAMPLER = -7,     /* 64 redraws of a mode all gave k = 0 (device flag) */
+  RBE_ERR_NONFINITE = -8,   /* a non-finite velocity or position update (device flag) */
+  RBE_ERR_STATE = -9        /* call not valid in this state (e.g. no forces computed yet) */
+};
+
+enum {
+  RBE_FP32_COMP = 0, /* FP32 pair and phase math; compensated FP32 partials, FP64 combine */
+  RBE_FP32 = 1,      /* plain FP32 everywhere, partials combined in FP32 */
+  RBE_FP64 = 2       /* FP64 pair, phase and trig math, FP64 accumulation */
+};
+
+/* Energies written by rbe_forces (all in the caller's energy unit). */
+enum {
+  RBE_E_REAL = 0,  /* U^N Coulomb: 1/2 sum C q_i q_j erfc(sqrt(alpha) r)/r over r <= r_c */
+  RBE_E_LJ = 1,    /* U_LJ of Eq. LJ, plainly truncated at r_c */
+  RBE_E_KSPACE = 2,/* RBE estimator of Eq. U_Coul_Fourier: (S/P) sum_l 2 pi C |rho_l|^2/(V k_l^2) */
+  RBE_E_SELF = 3,  /* Eq. U_self: C sqrt(alpha/pi) sum q^2 */
+  RBE_E_TOTAL = 4, /* REAL + LJ + KSPACE - SELF */
+  RBE_E_KINETIC = 5,/* 1/2 sum m v^2 / kappa at the current velocities */
+  RBE_N_ENERGY = 6
+};
+
+/* Scalar virials W = sum r . F (W_k from the homogeneity of U^F: sum_l E_l (1 - k_l^2/2 alpha)). */
+enum { RBE_W_REAL = 0, RBE_W_LJ = 1, RBE_W_KSPACE = 2, RBE_W_TOTAL = 3, RBE_N_VIRIAL = 4 };
+
+typedef struct {
+  double alpha;        /* Ewald splitting parameter, length^-2 (Eq. Ewald) */
+  double r_c;          /* real-space cutoff: the paper's r_s in Eq. Ci_Si (and r_c of Eq. F_i) */
+  double r_core;       /* RBL core radius, the paper's r_c of Eq. Ci_Si; 0 selects the plain
+                          cell-list real space */
+  int32_t p_rbl;       /* RBL shell batch size p (Eq. RBL); used when r_core > 0 */
+  int32_t P;           /* number of sampled Fourier modes (Eq. F_long_RBE), >= 1 */
+  uint64_t seed;       /* Philox key for the mode and RBL draws */
+  uint32_t replica;    /* xored into the upper key word: independent streams per replica */
+  int32_t precision;   /* RBE_FP32_COMP, RBE_FP32 or RBE_FP64 */
+  double coulomb_C;    /* Coulomb constant C (energy x length / charge^2) */
+  double dt;           /* time step of rbe_step */
+  double kappa;        /* force / mass -> acceleration factor of rbe_step */
+  int32_t n_types;     /* number of LJ types, 1..16 */
+  const double *lj_eps;   /* n_types x n_types, symmetric (Eq. LJ epsilon_ij) */
+  const double *lj_sigma; /* n_types x n_types, symmetric (Eq. LJ sigma_ij) */
+  int32_t cell_sub;    /* real-space cells per cutoff length (1, 2 or 3); 0 = library default */
+} rbe_params;
+
+/* Create a handle for N particles in box[3] (orthorhombic side lengths).
+ *  pos   N x 3 positions (host), wrapped into the box and quantised to the 2^-32 grid
+ *  q     N charges (host); the system must be neutral
+ *  type  N LJ type indices in [0, n_types) (host), or NULL for all type 0
+ *  mass  N masses (host), or NULL when rbe_step is not used (mass 1)
+ *  vel   N x 3 velocities (host), or NULL for zero
+ *  cuda_stream  a cudaStream_t the library launches on (NULL = legacy default stream)
+ * Allocates all device memory for the system; no allocation happens after this call. */
+int rbe_init(rbe_handle *h, const rbe_params *p, int64_t N, const double box[3],
+             const double *pos, const double *q, const int32_t *type, const double *mass,
+             const double *vel, void *cuda_stream);
+
+/* Draw the P modes of step `step` (Eq. F_long_RBE; the sampling density of Sec. 2.1) on the
+ * device and, if m_out (host, P x 3 int32) is non-NULL, copy them back; *S_out (nullable)
+ * receives the normaliser S = sum_{k != 0} exp(-k^2 / 4 alpha). Mode l is a pure function
+ * of (seed, replica, step, l) (Philox4x32-10 counter (l, attempt, step, 0)), which plays
+ * the role of the paper's broadcast seed (Sec. 2.3.1). */
+int rbe_sample_k(rbe_handle h, uint64_t step, int32_t *m_out, double *S_out);
+
+/* Replace the positions (N x 3, in id order) from host (on_device = 0) or device memory. */
+int rbe_set_positions(rbe_handle h, const double *pos, int on_device);
+
+/* One nonbonded force evaluation for step `step`:
+ * bin + sort -> sample P modes -> structure factor -> k-space gather -> real space
+ * (cell list, or RBL with the mean-force correction when r_core > 0) -> totals.
+ *  F_out     N x 3 float forces in id order (nullable), in host (F_on_device = 0) or
+ *            device memory
+ *  energies  RBE_N_ENERGY doubles (nullable, host)
+ *  virial    RBE_N_VIRIAL doubles (nullable, host)
+ * The call synchronises when any host output is requested. */
+int rbe_forces(rbe_handle h, uint64_t step, float *F_out, int F_on_device, double *energies,
+               double *virial);
+
+/* Same as rbe_forces, with FP64 forces written to host memory (for parity checks). */
+int rbe_forces_f64(rbe_handle h, uint64_t step, double *F_out, double *energies,
+                   double *virial);
+
+/* Advance nsteps velocity-Verlet steps (kick-drift, forces, kick) from the current step
+ * counter, replaying one captured CUDA graph per step; asynchronous. The first call
+ * computes the initial forces if none exist and captures the graph. */
+int rbe_step(rbe_handle h, int nsteps);
+
+/* Energies and virials of the last force evaluation or Verlet step (host, nullable each;
+ * RBE_N_ENERGY and RBE_N_VIRIAL doubles). Synchronises the stream. */
+int rbe_get_energies(rbe_handle h, double *energies, double *virial);
+
+/* Current step counter (number of completed rbe_step steps). */
+int rbe_get_step(rbe_handle h, uint64_t *step);
+
+/* Copy the state back in id order (each nullable): positions (exact dequantisation of the
+ * 2^-32 grid, wrapped into [0, L)), velocities, and the raw fractional coordinates. */
+int rbe_get_state(rbe_handle h, double *pos, double *vel, uint32_t *s_frac);
+
+/* Copy the linked cells of the last force evaluation: n_cells[3] cells per axis,
+ * cell_start (n_x n_y n_z + 1 entries) and sorted_ids (N ids in (cell, id) order). Either
+ * array may be NULL (query n_cells first to size cell_start). */
+int rbe_get_cells(rbe_handle h, int32_t n_cells[3], int64_t *cell_start, int64_t *sorted_ids);
+
+/* Copy the structure factor of the last evaluation, rho (P x 2: Re, Im, FP64), and the modes. */
+int rbe_get_rho(rbe_handle h, double *rho, int32_t *m_out);
+
+/* Per-particle neighbour counts of the last evaluation (id order, nullable):
+ * plain cell list: n_core = #{j != i: r_ij <= r_c}, n_shell = 0;
+ * RBL: n_core = #C_i, n_shell = #S_i (Eq. Ci_Si). Cutoff decisions are exact: the FP64
+ * comparison of dx^2 + dy^2 + dz^2 with r^2, dx_d = (int32)(s_i - s_j) * (L_d / 2^32). */
+int rbe_get_neighbor_counts(rbe_handle h, int32_t *n_core, int32_t *n_shell);
+
+/* RBL draws of the last evaluation (N x p_rbl ids in id order; -1 where unused). */
+int rbe_get_rbl_partners(rbe_handle h, int32_t *partners);
+
+/* Phases timed by the profiler (CUDA events recorded on the library's stream). */
+enum {
+  RBE_PH_KICK_DRIFT = 0, /* first half-kick + drift (rbe_step only) */
+  RBE_PH_BIN = 1,        /* linked-cell binning and reordering */
+  RBE_PH_SAMPLE = 2,     /* Philox mode sampler */
+  RBE_PH_SF = 3,         /* structure factor + FP64 combine */
+  RBE_PH_PAIR = 4,       /* main real-space kernel (cell list LJ[+Coulomb], or RBL) */
+  RBE_PH_PAIR2 = 5,      /* charged-subset Coulomb pass, or the RBL mean-force correction */
+  RBE_PH_GATHER = 6,     /* k-space force gather */
+  RBE_PH_TAIL = 7,       /* second half-kick, kinetic energy and totals */
+  RBE_N_PHASE = 8
+};
+
+/* Turn per-phase event timing on or off (off by default). Toggling it discards the
+ * captured step graph, which is captured again on the next rbe_step. */
+int rbe_set_profiling(rbe_handle h, int enable);
+
+/* Per-phase device times (ms, RBE_N_PHASE doubles) of the most recent force evaluation
+ * or Verlet step, and the number of kernels one Verlet step launches. Synchronises. */
+int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kernels_per_step);
+
+/* Bytes of device memory held by the handle. */
+int rbe_get_memory(rbe_handle h, int64_t *bytes);
+
+/* Read and clear the device error flags (RBE_ERR_SAMPLER / RBE_ERR_NONFINITE bits). */
+int rbe_check_device(rbe_handle h);
+
+/* Free every device buffer and the handle. NULL is accepted. */
+int rbe_destroy(rbe_handle h);
+
+/* Static description of an error code. */
+const char *rbe_error_string(int code);
+
+/* Library version string. */
+const char *rbe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,248 @@
+// k_bin.cu -- linked-cell binning and cell-wise reordering (Sec. 2.2: "linked-cell
+// reassignment and cell-wise reordering").
+//
+// Cell of a particle: c_d = floor(s_d n_d / 2^32) (exact on the fixed-point grid),
+// c = c_x + n_x (c_y + n_y c_z). Particles are reordered by (cell, id), which is unique, so
+// the order (and every sum taken in it) is independent of the previous order and of
+// atomic timing. The charged subset is reordered the same way into its own arrays.
+// Pipeline: count (atomics give a provisional slot) -> exclusive scan of the counts ->
+// provisional scatter -> per-cell rank by id + permute of every field (one warp per cell).
+// Integer work, HBM-bound.
+#include <climits>
+
+#include "rbe_internal.cuh"
+
+namespace rbe {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+__global__ void bin_count_kernel(int64_t N, const uint32_t *__restrict__ s,
+                                 const float *__restrict__ q, int n0, int n1, int n2,
+                                 int32_t *__restrict__ count, int32_t *__restrict__ ccount,
+                                 int32_t *__restrict__ key, int32_t *__restrict__ off) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int cx = cell_of(s[i], n0), cy = cell_of(s[N + i], n1), cz = cell_of(s[2 * N + i], n2);
+  const int c = cx + n0 * (cy + n1 * cz);
+  key[i] = c;
+  off[i] = atomicAdd(&count[c], 1);
+  if (q[i] != 0.0f) atomicAdd(&ccount[c], 1);
+}
+
+// Exclusive scan, three passes. Arrays hold two independent sequences (blockIdx.y).
+__global__ void __launch_bounds__(kScanThreads)
+    scan_block_kernel(const int32_t *__restrict__ cnt, int32_t *__restrict__ start,
+                      int32_t *__restrict__ blk, int64_t ncell, int64_t nblk) {
+  __shared__ int32_t warp_tot[kScanThreads / 32];
+  const int which = blockIdx.y;
+  const int32_t *in = cnt + which * ncell;
+  int32_t *out = start + which * (ncell + 1);
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+  int32_t v[kScanItems];
+  int32_t tsum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t idx = base + k;
+    v[k] = idx < ncell ? in[idx] : 0;
+    tsum += v[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t incl = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+    int32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;  // exclusive
+  }
+  __syncthreads();
+  int32_t run = warp_tot[wid] + incl - tsum;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t idx = base + k;
+    if (idx < ncell) out[idx] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) blk[which * nblk + blockIdx.x] = run;  // block total
+}
+
+__global__ void __launch_bounds__(1024)
+    scan_top_kernel(int32_t *__restrict__ blk, int64_t nblk, int32_t *__restrict__ start,
+                    int64_t ncell) {
+  __shared__ int32_t warp_tot[32];
+  __shared__ int32_t carry_s;
+  const int which = blockIdx.x;
+  int32_t *b = blk + which * nblk;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nblk; base += 1024) {
+    const int64_t idx = base + threadIdx.x;
+    const int32_t v = idx < nblk ? b[idx] : 0;
+    int32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const int32_t w = warp_tot[lane];
+      int32_t wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    const int32_t carry = carry_s;
+    const int32_t excl = carry + warp_tot[wid] + incl - v;
+    if (idx < nblk) b[idx] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry_s = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) start[which * (ncell + 1) + ncell] = carry_s;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_add_kernel(int32_t *__restrict__ start, const int32_t *__restrict__ blk,
+                    int64_t ncell, int64_t nblk) {
+  const int which = blockIdx.y;
+  int32_t *out = start + which * (ncell + 1);
+  const int32_t add = blk[which * nblk + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  for (int k = threadIdx.x; k < kScanBlock; k += kScanThreads) {
+    const int64_t idx = base + k;
+    if (idx < ncell) out[idx] += add;
+  }
+}
+
+__global__ void bin_scatter_kernel(int64_t N, const int32_t *__restrict__ key,
+                                   const int32_t *__restrict__ off,
+                                   const int32_t *__restrict__ start, int32_t *__restrict__ tmp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  tmp[start[key[i]] + off[i]] = (int32_t)i;
+}
+
+struct PermuteArgs {
+  int64_t N, Nq, ncell;
+  const int32_t *cell_start, *ccell_start, *tmp;
+  const uint32_t *s0; uint32_t *s1;
+  const float *vf0; float *vf1;
+  const double *vd0; double *vd1;
+  const int32_t *id0; int32_t *id1;
+  const float *qf0; float *qf1;
+  const double *qd0; double *qd1;
+  const int32_t *ty0; int32_t *ty1;
+  const float *im0; float *im1;
+  uint32_t *cs; float *cqf; double *cqd; int32_t *cmap;
+};
+
+// One warp per cell: rank members by id (and charged members among themselves), then move
+// every field of the particle to its final slot.
+__global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= a.ncell) return;
+  const int32_t beg = a.cell_start[c];
+  const int32_t cnt = a.cell_start[c + 1] - beg;
+  const int32_t cbeg = a.ccell_start[c];
+  const int64_t N = a.N, Nq = a.Nq;
+  for (int kb = 0; kb < cnt; kb += 32) {
+    const int k = kb + lane;
+    const bool valid = k < cnt;
+    const int32_t o = valid ? a.tmp[beg + k] : 0;
+    const int32_t myid = valid ? a.id0[o] : INT_MAX;
+    const bool mych = valid && a.qf0[o] != 0.0f;
+    int rank = 0, crank = 0;
+    for (int mb = 0; mb < cnt; mb += 32) {
+      const int mm = mb + lane;
+      const int32_t ov = mm < cnt ? a.tmp[beg + mm] : 0;
+      const int32_t oid = mm < cnt ? a.id0[ov] : INT_MAX;
+      const int och = (mm < cnt && a.qf0[ov] != 0.0f) ? 1 : 0;
+      const int lim = min(32, cnt - mb);
+      for (int t = 0; t < lim; ++t) {
+        const int32_t x = __shfl_sync(0xffffffffu, oid, t);
+        const int xc = __shfl_sync(0xffffffffu, och, t);
+        if (x < myid) { ++rank; crank += xc; }
+      }
+    }
+    if (valid) {
+      const int64_t p = beg + rank;
+      const uint32_t sx = a.s0[o], sy = a.s0[N + o], sz = a.s0[2 * N + o];
+      a.s1[p] = sx; a.s1[N + p] = sy; a.s1[2 * N + p] = sz;
+      if (a.vf0) { a.vf1[p] = a.vf0[o]; a.vf1[N + p] = a.vf0[N + o]; a.vf1[2 * N + p] = a.vf0[2 * N + o]; }
+      if (a.vd0) { a.vd1[p] = a.vd0[o]; a.vd1[N + p] = a.vd0[N + o]; a.vd1[2 * N + p] = a.vd0[2 * N + o]; }
+      a.id1[p] = myid;
+      const float qv = a.qf0[o];
+      a.qf1[p] = qv;
+      if (a.qd0) a.qd1[p] = a.qd0[o];
+      if (a.ty0) a.ty1[p] = a.ty0[o];
+      a.im1[p] = a.im0[o];
+      if (mych) {
+        const int64_t pc = cbeg + crank;
+        a.cs[pc] = sx; a.cs[Nq + pc] = sy; a.cs[2 * Nq + pc] = sz;
+        a.cqf[pc] = qv;
+        if (a.cqd) a.cqd[pc] = a.qd0[o];
+        a.cmap[pc] = (int32_t)p;
+      }
+    }
+  }
+}
+
+cudaError_t launch_bin_sort(Ctx &c) {
+  const int64_t N = c.N, nc = c.grid.ncell;
+  const int b0 = c.cur, b1 = 1 - c.cur;
+  cudaError_t e = cudaMemsetAsync(c.cell_count, 0, sizeof(int32_t) * 2 * nc, c.stream);
+  if (e != cudaSuccess) return e;
+  if (N > 0) {
+    bin_count_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(
+        N, c.s[b0], c.qf[b0], c.grid.n[0], c.grid.n[1], c.grid.n[2], c.cell_count,
+        c.ccell_count, c.key, c.off);
+  }
+  const int64_t nblk = c.scan_nblk;
+  scan_block_kernel<<<dim3((unsigned)nblk, 2), kScanThreads, 0, c.stream>>>(
+      c.cell_count, c.cell_start, c.scan_blk, nc, nblk);
+  scan_top_kernel<<<2, 1024, 0, c.stream>>>(c.scan_blk, nblk, c.cell_start, nc);
+  scan_add_kernel<<<dim3((unsigned)nblk, 2), kScanThreads, 0, c.stream>>>(c.cell_start,
+                                                                         c.scan_blk, nc, nblk);
+  if (N > 0) {
+    bin_scatter_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(
+        N, c.key, c.off, c.cell_start, c.tmp);
+    PermuteArgs a;
+    a.N = N; a.Nq = c.Nq; a.ncell = nc;
+    a.cell_start = c.cell_start; a.ccell_start = c.ccell_start; a.tmp = c.tmp;
+    a.s0 = c.s[b0]; a.s1 = c.s[b1];
+    a.vf0 = c.vf[b0]; a.vf1 = c.vf[b1];
+    a.vd0 = c.vd[b0]; a.vd1 = c.vd[b1];
+    a.id0 = c.id[b0]; a.id1 = c.id[b1];
+    a.qf0 = c.qf[b0]; a.qf1 = c.qf[b1];
+    a.qd0 = c.qd[b0]; a.qd1 = c.qd[b1];
+    a.ty0 = c.type[b0]; a.ty1 = c.type[b1];
+    a.im0 = c.invm[b0]; a.im1 = c.invm[b1];
+    a.cs = c.cs; a.cqf = c.cqf; a.cqd = c.cqd; a.cmap = c.cmap;
+    const int64_t threads = nc * 32;
+    bin_rank_permute_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(a);
+  }
+  c.cur = b1;
+  return cudaGetLastError();
+}
+
+}  // namespace rbe

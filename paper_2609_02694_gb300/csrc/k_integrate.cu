@@ -1,0 +1,258 @@
+// k_integrate.cu -- velocity Verlet on the fixed-point grid, energy totals, and the
+// gathers that translate between cell-sorted storage and caller id order.
+//
+// Velocity Verlet (the time integrator of Sec. 2.1):
+//   v += (F/m)(dt/2) kappa;  s += rint(v dt 2^32 / L)  (FP64 increment, wraps mod 2^32)
+//   ... forces at the new positions ...;  v += (F/m)(dt/2) kappa
+// Every kernel here is a single streaming pass (HBM-bound) except the totals, which sum
+// the per-block partials of all force kernels in a fixed order (latency-bound).
+#include "rbe_internal.cuh"
+
+namespace rbe {
+
+template <typename V, typename FT>
+__global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
+                                  const float *__restrict__ invm, uint32_t *__restrict__ s,
+                                  int64_t N, double hdk, double dt, double Lx, double Ly,
+                                  double Lz, int *__restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double L[3] = {Lx, Ly, Lz};
+  const V im = (V)invm[i];
+  bool bad = false;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    V vv = v[d * N + i] + (V)F[d * N + i] * im * (V)hdk;
+    v[d * N + i] = vv;
+    const double inc = __ddiv_rn(__dmul_rn(__dmul_rn((double)vv, dt), kTwo32), L[d]);
+    bad |= !isfinite(inc) || fabs(inc) > 2.0e9;
+    const long long st = bad ? 0ll : __double2ll_rn(inc);
+    s[d * N + i] += (uint32_t)st;
+  }
+  if (bad) atomicOr(err, ERRBIT_NONFINITE);
+}
+
+template <typename V, typename FT>
+__global__ void __launch_bounds__(256)
+    kick_kernel(V *__restrict__ v, const FT *__restrict__ F, const float *__restrict__ invm,
+                int64_t N, double hdk, double inv_kappa, int do_kick,
+                double *__restrict__ ke_part) {
+  __shared__ double sh[256];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double ke = 0.0;
+  if (i < N) {
+    const V im = (V)invm[i];
+    double v2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      V vv = v[d * N + i];
+      if (do_kick) {
+        vv += (V)F[d * N + i] * im * (V)hdk;
+        v[d * N + i] = vv;
+      }
+      v2 += (double)vv * (double)vv;
+    }
+    ke = 0.5 * v2 / (double)invm[i] * inv_kappa;
+  }
+  sh[threadIdx.x] = ke;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ke_part[blockIdx.x] = sh[0];
+}
+
+struct TotalsArgs {
+  const double *pair, *coul, *rbl, *ke, *emode;
+  int64_t n_pair, n_coul, n_rbl, n_ke;
+  int P;
+  double U_self;
+  double *scal;
+};
+
+// Fixed-order reduction of every partial into the scalars (ACC = float for the plain
+// FP32 form, double otherwise).
+template <typename ACC>
+__global__ void __launch_bounds__(256) totals_kernel(TotalsArgs a) {
+  constexpr int NV = 7;  // ureal ulj wreal wlj uk wk ke
+  __shared__ ACC sh[NV][256];
+  ACC acc[NV];
+  for (int k = 0; k < NV; ++k) acc[k] = (ACC)0;
+  const double *srcs[3] = {a.pair, a.coul, a.rbl};
+  const int64_t ns[3] = {a.n_pair, a.n_coul, a.n_rbl};
+  for (int r = 0; r < 3; ++r)
+    for (int64_t b = threadIdx.x; b < ns[r]; b += blockDim.x)
+      for (int k = 0; k < NQ_PAIR; ++k) acc[k] += (ACC)srcs[r][b * NQ_PAIR + k];
+  for (int l = threadIdx.x; l < a.P; l += blockDim.x) {
+    acc[4] += (ACC)a.emode[2 * l];
+    acc[5] += (ACC)a.emode[2 * l + 1];
+  }
+  for (int64_t b = threadIdx.x; b < a.n_ke; b += blockDim.x) acc[6] += (ACC)a.ke[b];
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double ur = (double)sh[Q_UREAL][0], ul = (double)sh[Q_ULJ][0];
+    const double wr = (double)sh[Q_WREAL][0], wl = (double)sh[Q_WLJ][0];
+    const double uk = (double)sh[4][0], wk = (double)sh[5][0], ke = (double)sh[6][0];
+    a.scal[S_UREAL] = ur;
+    a.scal[S_ULJ] = ul;
+    a.scal[S_UK] = uk;
+    a.scal[S_USELF] = a.U_self;
+    a.scal[S_UTOT] = ur + ul + uk - a.U_self;
+    a.scal[S_KE] = ke;
+    a.scal[S_WREAL] = wr;
+    a.scal[S_WLJ] = wl;
+    a.scal[S_WK] = wk;
+    a.scal[S_WTOT] = wr + wl + wk;
+  }
+}
+
+template <typename FT, typename OT>
+__global__ void scatter_forces_kernel(const FT *__restrict__ F, const int32_t *__restrict__ id,
+                                      int64_t N, OT *__restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t o = (int64_t)id[k] * 3;
+  out[o] = (OT)F[k];
+  out[o + 1] = (OT)F[N + k];
+  out[o + 2] = (OT)F[2 * N + k];
+}
+
+template <typename V>
+__global__ void scatter_state_kernel(const uint32_t *__restrict__ s, const V *__restrict__ v,
+                                     const int32_t *__restrict__ id, int64_t N, int what,
+                                     double hx, double hy, double hz, double *__restrict__ outd,
+                                     uint32_t *__restrict__ outu) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t o = (int64_t)id[k] * 3;
+  if (what == 0) {
+    outd[o] = (double)s[k] * hx;
+    outd[o + 1] = (double)s[N + k] * hy;
+    outd[o + 2] = (double)s[2 * N + k] * hz;
+  } else if (what == 1) {
+    outd[o] = (double)v[k];
+    outd[o + 1] = (double)v[N + k];
+    outd[o + 2] = (double)v[2 * N + k];
+  } else {
+    outu[o] = s[k];
+    outu[o + 1] = s[N + k];
+    outu[o + 2] = s[2 * N + k];
+  }
+}
+
+__global__ void set_positions_kernel(const double *__restrict__ pos, const int32_t *__restrict__ id,
+                                     int64_t N, double Lx, double Ly, double Lz,
+                                     uint32_t *__restrict__ s) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t o = (int64_t)id[k] * 3;
+  const double L[3] = {Lx, Ly, Lz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double f = __dmul_rn(__ddiv_rn(pos[o + d], L[d]), kTwo32);
+    const double fm = f - kTwo32 * floor(f / kTwo32);  // wrap into [0, 2^32)
+    s[d * N + k] = (uint32_t)(unsigned long long)__double2ll_rn(fm);
+  }
+}
+
+__global__ void scatter_int_kernel(const int32_t *__restrict__ src, const int32_t *__restrict__ id,
+                                   int64_t N, int width, int32_t *__restrict__ dst) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t o = (int64_t)id[k] * width;
+  for (int w = 0; w < width; ++w) dst[o + w] = src[k * width + w];
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_kick_drift(Ctx &c) {
+  const int b = c.cur;
+  const double hdk = 0.5 * c.dt * c.kappa;
+  if (c.N == 0) return cudaSuccess;
+  if (c.precision == RBE_FP64)
+    kick_drift_kernel<double, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(
+        c.vd[b], c.Fd, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err);
+  else
+    kick_drift_kernel<float, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(
+        c.vf[b], c.F, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err);
+  return cudaGetLastError();
+}
+
+static cudaError_t kick_impl(Ctx &c, int do_kick) {
+  const int b = c.cur;
+  const double hdk = 0.5 * c.dt * c.kappa;
+  if (c.N == 0) return cudaSuccess;
+  if (c.precision == RBE_FP64)
+    kick_kernel<double, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(
+        c.vd[b], c.Fd, c.invm[b], c.N, hdk, 1.0 / c.kappa, do_kick, c.epart + c.off_ke);
+  else
+    kick_kernel<float, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(
+        c.vf[b], c.F, c.invm[b], c.N, hdk, 1.0 / c.kappa, do_kick, c.epart + c.off_ke);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick(Ctx &c) { return kick_impl(c, 1); }
+cudaError_t launch_kinetic(Ctx &c) { return kick_impl(c, 0); }
+
+cudaError_t launch_totals(Ctx &c) {
+  TotalsArgs a;
+  a.pair = c.epart + c.off_pair; a.n_pair = c.n_pair_blk;
+  a.coul = c.epart + c.off_coul; a.n_coul = c.n_coul_blk;
+  a.rbl = c.epart + c.off_rbl; a.n_rbl = c.n_rbl_blk;
+  a.ke = c.epart + c.off_ke; a.n_ke = c.n_ke_blk;
+  a.emode = c.emode; a.P = c.P;
+  a.U_self = c.U_self;
+  a.scal = c.scal;
+  if (c.precision == RBE_FP32) totals_kernel<float><<<1, 256, 0, c.stream>>>(a);
+  else totals_kernel<double><<<1, 256, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_forces(Ctx &c, bool to_double) {
+  const int b = c.cur;
+  if (c.N == 0) return cudaSuccess;
+  if (c.precision == RBE_FP64) {
+    if (to_double) scatter_forces_kernel<double, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(c.Fd, c.id[b], c.N, c.outd);
+    else scatter_forces_kernel<double, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(c.Fd, c.id[b], c.N, c.outf);
+  } else {
+    if (to_double) scatter_forces_kernel<float, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(c.F, c.id[b], c.N, c.outd);
+    else scatter_forces_kernel<float, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(c.F, c.id[b], c.N, c.outf);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_state(Ctx &c, int what) {
+  const int b = c.cur;
+  if (c.N == 0) return cudaSuccess;
+  const double hx = c.box[0] / kTwo32, hy = c.box[1] / kTwo32, hz = c.box[2] / kTwo32;
+  uint32_t *outu = reinterpret_cast<uint32_t *>(c.outf);
+  if (c.precision == RBE_FP64)
+    scatter_state_kernel<double><<<nblk(c.N, 256), 256, 0, c.stream>>>(c.s[b], c.vd[b], c.id[b], c.N, what, hx, hy, hz, c.outd, outu);
+  else
+    scatter_state_kernel<float><<<nblk(c.N, 256), 256, 0, c.stream>>>(c.s[b], c.vf[b], c.id[b], c.N, what, hx, hy, hz, c.outd, outu);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_positions(Ctx &c) {
+  const int b = c.cur;
+  if (c.N == 0) return cudaSuccess;
+  set_positions_kernel<<<nblk(c.N, 256), 256, 0, c.stream>>>(c.pos_stage, c.id[b], c.N, c.box[0],
+                                                             c.box[1], c.box[2], c.s[b]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_int(Ctx &c, const int32_t *src_sorted, int32_t *dst_id, int width) {
+  const int b = c.cur;
+  if (c.N == 0) return cudaSuccess;
+  scatter_int_kernel<<<nblk(c.N, 256), 256, 0, c.stream>>>(src_sorted, c.id[b], c.N, width, dst_id);
+  return cudaGetLastError();
+}
+
+}  // namespace rbe

@@ -1,0 +1,205 @@
+// k_pair.cu -- real-space pair forces over linked cells (Eqs. F_i, G_short, LJ).
+//
+// F_i += sum_{j != i, r_ij <= r_c} (C q_i q_j G(r) + G_LJ(r)) (r_i - r_j)
+//   G(r)    = erfc(sqrt(alpha) r) / r^3 + 2 sqrt(alpha) exp(-alpha r^2) / (sqrt(pi) r^2)
+//   G_LJ(r) = 24 eps (2 sigma^12 / r^14 - sigma^6 / r^8)
+// with r_i - r_j the minimum image: on the 2^-32 grid that is the two's-complement
+// difference of the fractional coordinates, so no image shifts are needed.
+//
+// Work decomposition (one thread per particle i, 32 consecutive cell-sorted particles per
+// warp). Lanes sharing a cell row (c_y, c_z) form a group, and the group walks the union
+// of its members' stencils: for every (dy, dz) row, one contiguous run of cells in x.
+//  1. Stage: the warp loads 32 candidates j at a time. Each lane converts one of them to
+//     FP32 coordinates relative to the group leader and writes it to shared memory.
+//  2. Test: every lane tests its own i against the 32 staged j (broadcast reads) with a
+//     cutoff widened by 1e-5, and appends the hits to a per-lane list in shared memory.
+//     The append is branch-free.
+//  3. Evaluate: when a list may overflow, and at the end, each lane walks its own list.
+//     It recomputes the displacement exactly from the integer coordinates and applies
+//     the exact cutoff decision: FP32 outside a +-1e-5 band, FP64 inside it, which
+//     matches the oracle's decision bit for bit. Then it evaluates the pair force.
+// Forces are summed per i in a fixed j order with no atomics, so results are run-to-run
+// reproducible. The hot loop is FP32 ALU / SFU bound.
+#include <climits>
+
+#include "pair_common.cuh"
+
+namespace rbe {
+
+template <typename real, bool LJ, bool COUL, bool MULTI>
+__global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a) {
+  __shared__ float4 stage[kPairWarps][32];
+  __shared__ int32_t list[kPairWarps][kListK][32];
+  __shared__ double wred[kPairWarps][NQ_PAIR];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const int64_t n = a.set.n;
+  const int64_t i0 = ((int64_t)blockIdx.x * kPairWarps + wid) * 32;
+  const int64_t i = i0 + lane;
+  const bool valid = i < n;
+  const LJTable *tab = a.table;
+  PairAcc<real> acc;
+  acc.fx = acc.fy = acc.fz = acc.ulj = acc.wlj = acc.uc = acc.wc = (real)0;
+  acc.nbr = 0;
+  if (i0 < n) {
+    const int n0 = a.grid.n[0], n1 = a.grid.n[1], n2 = a.grid.n[2];
+    const int R0 = a.grid.R[0], R1 = a.grid.R[1], R2 = a.grid.R[2];
+    const uint32_t sxi = valid ? a.set.sx[i] : 0u;
+    const uint32_t syi = valid ? a.set.sy[i] : 0u;
+    const uint32_t szi = valid ? a.set.sz[i] : 0u;
+    real qi = (real)0;
+    if (COUL && valid) qi = sizeof(real) == 8 ? (real)a.set.qd[i] : (real)a.set.qf[i];
+    const int ti = (MULTI && valid) ? a.set.type[i] : 0;
+    const int cx = cell_of(sxi, n0), cy = cell_of(syi, n1), cz = cell_of(szi, n2);
+    int cnt = 0;
+    auto flush = [&]() {
+      const int maxc = __reduce_max_sync(FULL, cnt);
+      for (int t = 0; t < maxc; ++t) {
+        if (t < cnt) {
+          const int64_t j = list[wid][t][lane];
+          pair_body<real, LJ, COUL, MULTI>(a, tab, sxi, syi, szi, qi, ti, j, acc);
+        }
+      }
+      cnt = 0;
+      __syncwarp();
+    };
+    unsigned remaining = __ballot_sync(FULL, valid);
+    while (remaining) {
+      const int leader = __ffs(remaining) - 1;
+      const int gy = __shfl_sync(FULL, cy, leader), gz = __shfl_sync(FULL, cz, leader);
+      const bool in = valid && cy == gy && cz == gz && ((remaining >> lane) & 1u);
+      const unsigned gmask = __ballot_sync(FULL, in);
+      remaining &= ~gmask;
+      const int cxlo = __reduce_min_sync(FULL, in ? cx : INT_MAX);
+      const int cxhi = __reduce_max_sync(FULL, in ? cx : INT_MIN);
+      const uint32_t ox = __shfl_sync(FULL, sxi, leader);
+      const uint32_t oy = __shfl_sync(FULL, syi, leader);
+      const uint32_t oz = __shfl_sync(FULL, szi, leader);
+      const float xi = (float)(int)(sxi - ox) * a.pc.h[0];
+      const float yi = (float)(int)(syi - oy) * a.pc.h[1];
+      const float zi = (float)(int)(szi - oz) * a.pc.h[2];
+      const int span = cxhi - cxlo + 2 * R0 + 1;
+      for (int dz = -R2; dz <= R2; ++dz) {
+        const int rz = ((gz + dz) % n2 + n2) % n2;
+        for (int dy = -R1; dy <= R1; ++dy) {
+          const int ry = ((gy + dy) % n1 + n1) % n1;
+          const int64_t rowbase = (int64_t)n0 * (ry + (int64_t)n1 * rz);
+          int sa[2], sb[2], nseg;
+          if (span >= n0) {
+            sa[0] = 0; sb[0] = n0 - 1; nseg = 1;
+          } else {
+            const int lo = cxlo - R0, hi = cxhi + R0;
+            if (lo < 0) { sa[0] = lo + n0; sb[0] = n0 - 1; sa[1] = 0; sb[1] = hi; nseg = 2; }
+            else if (hi >= n0) { sa[0] = lo; sb[0] = n0 - 1; sa[1] = 0; sb[1] = hi - n0; nseg = 2; }
+            else { sa[0] = lo; sb[0] = hi; nseg = 1; }
+          }
+          for (int sgi = 0; sgi < nseg; ++sgi) {
+            const int64_t j0 = a.set.cell_start[rowbase + sa[sgi]];
+            const int64_t j1 = a.set.cell_start[rowbase + sb[sgi] + 1];
+            for (int64_t base = j0; base < j1; base += 32) {
+              if (__any_sync(FULL, cnt > kListK - 32)) flush();
+              const int64_t jj = base + lane;
+              if (jj < j1) {
+                stage[wid][lane] = make_float4((float)(int)(a.set.sx[jj] - ox) * a.pc.h[0],
+                                               (float)(int)(a.set.sy[jj] - oy) * a.pc.h[1],
+                                               (float)(int)(a.set.sz[jj] - oz) * a.pc.h[2], 0.f);
+              }
+              __syncwarp();
+              const int nj = (int)min((int64_t)32, j1 - base);
+              for (int t = 0; t < nj; ++t) {
+                const float4 p = stage[wid][t];
+                const float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
+                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                const bool hit = in && r2 < a.pc.rc2_hi && (base + t) != i;
+                list[wid][cnt][lane] = (int32_t)(base + t);
+                cnt += hit ? 1 : 0;
+              }
+              __syncwarp();
+            }
+          }
+        }
+      }
+    }
+    flush();
+    if (valid) {
+      const int64_t o = a.set.map ? (int64_t)a.set.map[i] : i;
+      const int64_t S = a.Fstride;
+      if (sizeof(real) == 8) {
+        if (a.accumulate) { a.Fd[o] += (double)acc.fx; a.Fd[S + o] += (double)acc.fy; a.Fd[2 * S + o] += (double)acc.fz; }
+        else { a.Fd[o] = (double)acc.fx; a.Fd[S + o] = (double)acc.fy; a.Fd[2 * S + o] = (double)acc.fz; }
+      } else {
+        if (a.accumulate) { a.F[o] += (float)acc.fx; a.F[S + o] += (float)acc.fy; a.F[2 * S + o] += (float)acc.fz; }
+        else { a.F[o] = (float)acc.fx; a.F[S + o] = (float)acc.fy; a.F[2 * S + o] = (float)acc.fz; }
+      }
+      if (a.nbr) a.nbr[i] = acc.nbr;
+    }
+  }
+  // block partials of the energies and virials (halves of the per-i sums)
+  double v[NQ_PAIR] = {(double)acc.uc, (double)acc.ulj, (double)acc.wc, (double)acc.wlj};
+#pragma unroll
+  for (int k = 0; k < NQ_PAIR; ++k) {
+    const double w = warp_sum(v[k]);
+    if (lane == 0) wred[wid][k] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ_PAIR) {
+    double s = 0.0;
+    for (int w = 0; w < kPairWarps; ++w) s += wred[w][threadIdx.x];
+    a.epart[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = 0.5 * s;
+  }
+}
+
+template <typename real, bool LJ, bool COUL>
+static void launch_one(const PairArgs &a, int64_t n, bool multi, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((n + 32 * kPairWarps - 1) / (32 * kPairWarps));
+  if (blocks == 0) return;
+  if (multi) pair_kernel<real, LJ, COUL, true><<<blocks, kPairWarps * 32, 0, st>>>(a);
+  else pair_kernel<real, LJ, COUL, false><<<blocks, kPairWarps * 32, 0, st>>>(a);
+}
+
+int64_t pair_blocks(int64_t n) { return (n + 32 * kPairWarps - 1) / (32 * kPairWarps); }
+
+cudaError_t launch_pair(Ctx &c, bool want_counts) {
+  const int b = c.cur;
+  const bool fused = c.Nq * 2 > c.N;  // most particles charged: one LJ + Coulomb pass
+  const bool multi = c.nt > 1;
+  PairArgs a;
+  a.grid = c.grid;
+  a.pc = c.pc;
+  a.eps24 = c.lj.eps24[0]; a.eps4 = c.lj.eps4[0]; a.sig2 = c.lj.sig2[0];
+  a.eps24d = c.lj.eps24d[0]; a.eps4d = c.lj.eps4d[0]; a.sig2d = c.lj.sig2d[0];
+  a.table = reinterpret_cast<const LJTable *>(c.lj_dev);
+  a.F = c.F; a.Fd = c.Fd; a.Fstride = c.N;
+  // full set
+  a.set.sx = c.s[b]; a.set.sy = c.s[b] + c.N; a.set.sz = c.s[b] + 2 * c.N;
+  a.set.qf = c.qf[b]; a.set.qd = c.qd[b]; a.set.type = c.type[b];
+  a.set.cell_start = c.cell_start; a.set.map = nullptr; a.set.n = c.N;
+  a.accumulate = 0;
+  a.epart = c.epart + c.off_pair;
+  a.nbr = want_counts ? c.nbr : nullptr;
+  const bool fp64 = c.precision == RBE_FP64;
+  if (fused) {
+    if (fp64) launch_one<double, true, true>(a, c.N, multi, c.stream);
+    else launch_one<float, true, true>(a, c.N, multi, c.stream);
+  } else {
+    if (fp64) launch_one<double, true, false>(a, c.N, multi, c.stream);
+    else launch_one<float, true, false>(a, c.N, multi, c.stream);
+  }
+  mark(c, RBE_PH_PAIR2);
+  if (!fused) {
+    if (c.Nq > 0) {
+      PairArgs b2 = a;
+      b2.set.sx = c.cs; b2.set.sy = c.cs + c.Nq; b2.set.sz = c.cs + 2 * c.Nq;
+      b2.set.qf = c.cqf; b2.set.qd = c.cqd; b2.set.type = nullptr;
+      b2.set.cell_start = c.ccell_start; b2.set.map = c.cmap; b2.set.n = c.Nq;
+      b2.accumulate = 1;
+      b2.epart = c.epart + c.off_coul;
+      b2.nbr = nullptr;
+      if (fp64) launch_one<double, false, true>(b2, c.Nq, false, c.stream);
+      else launch_one<float, false, true>(b2, c.Nq, false, c.stream);
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rbe

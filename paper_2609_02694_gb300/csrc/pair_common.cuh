@@ -1,0 +1,137 @@
+// pair_common.cuh -- pair interaction of the real-space part (Eqs. F_i, G_short, LJ) shared
+// by the cell-list kernel and the random batch list kernel.
+#pragma once
+#include "rbe_internal.cuh"
+
+namespace rbe {
+
+constexpr int kPairWarps = 4;
+constexpr int kListK = 64;
+
+struct PairArgs {
+  PairSet set;
+  Grid grid;
+  PairConst pc;
+  // single-type LJ parameters
+  float eps24, eps4, sig2;
+  double eps24d, eps4d, sig2d;
+  const LJTable *table;  // device copy, multi-type only
+  float *F;
+  double *Fd;
+  int64_t Fstride;   // N of the force arrays (SoA stride)
+  int accumulate;    // add to F instead of overwriting
+  double *epart;     // per-block partials (NQ_PAIR doubles each)
+  int32_t *nbr;      // per-particle neighbour counts (sorted order of the set), nullable
+};
+
+template <typename real>
+struct PairAcc {
+  real fx, fy, fz, ulj, wlj, uc, wc;
+  int nbr;
+};
+
+// Squared distance of the exact cutoff decision (the oracle's definition): dx_d =
+// (int32)(s_i - s_j) * (L_d / 2^32) and r2 = dx^2 + dy^2 + dz^2 in FP64, no FMA.
+__device__ __forceinline__ double exact_r2(const PairConst &pc, int dsx, int dsy, int dsz) {
+  const double ex = __dmul_rn((double)dsx, pc.hd[0]);
+  const double ey = __dmul_rn((double)dsy, pc.hd[1]);
+  const double ez = __dmul_rn((double)dsz, pc.hd[2]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+}
+
+// Pair force, energies and virial of one pair that is inside the cutoff (Eqs. F_i,
+// G_short, LJ), added to acc.
+template <typename real, bool LJ, bool COUL, bool MULTI>
+__device__ __forceinline__ void pair_force(const PairArgs &a, const LJTable *tab, real dx,
+                                           real dy, real dz, real r2, real qi, int ti,
+                                           int64_t j, PairAcc<real> &acc) {
+  const PairConst &pc = a.pc;
+  real g = (real)0;
+  if (LJ) {
+    real e24, e4, s2;
+    if (MULTI) {
+      const int tj = a.set.type[j];
+      const int pt = ti * tab->nt + tj;
+      if (sizeof(real) == 8) { e24 = (real)tab->eps24d[pt]; e4 = (real)tab->eps4d[pt]; s2 = (real)tab->sig2d[pt]; }
+      else { e24 = (real)tab->eps24[pt]; e4 = (real)tab->eps4[pt]; s2 = (real)tab->sig2[pt]; }
+    } else {
+      if (sizeof(real) == 8) { e24 = (real)a.eps24d; e4 = (real)a.eps4d; s2 = (real)a.sig2d; }
+      else { e24 = (real)a.eps24; e4 = (real)a.eps4; s2 = (real)a.sig2; }
+    }
+    real rinv2;
+    if (sizeof(real) == 8) rinv2 = (real)(1.0 / (double)r2);
+    else rinv2 = (real)__frcp_rn((float)r2);
+    const real sr2 = s2 * rinv2;
+    const real sr6 = sr2 * sr2 * sr2;
+    const real gl = e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);
+    g += gl;
+    acc.ulj += e4 * sr6 * (sr6 - (real)1);
+    acc.wlj += gl * r2;
+  }
+  if (COUL) {
+    real qj;
+    if (sizeof(real) == 8) qj = (real)a.set.qd[j];
+    else qj = (real)a.set.qf[j];
+    const real qq = qi * qj;
+    if (qq != (real)0) {
+      real r, rinv, erfcv, expv;
+      if (sizeof(real) == 8) {
+        r = (real)sqrt((double)r2);
+        rinv = (real)1 / r;
+        erfcv = (real)erfc(pc.sqrt_alpha_d * (double)r);
+        expv = (real)exp(-pc.alpha_d * (double)r2);
+      } else {
+        r = (real)sqrtf((float)r2);
+        rinv = (real)__frcp_rn((float)r);
+        erfcv = (real)erfcf(pc.sqrt_alpha * (float)r);
+        expv = (real)expf(-pc.alpha * (float)r2);
+      }
+      const real Cqq = (sizeof(real) == 8 ? (real)pc.C_d : (real)pc.C) * qq;
+      const real tsp = sizeof(real) == 8 ? (real)pc.two_sqrt_alpha_over_sqrt_pi_d
+                                         : (real)pc.two_sqrt_alpha_over_sqrt_pi;
+      const real rinv2 = rinv * rinv;
+      const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
+      g += gc;
+      acc.uc += Cqq * erfcv * rinv;
+      acc.wc += gc * r2;
+    }
+  }
+  acc.fx += g * dx;
+  acc.fy += g * dy;
+  acc.fz += g * dz;
+}
+
+
+// Exact cutoff decision at r_c followed by the pair force (cell-list real space).
+template <typename real, bool LJ, bool COUL, bool MULTI>
+__device__ __forceinline__ void pair_body(const PairArgs &a, const LJTable *tab, uint32_t sxi,
+                                          uint32_t syi, uint32_t szi, real qi, int ti,
+                                          int64_t j, PairAcc<real> &acc) {
+  const PairConst &pc = a.pc;
+  const int dsx = (int)(sxi - a.set.sx[j]);
+  const int dsy = (int)(syi - a.set.sy[j]);
+  const int dsz = (int)(szi - a.set.sz[j]);
+  real dx, dy, dz, r2;
+  if (sizeof(real) == 8) {
+    dx = (real)__dmul_rn((double)dsx, pc.hd[0]);
+    dy = (real)__dmul_rn((double)dsy, pc.hd[1]);
+    dz = (real)__dmul_rn((double)dsz, pc.hd[2]);
+    r2 = (real)__dadd_rn(__dadd_rn(__dmul_rn((double)dx, (double)dx),
+                                   __dmul_rn((double)dy, (double)dy)),
+                         __dmul_rn((double)dz, (double)dz));
+    if (!((double)r2 <= pc.rc2d)) return;
+  } else {
+    dx = (real)((float)dsx * pc.h[0]);
+    dy = (real)((float)dsy * pc.h[1]);
+    dz = (real)((float)dsz * pc.h[2]);
+    r2 = dx * dx + dy * dy + dz * dz;
+    if ((float)r2 > pc.rc2_hi) return;
+    if ((float)r2 >= pc.rc2_lo) {  // exact decision inside the band
+      if (!(exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d)) return;
+    }
+  }
+  acc.nbr += 1;
+  pair_force<real, LJ, COUL, MULTI>(a, tab, dx, dy, dz, r2, qi, ti, j, acc);
+}
+
+}  // namespace rbe

@@ -1,0 +1,767 @@
+// rbe_api.cu -- C ABI of the RBE force path: validation, one-time setup (sampling tables,
+// cell grid, device allocation), the force pipeline and the graph-captured Verlet step.
+//
+// Setup runs once on the host in FP64. The per-axis mode tables follow the sampling
+// density of Eq. F_long_RBE, and the cell grid follows the cutoff. Every per-step
+// operation runs in the kernels of k_*.cu, on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rbe_internal.cuh"
+
+using namespace rbe;
+
+namespace rbe {
+int64_t pair_blocks(int64_t n);
+int64_t rbl_blocks(int64_t n);
+}  // namespace rbe
+
+struct rbe_ctx : public rbe::Ctx {};
+
+namespace {
+
+#define RBE_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) {                                 \
+      fprintf(stderr, "rbe: CUDA error %s at %s:%d\n",       \
+              cudaGetErrorString(e_), __FILE__, __LINE__);   \
+      return RBE_ERR_CUDA;                                   \
+    }                                                        \
+  } while (0)
+
+template <typename T>
+int dalloc(Ctx &c, T **p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  const size_t bytes = sizeof(T) * (size_t)count;
+  if (cudaMalloc((void **)p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return RBE_ERR_OOM;
+  }
+  c.bytes += (int64_t)bytes;
+  return RBE_OK;
+}
+
+void dfree(void *p) {
+  if (p) cudaFree(p);
+}
+
+// Per-axis table of the 1-D discrete Gaussian exp(-k^2 / 4 alpha), k = 2 pi m / L:
+// half-width M (weights beyond it are below 2^-53), cumulative thresholds
+// T[i] = floor(CDF(m_i) / Z * 2^32) with T[2M] = 2^32, and Z.
+int axis_half_width(double L, double alpha) {
+  return (int)std::ceil(L * std::sqrt(4.0 * alpha * 53.0 * std::log(2.0)) / (2.0 * kPi));
+}
+
+double axis_weight(int m, double L, double alpha) {
+  const double km = 2.0 * kPi * (double)m / L;
+  return std::exp(-(km * km) / (4.0 * alpha));
+}
+
+void axis_table(double L, double alpha, int M, std::vector<uint64_t> &T, double &Z) {
+  const int n = 2 * M + 1;
+  T.assign(n, 0);
+  double z = 0.0;
+  for (int i = 0; i < n; ++i) z += axis_weight(i - M, L, alpha);
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) {
+    acc += axis_weight(i - M, L, alpha);
+    T[i] = (uint64_t)std::floor(acc / z * kTwo32);
+  }
+  T[n - 1] = (uint64_t)1 << 32;
+  Z = z;
+}
+
+uint32_t quantise(double r, double L) {
+  const double f = (r / L) * kTwo32;
+  const double fm = f - kTwo32 * std::floor(f / kTwo32);
+  return (uint32_t)(unsigned long long)std::llrint(fm);
+}
+
+}  // namespace
+
+namespace rbe {
+void mark(Ctx &c, int k) {
+  if (!c.timing || !c.ev[k]) return;
+  cudaEventRecord(c.ev[k], c.stream);
+  c.ev_used[k] = true;
+}
+}  // namespace rbe
+
+namespace {
+
+int free_all(Ctx &c) {
+  for (int k = 0; k <= RBE_N_PHASE; ++k)
+    if (c.ev[k]) {
+      cudaEventDestroy(c.ev[k]);
+      c.ev[k] = nullptr;
+    }
+  for (int b = 0; b < 2; ++b) {
+    dfree(c.s[b]); dfree(c.vf[b]); dfree(c.vd[b]); dfree(c.id[b]); dfree(c.qf[b]);
+    dfree(c.qd[b]); dfree(c.type[b]); dfree(c.invm[b]);
+    if (c.graph[b]) cudaGraphExecDestroy(c.graph[b]);
+    c.graph[b] = nullptr;
+  }
+  dfree(c.F); dfree(c.Fd); dfree(c.cs); dfree(c.cqf); dfree(c.cqd); dfree(c.cmap);
+  dfree(c.cell_count); dfree(c.cell_start); dfree(c.key); dfree(c.off); dfree(c.tmp);
+  dfree(c.scan_blk);
+  for (int d = 0; d < 3; ++d) dfree(c.T[d]);
+  dfree(c.m); dfree(c.kcf); dfree(c.kcd); dfree(c.sf_part); dfree(c.rho); dfree(c.abf);
+  dfree(c.abd); dfree(c.emode); dfree(c.epart); dfree(c.scal); dfree(c.step_dev);
+  dfree(c.err); dfree(c.nbr); dfree(c.nshell); dfree(c.partners); dfree(c.rbl_mean);
+  dfree(c.rbl_part); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+  c.cap_stream = nullptr;
+  if (c.scal_host) cudaFreeHost(c.scal_host);
+  c.scal_host = nullptr;
+  return RBE_OK;
+}
+
+// bin + sort -> sample -> structure factor -> real space -> k-space gather
+int force_pipeline(Ctx &c, bool debug) {
+  mark(c, RBE_PH_BIN);
+  RBE_CUDA_TRY(launch_bin_sort(c));
+  mark(c, RBE_PH_SAMPLE);
+  RBE_CUDA_TRY(launch_sample_k(c));
+  mark(c, RBE_PH_SF);
+  RBE_CUDA_TRY(launch_structure_factor(c));
+  mark(c, RBE_PH_PAIR);
+  if (c.rbl) RBE_CUDA_TRY(launch_rbl(c, debug));
+  else RBE_CUDA_TRY(launch_pair(c, debug));
+  mark(c, RBE_PH_GATHER);
+  RBE_CUDA_TRY(launch_kspace_gather(c));
+  mark(c, RBE_PH_TAIL);
+  return RBE_OK;
+}
+
+// Kernels one Verlet step launches (memsets excluded).
+int64_t kernels_per_step(const Ctx &c) {
+  int64_t k = 2;                         // kick-drift, step counter
+  k += 6;                                // count, 3 scan passes, scatter, rank+permute
+  k += 1;                                // sampler
+  k += c.Nq > 0 ? 2 : 0;                 // structure factor + combine
+  if (c.rbl) k += 3;                     // RBL, mean, subtract
+  else k += (c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2;  // pair passes
+  k += c.Nq > 0 ? 1 : 0;                 // gather
+  k += 2;                                // kick (+kinetic), totals
+  return k;
+}
+
+int read_device_flags(Ctx &c) {
+  int flags = 0;
+  RBE_CUDA_TRY(cudaMemcpyAsync(&flags, c.err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  if (flags) {
+    RBE_CUDA_TRY(cudaMemsetAsync(c.err, 0, sizeof(int), c.stream));
+    if (flags & ERRBIT_SAMPLER) return RBE_ERR_SAMPLER;
+    if (flags & ERRBIT_NONFINITE) return RBE_ERR_NONFINITE;
+  }
+  return RBE_OK;
+}
+
+int copy_scalars(Ctx &c, double *energies, double *virial) {
+  RBE_CUDA_TRY(cudaMemcpyAsync(c.scal_host, c.scal, sizeof(double) * S_COUNT,
+                               cudaMemcpyDeviceToHost, c.stream));
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  const double *s = c.scal_host;
+  if (energies) {
+    energies[RBE_E_REAL] = s[S_UREAL];
+    energies[RBE_E_LJ] = s[S_ULJ];
+    energies[RBE_E_KSPACE] = s[S_UK];
+    energies[RBE_E_SELF] = s[S_USELF];
+    energies[RBE_E_TOTAL] = s[S_UTOT];
+    energies[RBE_E_KINETIC] = s[S_KE];
+  }
+  if (virial) {
+    virial[RBE_W_REAL] = s[S_WREAL];
+    virial[RBE_W_LJ] = s[S_WLJ];
+    virial[RBE_W_KSPACE] = s[S_WK];
+    virial[RBE_W_TOTAL] = s[S_WTOT];
+  }
+  return RBE_OK;
+}
+
+// Capture one Verlet step into a graph. Capture runs on an internal non-blocking stream
+// (the legacy default stream cannot be captured); the graph is replayed on c.stream.
+int capture_step_graph(Ctx &c, int parity, cudaGraphExec_t *out) {
+  if (!c.cap_stream) RBE_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+  const int saved = c.cur;
+  cudaStream_t user = c.stream;
+  c.cur = parity;
+  c.stream = c.cap_stream;
+  cudaGraph_t g = nullptr;
+  cudaError_t eb = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+  if (eb != cudaSuccess) {
+    c.stream = user;
+    c.cur = saved;
+    RBE_CUDA_TRY(eb);
+  }
+  int rc = RBE_OK;
+  do {
+    mark(c, RBE_PH_KICK_DRIFT);
+    if (launch_kick_drift(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+    if (launch_step_advance(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+    rc = force_pipeline(c, false);
+    if (rc != RBE_OK) break;
+    if (launch_kick(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+    if (launch_totals(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+    mark(c, RBE_N_PHASE);
+  } while (0);
+  cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+  c.cur = saved;
+  c.stream = user;
+  if (rc != RBE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  RBE_CUDA_TRY(e);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  RBE_CUDA_TRY(e);
+  return RBE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rbe_version(void) { return "rbe-gb300 1.0 (sm_103a)"; }
+
+const char *rbe_error_string(int code) {
+  switch (code) {
+    case RBE_OK: return "ok";
+    case RBE_ERR_INVALID: return "invalid argument";
+    case RBE_ERR_NONNEUTRAL: return "system is not charge neutral";
+    case RBE_ERR_CUTOFF: return "cutoff must be smaller than half of every box side";
+    case RBE_ERR_CELLS: return "box too small for the cell stencil at this cutoff";
+    case RBE_ERR_OOM: return "device allocation failed";
+    case RBE_ERR_CUDA: return "CUDA runtime error";
+    case RBE_ERR_SAMPLER: return "mode sampler drew k = 0 in 64 consecutive attempts";
+    case RBE_ERR_NONFINITE: return "non-finite or runaway position update";
+    case RBE_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown error";
+  }
+}
+
+int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[3],
+             const double *pos, const double *q, const int32_t *type, const double *mass,
+             const double *vel, void *cuda_stream) {
+  if (!hout) return RBE_ERR_INVALID;
+  *hout = nullptr;
+  if (!p || !box || N <= 0 || N >= ((int64_t)1 << 31) || !pos || !q) return RBE_ERR_INVALID;
+  if (!(p->alpha > 0) || !(p->r_c > 0) || p->P < 1 || p->P > (1 << 20)) return RBE_ERR_INVALID;
+  if (p->precision < RBE_FP32_COMP || p->precision > RBE_FP64) return RBE_ERR_INVALID;
+  if (p->n_types < 1 || p->n_types > kMaxTypes || !p->lj_eps || !p->lj_sigma) return RBE_ERR_INVALID;
+  if (!(p->coulomb_C >= 0) || !std::isfinite(p->coulomb_C)) return RBE_ERR_INVALID;
+  const bool rbl = p->r_core > 0;
+  if (rbl && (!(p->r_core < p->r_c) || p->p_rbl < 1 || p->p_rbl > 32)) return RBE_ERR_INVALID;
+  if (p->cell_sub < 0 || p->cell_sub > 3) return RBE_ERR_INVALID;
+  for (int d = 0; d < 3; ++d) {
+    if (!(box[d] > 0) || !std::isfinite(box[d])) return RBE_ERR_INVALID;
+    if (!(2.0 * p->r_c < box[d])) return RBE_ERR_CUTOFF;
+  }
+  double qsum = 0.0, qabs = 0.0, q2 = 0.0;
+  int64_t Nq = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    if (!std::isfinite(q[i])) return RBE_ERR_INVALID;
+    qsum += q[i];
+    qabs += std::fabs(q[i]);
+    q2 += q[i] * q[i];
+    if (q[i] != 0.0) ++Nq;
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(pos[3 * i + d])) return RBE_ERR_INVALID;
+    if (type && (type[i] < 0 || type[i] >= p->n_types)) return RBE_ERR_INVALID;
+    if (mass && !(mass[i] > 0)) return RBE_ERR_INVALID;
+  }
+  if (std::fabs(qsum) > 1e-9 * std::fmax(1.0, qabs)) return RBE_ERR_NONNEUTRAL;
+
+  rbe_ctx *h = new (std::nothrow) rbe_ctx();
+  if (!h) return RBE_ERR_OOM;
+  Ctx &c = *h;
+  c.N = N; c.Nq = Nq;
+  for (int d = 0; d < 3; ++d) c.box[d] = box[d];
+  c.V = box[0] * box[1] * box[2];
+  c.alpha = p->alpha; c.rc = p->r_c; c.r_core = rbl ? p->r_core : 0.0;
+  c.C = p->coulomb_C; c.dt = p->dt; c.kappa = p->kappa;
+  c.P = p->P; c.p_rbl = rbl ? p->p_rbl : 0; c.precision = p->precision;
+  c.nt = p->n_types; c.seed = p->seed; c.replica = p->replica; c.rbl = rbl;
+  c.stream = (cudaStream_t)cuda_stream;
+  c.sum_q2 = q2;
+  c.U_self = c.C * std::sqrt(c.alpha / kPi) * q2;
+
+  // cell grid
+  if (rbl) {
+    c.sub = 1;
+    for (int d = 0; d < 3; ++d) {
+      c.grid.n[d] = (int)std::floor(box[d] / c.rc);
+      c.grid.R[d] = 1;
+      if (c.grid.n[d] < 3) { delete h; return RBE_ERR_CELLS; }
+    }
+  } else {
+    int sub = p->cell_sub > 0 ? p->cell_sub : 2;
+    for (;; --sub) {
+      bool ok = true;
+      for (int d = 0; d < 3; ++d) {
+        c.grid.n[d] = (int)std::floor(box[d] * sub / c.rc);
+        const double a = box[d] / c.grid.n[d];
+        c.grid.R[d] = (int)std::ceil(c.rc / a);
+        if (c.grid.n[d] < 2 * c.grid.R[d] + 1) ok = false;
+      }
+      if (ok) break;
+      if (sub == 1) { delete h; return RBE_ERR_CELLS; }
+    }
+    c.sub = sub;
+  }
+  c.grid.ncell = (int64_t)c.grid.n[0] * c.grid.n[1] * c.grid.n[2];
+  if (c.grid.ncell >= ((int64_t)1 << 31) - 2) { delete h; return RBE_ERR_CELLS; }
+
+  // pair constants
+  for (int d = 0; d < 3; ++d) {
+    c.pc.hd[d] = box[d] / kTwo32;
+    c.pc.h[d] = (float)c.pc.hd[d];
+  }
+  const double rc2 = c.rc * c.rc;
+  c.pc.rc2d = rc2;
+  c.pc.rc2_lo = (float)(rc2 * (1.0 - 1e-5));
+  c.pc.rc2_hi = (float)(rc2 * (1.0 + 1e-5));
+  c.pc.alpha_d = c.alpha; c.pc.alpha = (float)c.alpha;
+  c.pc.sqrt_alpha_d = std::sqrt(c.alpha); c.pc.sqrt_alpha = (float)c.pc.sqrt_alpha_d;
+  c.pc.C_d = c.C; c.pc.C = (float)c.C;
+  c.pc.two_sqrt_alpha_over_sqrt_pi_d = 2.0 * std::sqrt(c.alpha) / std::sqrt(kPi);
+  c.pc.two_sqrt_alpha_over_sqrt_pi = (float)c.pc.two_sqrt_alpha_over_sqrt_pi_d;
+  // LJ table
+  c.lj.nt = c.nt;
+  for (int a = 0; a < c.nt; ++a)
+    for (int b = 0; b < c.nt; ++b) {
+      const int k = a * c.nt + b;
+      const double e = p->lj_eps[k], s = p->lj_sigma[k];
+      if (!(e >= 0) || !(s > 0) || p->lj_eps[b * c.nt + a] != e || p->lj_sigma[b * c.nt + a] != s) {
+        delete h;
+        return RBE_ERR_INVALID;
+      }
+      c.lj.eps24d[k] = 24.0 * e; c.lj.eps4d[k] = 4.0 * e; c.lj.sig2d[k] = s * s;
+      c.lj.eps24[k] = (float)(24.0 * e); c.lj.eps4[k] = (float)(4.0 * e); c.lj.sig2[k] = (float)(s * s);
+    }
+
+  // sampling tables
+  std::vector<uint64_t> T[3];
+  double Z[3];
+  for (int d = 0; d < 3; ++d) {
+    c.M[d] = axis_half_width(box[d], c.alpha);
+    axis_table(box[d], c.alpha, c.M[d], T[d], Z[d]);
+  }
+  c.S = Z[0] * Z[1] * Z[2] - 1.0;
+
+  // structure-factor launch shape: one thread per mode, particle tiles per block
+  c.sf_mb = std::min(256, ((c.P + 31) / 32) * 32);
+  c.sf_nblk_m = (c.P + c.sf_mb - 1) / c.sf_mb;
+  {
+    const int64_t target_blocks = 152 * 8;
+    int64_t tile = Nq * c.sf_nblk_m / std::max<int64_t>(1, target_blocks);
+    tile = std::max<int64_t>(32, std::min<int64_t>(512, ((tile + 31) / 32) * 32));
+    c.sf_tile = (int)tile;
+    c.sf_nblk_p = (int)std::max<int64_t>(1, (Nq + tile - 1) / tile);
+  }
+
+  // reductions layout
+  c.n_pair_blk = rbl ? 0 : pair_blocks(N);
+  c.n_coul_blk = rbl ? 0 : pair_blocks(Nq);
+  c.n_rbl_blk = rbl ? rbl_blocks(N) : 0;
+  c.n_ke_blk = (N + 255) / 256;
+  c.off_pair = 0;
+  c.off_coul = c.off_pair + c.n_pair_blk * NQ_PAIR;
+  c.off_rbl = c.off_coul + c.n_coul_blk * NQ_PAIR;
+  c.off_ke = c.off_rbl + c.n_rbl_blk * NQ_PAIR;
+  c.epart_slots = c.off_ke + c.n_ke_blk;
+  c.scan_nblk = (c.grid.ncell + 2047) / 2048;
+
+  // allocation
+  const bool fp64 = c.precision == RBE_FP64;
+  int rc = RBE_OK;
+  for (int b = 0; b < 2 && rc == RBE_OK; ++b) {
+    rc |= dalloc(c, &c.s[b], 3 * N);
+    if (fp64) rc |= dalloc(c, &c.vd[b], 3 * N);
+    else rc |= dalloc(c, &c.vf[b], 3 * N);
+    rc |= dalloc(c, &c.id[b], N);
+    rc |= dalloc(c, &c.qf[b], N);
+    if (fp64) rc |= dalloc(c, &c.qd[b], N);
+    if (c.nt > 1) rc |= dalloc(c, &c.type[b], N);
+    rc |= dalloc(c, &c.invm[b], N);
+  }
+  if (fp64) rc |= dalloc(c, &c.Fd, 3 * N);
+  else rc |= dalloc(c, &c.F, 3 * N);
+  rc |= dalloc(c, &c.cs, 3 * Nq);
+  rc |= dalloc(c, &c.cqf, Nq);
+  if (fp64) rc |= dalloc(c, &c.cqd, Nq);
+  rc |= dalloc(c, &c.cmap, Nq);
+  rc |= dalloc(c, &c.cell_count, 2 * c.grid.ncell);
+  rc |= dalloc(c, &c.cell_start, 2 * (c.grid.ncell + 1));
+  rc |= dalloc(c, &c.key, N);
+  rc |= dalloc(c, &c.off, N);
+  rc |= dalloc(c, &c.tmp, N);
+  rc |= dalloc(c, &c.scan_blk, 2 * c.scan_nblk);
+  for (int d = 0; d < 3; ++d) rc |= dalloc(c, &c.T[d], 2 * c.M[d] + 1);
+  rc |= dalloc(c, &c.m, c.P);
+  rc |= dalloc(c, &c.kcf, c.P);
+  rc |= dalloc(c, &c.kcd, c.P);
+  rc |= dalloc(c, &c.sf_part, (int64_t)c.sf_nblk_p * c.P * 2);
+  rc |= dalloc(c, &c.rho, c.P);
+  rc |= dalloc(c, &c.abf, c.P);
+  rc |= dalloc(c, &c.abd, c.P);
+  rc |= dalloc(c, &c.emode, 2 * c.P);
+  rc |= dalloc(c, &c.epart, c.epart_slots);
+  rc |= dalloc(c, &c.scal, S_COUNT);
+  rc |= dalloc(c, &c.step_dev, 1);
+  rc |= dalloc(c, &c.err, 1);
+  rc |= dalloc(c, &c.nbr, N);
+  if (rbl) {
+    rc |= dalloc(c, &c.nshell, N);
+    rc |= dalloc(c, &c.partners, N * c.p_rbl);
+    rc |= dalloc(c, &c.rbl_part, c.n_rbl_blk * 3);
+  }
+  rc |= dalloc(c, &c.rbl_mean, 3);
+  rc |= dalloc(c, &c.outf, 3 * N);
+  rc |= dalloc(c, &c.outd, 3 * N);
+  rc |= dalloc(c, &c.pos_stage, 3 * N);
+  rc |= dalloc(c, &c.lj_dev, (int64_t)sizeof(LJTable));
+  if (rc != RBE_OK) {
+    free_all(c);
+    delete h;
+    return RBE_ERR_OOM;
+  }
+  if (cudaMallocHost((void **)&c.scal_host, sizeof(double) * S_COUNT) != cudaSuccess) {
+    cudaGetLastError();
+    free_all(c);
+    delete h;
+    return RBE_ERR_OOM;
+  }
+  c.cell_start += 0;
+  c.ccell_start = c.cell_start + (c.grid.ncell + 1);
+  c.ccell_count = c.cell_count + c.grid.ncell;
+
+  // initial state (identity order), uploaded once
+  {
+    std::vector<uint32_t> s(3 * N);
+    std::vector<int32_t> ids(N), ty;
+    std::vector<float> qf(N), im(N), vf;
+    std::vector<double> vd;
+    for (int64_t i = 0; i < N; ++i) {
+      for (int d = 0; d < 3; ++d) s[d * N + i] = quantise(pos[3 * i + d], box[d]);
+      ids[i] = (int32_t)i;
+      qf[i] = (float)q[i];
+      im[i] = (float)(1.0 / (mass ? mass[i] : 1.0));
+    }
+    int e = 0;
+    e |= cudaMemcpy(c.s[0], s.data(), sizeof(uint32_t) * 3 * N, cudaMemcpyHostToDevice);
+    e |= cudaMemcpy(c.id[0], ids.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice);
+    e |= cudaMemcpy(c.qf[0], qf.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    e |= cudaMemcpy(c.invm[0], im.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    if (fp64) e |= cudaMemcpy(c.qd[0], q, sizeof(double) * N, cudaMemcpyHostToDevice);
+    if (c.nt > 1) {
+      ty.assign(N, 0);
+      if (type) for (int64_t i = 0; i < N; ++i) ty[i] = type[i];
+      e |= cudaMemcpy(c.type[0], ty.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice);
+    }
+    if (fp64) {
+      vd.assign(3 * N, 0.0);
+      if (vel) for (int64_t i = 0; i < N; ++i) for (int d = 0; d < 3; ++d) vd[d * N + i] = vel[3 * i + d];
+      e |= cudaMemcpy(c.vd[0], vd.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice);
+    } else {
+      vf.assign(3 * N, 0.f);
+      if (vel) for (int64_t i = 0; i < N; ++i) for (int d = 0; d < 3; ++d) vf[d * N + i] = (float)vel[3 * i + d];
+      e |= cudaMemcpy(c.vf[0], vf.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice);
+    }
+    for (int d = 0; d < 3; ++d)
+      e |= cudaMemcpy(c.T[d], T[d].data(), sizeof(uint64_t) * T[d].size(), cudaMemcpyHostToDevice);
+    e |= cudaMemcpy(c.lj_dev, &c.lj, sizeof(LJTable), cudaMemcpyHostToDevice);
+    e |= cudaMemset(c.epart, 0, sizeof(double) * c.epart_slots);
+    e |= cudaMemset(c.emode, 0, sizeof(double) * 2 * c.P);
+    e |= cudaMemset(c.err, 0, sizeof(int));
+    e |= cudaMemset(c.step_dev, 0, sizeof(uint64_t));
+    e |= cudaMemset(c.scal, 0, sizeof(double) * S_COUNT);
+    if (e != 0) {
+      cudaGetLastError();
+      free_all(c);
+      delete h;
+      return RBE_ERR_CUDA;
+    }
+  }
+  *hout = h;
+  return RBE_OK;
+}
+
+int rbe_destroy(rbe_handle h) {
+  if (!h) return RBE_OK;
+  cudaStreamSynchronize(h->stream);
+  free_all(*h);
+  delete h;
+  return RBE_OK;
+}
+
+int rbe_sample_k(rbe_handle h, uint64_t step, int32_t *m_out, double *S_out) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  RBE_CUDA_TRY(launch_set_step(c, step));
+  RBE_CUDA_TRY(launch_sample_k(c));
+  c.have_forces = false;
+  if (m_out) {
+    std::vector<int4> mm(c.P);
+    RBE_CUDA_TRY(cudaMemcpyAsync(mm.data(), c.m, sizeof(int4) * c.P, cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    for (int l = 0; l < c.P; ++l) {
+      m_out[3 * l] = mm[l].x; m_out[3 * l + 1] = mm[l].y; m_out[3 * l + 2] = mm[l].z;
+    }
+  }
+  if (S_out) *S_out = c.S;
+  return read_device_flags(c);
+}
+
+int rbe_set_positions(rbe_handle h, const double *pos, int on_device) {
+  if (!h || !pos) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  RBE_CUDA_TRY(cudaMemcpyAsync(c.pos_stage, pos, sizeof(double) * 3 * c.N,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               c.stream));
+  RBE_CUDA_TRY(launch_set_positions(c));
+  c.have_forces = false;
+  return RBE_OK;
+}
+
+static int forces_common(rbe_handle h, uint64_t step, bool debug) {
+  Ctx &c = *h;
+  RBE_CUDA_TRY(launch_set_step(c, step));
+  mark(c, RBE_PH_KICK_DRIFT);
+  int rc = force_pipeline(c, debug);
+  if (rc != RBE_OK) return rc;
+  RBE_CUDA_TRY(launch_kinetic(c));
+  RBE_CUDA_TRY(launch_totals(c));
+  mark(c, RBE_N_PHASE);
+  c.have_forces = (step == c.step);
+  return RBE_OK;
+}
+
+int rbe_forces(rbe_handle h, uint64_t step, float *F_out, int F_on_device, double *energies,
+               double *virial) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  int rc = forces_common(h, step, true);
+  if (rc != RBE_OK) return rc;
+  if (F_out) {
+    RBE_CUDA_TRY(launch_scatter_forces(c, false));
+    RBE_CUDA_TRY(cudaMemcpyAsync(F_out, c.outf, sizeof(float) * 3 * c.N,
+                                 F_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c.stream));
+  }
+  if (energies || virial) {
+    rc = copy_scalars(c, energies, virial);
+    if (rc != RBE_OK) return rc;
+  }
+  if ((F_out && !F_on_device) || energies || virial) return read_device_flags(c);
+  return RBE_OK;
+}
+
+int rbe_forces_f64(rbe_handle h, uint64_t step, double *F_out, double *energies, double *virial) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  int rc = forces_common(h, step, true);
+  if (rc != RBE_OK) return rc;
+  if (F_out) {
+    RBE_CUDA_TRY(launch_scatter_forces(c, true));
+    RBE_CUDA_TRY(cudaMemcpyAsync(F_out, c.outd, sizeof(double) * 3 * c.N, cudaMemcpyDeviceToHost,
+                                 c.stream));
+  }
+  rc = copy_scalars(c, energies, virial);
+  if (rc != RBE_OK) return rc;
+  return read_device_flags(c);
+}
+
+int rbe_step(rbe_handle h, int nsteps) {
+  if (!h || nsteps < 0) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  if (nsteps == 0) return RBE_OK;
+  if (!c.have_forces) {
+    int rc = forces_common(h, c.step, false);
+    if (rc != RBE_OK) return rc;
+  }
+  for (int b = 0; b < 2; ++b)
+    if (!c.graph[b]) {
+      int rc = capture_step_graph(c, b, &c.graph[b]);
+      if (rc != RBE_OK) return rc;
+    }
+  for (int k = 0; k < nsteps; ++k) {
+    RBE_CUDA_TRY(cudaGraphLaunch(c.graph[c.cur], c.stream));
+    c.cur = 1 - c.cur;
+    c.step += 1;
+  }
+  c.have_forces = true;
+  return RBE_OK;
+}
+
+int rbe_get_step(rbe_handle h, uint64_t *step) {
+  if (!h || !step) return RBE_ERR_INVALID;
+  *step = h->step;
+  return RBE_OK;
+}
+
+int rbe_get_energies(rbe_handle h, double *energies, double *virial) {
+  if (!h) return RBE_ERR_INVALID;
+  return copy_scalars(*h, energies, virial);
+}
+
+int rbe_get_state(rbe_handle h, double *pos, double *vel, uint32_t *s_frac) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  if (pos) {
+    RBE_CUDA_TRY(launch_scatter_state(c, 0));
+    RBE_CUDA_TRY(cudaMemcpyAsync(pos, c.outd, sizeof(double) * 3 * c.N, cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  }
+  if (vel) {
+    RBE_CUDA_TRY(launch_scatter_state(c, 1));
+    RBE_CUDA_TRY(cudaMemcpyAsync(vel, c.outd, sizeof(double) * 3 * c.N, cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  }
+  if (s_frac) {
+    RBE_CUDA_TRY(launch_scatter_state(c, 2));
+    RBE_CUDA_TRY(cudaMemcpyAsync(s_frac, c.outf, sizeof(uint32_t) * 3 * c.N, cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  }
+  return read_device_flags(c);
+}
+
+int rbe_get_cells(rbe_handle h, int32_t n_cells[3], int64_t *cell_start, int64_t *sorted_ids) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  if (n_cells) for (int d = 0; d < 3; ++d) n_cells[d] = c.grid.n[d];
+  if (cell_start) {
+    std::vector<int32_t> cs(c.grid.ncell + 1);
+    RBE_CUDA_TRY(cudaMemcpyAsync(cs.data(), c.cell_start, sizeof(int32_t) * cs.size(),
+                                 cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    for (size_t k = 0; k < cs.size(); ++k) cell_start[k] = cs[k];
+  }
+  if (sorted_ids) {
+    std::vector<int32_t> ids(c.N);
+    RBE_CUDA_TRY(cudaMemcpyAsync(ids.data(), c.id[c.cur], sizeof(int32_t) * c.N,
+                                 cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    for (int64_t k = 0; k < c.N; ++k) sorted_ids[k] = ids[k];
+  }
+  return RBE_OK;
+}
+
+int rbe_get_rho(rbe_handle h, double *rho, int32_t *m_out) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  if (rho) {
+    RBE_CUDA_TRY(cudaMemcpyAsync(rho, c.rho, sizeof(double2) * c.P, cudaMemcpyDeviceToHost, c.stream));
+  }
+  if (m_out) {
+    std::vector<int4> mm(c.P);
+    RBE_CUDA_TRY(cudaMemcpyAsync(mm.data(), c.m, sizeof(int4) * c.P, cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    for (int l = 0; l < c.P; ++l) {
+      m_out[3 * l] = mm[l].x; m_out[3 * l + 1] = mm[l].y; m_out[3 * l + 2] = mm[l].z;
+    }
+  }
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  return RBE_OK;
+}
+
+int rbe_get_neighbor_counts(rbe_handle h, int32_t *n_core, int32_t *n_shell) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  int32_t *dst = reinterpret_cast<int32_t *>(c.outf);
+  if (n_core) {
+    RBE_CUDA_TRY(launch_scatter_int(c, c.nbr, dst, 1));
+    RBE_CUDA_TRY(cudaMemcpyAsync(n_core, dst, sizeof(int32_t) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  }
+  if (n_shell) {
+    if (c.rbl) {
+      RBE_CUDA_TRY(launch_scatter_int(c, c.nshell, dst, 1));
+      RBE_CUDA_TRY(cudaMemcpyAsync(n_shell, dst, sizeof(int32_t) * c.N, cudaMemcpyDeviceToHost, c.stream));
+      RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    } else {
+      memset(n_shell, 0, sizeof(int32_t) * c.N);
+    }
+  }
+  return RBE_OK;
+}
+
+int rbe_get_rbl_partners(rbe_handle h, int32_t *partners) {
+  if (!h || !partners) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  if (!c.rbl) return RBE_ERR_STATE;
+  std::vector<int32_t> srt((size_t)c.N * c.p_rbl), ids(c.N);
+  RBE_CUDA_TRY(cudaMemcpyAsync(srt.data(), c.partners, sizeof(int32_t) * srt.size(),
+                               cudaMemcpyDeviceToHost, c.stream));
+  RBE_CUDA_TRY(cudaMemcpyAsync(ids.data(), c.id[c.cur], sizeof(int32_t) * c.N,
+                               cudaMemcpyDeviceToHost, c.stream));
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  for (int64_t k = 0; k < c.N; ++k)
+    memcpy(partners + (size_t)ids[k] * c.p_rbl, srt.data() + (size_t)k * c.p_rbl,
+           sizeof(int32_t) * c.p_rbl);
+  return RBE_OK;
+}
+
+int rbe_set_profiling(rbe_handle h, int enable) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  const bool on = enable != 0;
+  if (on == c.timing) return RBE_OK;
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  for (int b = 0; b < 2; ++b)
+    if (c.graph[b]) {
+      cudaGraphExecDestroy(c.graph[b]);
+      c.graph[b] = nullptr;
+    }
+  if (on)
+    for (int k = 0; k <= RBE_N_PHASE; ++k)
+      if (!c.ev[k]) RBE_CUDA_TRY(cudaEventCreate(&c.ev[k]));
+  c.timing = on;
+  return RBE_OK;
+}
+
+int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kps) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  if (kps) *kps = kernels_per_step(c);
+  if (phase_ms) {
+    if (!c.timing) return RBE_ERR_STATE;
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    for (int k = 0; k < RBE_N_PHASE; ++k) {
+      float ms = 0.f;
+      // a phase that was not recorded in the last run (e.g. no kick-drift in rbe_forces)
+      // reads as zero
+      if (c.ev_used[k] && c.ev_used[k + 1]) {
+        if (cudaEventElapsedTime(&ms, c.ev[k], c.ev[k + 1]) != cudaSuccess) {
+          cudaGetLastError();
+          ms = 0.f;
+        }
+      }
+      phase_ms[k] = ms;
+    }
+  }
+  return RBE_OK;
+}
+
+int rbe_get_memory(rbe_handle h, int64_t *bytes) {
+  if (!h || !bytes) return RBE_ERR_INVALID;
+  *bytes = h->bytes;
+  return RBE_OK;
+}
+
+int rbe_check_device(rbe_handle h) {
+  if (!h) return RBE_ERR_INVALID;
+  return read_device_flags(*h);
+}
+
+}  // extern "C"

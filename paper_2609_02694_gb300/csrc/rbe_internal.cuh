@@ -1,0 +1,226 @@
+// rbe_internal.cuh -- device state, helpers and kernel launchers of the RBE force path.
+//
+// Data layout in HBM (all particle arrays in cell-sorted order, structure of arrays):
+//   s[b]      uint32 x 3N   fractional coordinates s_d = r_d / L_d * 2^32 (x block, y, z)
+//   vf/vd[b]  velocities (float, or double in the FP64 form), 3N
+//   id[b]     int32 N       caller id of the particle at each sorted slot
+//   qf/qd[b]  charge (float; double copy in the FP64 form)
+//   type[b]   int32 N       LJ type (only when n_types > 1)
+//   invm[b]   float N       inverse mass
+//   F / Fd    forces in sorted order, 3N
+// b in {0,1}: the cell sort writes the other buffer and flips `cur`.
+// The charged subset (q != 0) is kept in the same cell order in its own arrays
+// (cs, cqf/cqd, cmap: charged slot -> full sorted slot, ccell_start).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rbe.h"
+
+namespace rbe {
+
+constexpr double kTwo32 = 4294967296.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxTypes = 16;
+
+// Device error bits (OR-ed into ctx.err).
+enum : int { ERRBIT_SAMPLER = 1, ERRBIT_NONFINITE = 2 };
+
+// Partial-sum slots (doubles per block) of the energy / virial reductions.
+enum : int { Q_UREAL = 0, Q_ULJ = 1, Q_WREAL = 2, Q_WLJ = 3, NQ_PAIR = 4 };
+
+struct Grid {
+  int n[3];       // cells per axis
+  int R[3];       // stencil half-width in cells per axis
+  int64_t ncell;
+};
+
+struct PairSet {        // one cell-sorted particle set seen by the pair kernels
+  const uint32_t *sx, *sy, *sz;
+  const float *qf;
+  const double *qd;
+  const int32_t *type;  // nullptr: single type
+  const int32_t *cell_start;
+  const int32_t *map;   // output slot of each particle (nullptr: identity)
+  int64_t n;
+};
+
+struct LJTable {
+  float eps24[kMaxTypes * kMaxTypes];   // 24 eps_ij
+  float eps4[kMaxTypes * kMaxTypes];    // 4 eps_ij
+  float sig2[kMaxTypes * kMaxTypes];    // sigma_ij^2
+  double eps24d[kMaxTypes * kMaxTypes];
+  double eps4d[kMaxTypes * kMaxTypes];
+  double sig2d[kMaxTypes * kMaxTypes];
+  int nt;
+};
+
+struct PairConst {
+  float h[3];            // L_d / 2^32 (float)
+  double hd[3];          // L_d / 2^32 (double)
+  float rc2_lo, rc2_hi;  // r_c^2 (1 -/+ 1e-5): outside this band FP32 decides
+  double rc2d;           // r_c^2, the exact decision inside the band
+  float sqrt_alpha, alpha, C;   // Coulomb
+  double sqrt_alpha_d, alpha_d, C_d;
+  float two_sqrt_alpha_over_sqrt_pi;
+  double two_sqrt_alpha_over_sqrt_pi_d;
+};
+
+struct Ctx {
+  // --- parameters
+  int64_t N = 0, Nq = 0;
+  double box[3] = {0, 0, 0};
+  double alpha = 0, rc = 0, r_core = 0, C = 0, dt = 0, kappa = 0;
+  int P = 0, p_rbl = 0, precision = RBE_FP32_COMP, nt = 1, sub = 2;
+  uint64_t seed = 0;
+  uint32_t replica = 0;
+  bool rbl = false;
+  double sum_q2 = 0, U_self = 0, S = 0, V = 0;
+  cudaStream_t stream = nullptr;
+  Grid grid{};
+  LJTable lj{};
+  void *lj_dev = nullptr;     // device copy of lj (multi-type pair kernels)
+  PairConst pc{};
+  // --- particle arrays
+  int cur = 0;
+  uint32_t *s[2] = {nullptr, nullptr};
+  float *vf[2] = {nullptr, nullptr};
+  double *vd[2] = {nullptr, nullptr};
+  int32_t *id[2] = {nullptr, nullptr};
+  float *qf[2] = {nullptr, nullptr};
+  double *qd[2] = {nullptr, nullptr};
+  int32_t *type[2] = {nullptr, nullptr};
+  float *invm[2] = {nullptr, nullptr};
+  float *F = nullptr;
+  double *Fd = nullptr;
+  // charged subset
+  uint32_t *cs = nullptr;
+  float *cqf = nullptr;
+  double *cqd = nullptr;
+  int32_t *cmap = nullptr;
+  // cells
+  int32_t *cell_count = nullptr, *ccell_count = nullptr;   // ncell each (contiguous pair)
+  int32_t *cell_start = nullptr, *ccell_start = nullptr;   // ncell + 1 each
+  int32_t *key = nullptr, *off = nullptr, *tmp = nullptr;  // N each
+  int32_t *scan_blk = nullptr;                              // 2 x scan blocks
+  int64_t scan_nblk = 0;
+  // k-space
+  uint64_t *T[3] = {nullptr, nullptr, nullptr};
+  int M[3] = {0, 0, 0};
+  int4 *m = nullptr;
+  float4 *kcf = nullptr;     // (kx, ky, kz, c_l)
+  double4 *kcd = nullptr;
+  double *sf_part = nullptr; // sf blocks x P x 2
+  int sf_tile = 256, sf_mb = 128, sf_nblk_p = 0, sf_nblk_m = 0;
+  double2 *rho = nullptr;
+  float2 *abf = nullptr;     // (c Im rho, c Re rho)
+  double2 *abd = nullptr;
+  double *emode = nullptr;   // per-mode (E_l, W_l) pairs: 2P
+  // reductions
+  double *epart = nullptr;   // partial slots
+  int64_t epart_slots = 0;
+  int64_t off_pair = 0, off_coul = 0, off_rbl = 0, off_ke = 0, n_pair_blk = 0,
+          n_coul_blk = 0, n_rbl_blk = 0, n_ke_blk = 0;
+  double *scal = nullptr;    // device scalars (see integrate kernels)
+  double *scal_host = nullptr;  // pinned
+  uint64_t *step_dev = nullptr;
+  uint64_t step = 0;
+  int *err = nullptr;
+  // debug / outputs
+  int32_t *nbr = nullptr;      // sorted order
+  int32_t *nshell = nullptr;   // sorted order
+  int32_t *partners = nullptr; // sorted order, N x p (ids)
+  double *rbl_mean = nullptr;  // 3 doubles: mean short-range force
+  double *rbl_part = nullptr;  // RBL blocks x 3
+  float *outf = nullptr;       // 3N id-order staging
+  double *outd = nullptr;      // 3N id-order staging (FP64 outputs, positions)
+  float *out_host = nullptr;   // pinned
+  double *pos_stage = nullptr; // 3N doubles (set_positions)
+  bool have_forces = false;
+  // graph
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per starting buffer parity
+  cudaStream_t cap_stream = nullptr;  // internal non-blocking stream used only for capture
+  // profiling: ev[k] is recorded before phase k, ev[RBE_N_PHASE] after the last one
+  bool timing = false;
+  cudaEvent_t ev[RBE_N_PHASE + 1] = {};
+  bool ev_used[RBE_N_PHASE + 1] = {};
+  int64_t bytes = 0;
+};
+
+// ---------------------------------------------------------------------------------------
+// Device helpers
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): two 32x32 products per round,
+// multipliers 0xD2511F53 / 0xCD9E8D57, key Weyl increments 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Cell index along one axis: floor(s * n / 2^32), exact.
+__device__ __forceinline__ int cell_of(uint32_t s, int n) {
+  return (int)(((uint64_t)s * (uint64_t)n) >> 32);
+}
+
+// Phase of exp(i k.r) in turns as a 32-bit fraction: k.r / 2 pi = sum_d m_d s_d / 2^32 (mod 1).
+__device__ __forceinline__ uint32_t phase_u32(int4 m, uint32_t sx, uint32_t sy, uint32_t sz) {
+  return (uint32_t)m.x * sx + (uint32_t)m.y * sy + (uint32_t)m.z * sz;
+}
+
+// Angle in radians in [-pi, pi) of a 32-bit phase, rounded to 2^-23 turns. The rounded
+// 23-bit signed value converts to float exactly through the 1.5 * 2^23 bias.
+__device__ __forceinline__ float phase_to_radians(uint32_t ph) {
+  const int v = ((int)(ph + 256u)) >> 9;  // |v| <= 2^22
+  const float f = __int_as_float(0x4B400000 + v) - 12582912.0f;
+  return f * (float)(2.0 * kPi / 8388608.0);
+}
+
+__device__ __forceinline__ double phase_to_radians_d(uint32_t ph) {
+  return (double)(int)ph * (2.0 * kPi / kTwo32);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------
+// Launchers (each in its own translation unit). All return cudaGetLastError().
+
+cudaError_t launch_sample_k(Ctx &c);
+cudaError_t launch_bin_sort(Ctx &c);
+cudaError_t launch_structure_factor(Ctx &c);
+cudaError_t launch_kspace_gather(Ctx &c);
+cudaError_t launch_pair(Ctx &c, bool want_counts);   // main pass, then mark, then Coulomb pass
+void mark(Ctx &c, int k);  // record the profiling event k (no-op when profiling is off)
+cudaError_t launch_rbl(Ctx &c, bool want_debug);
+cudaError_t launch_kick_drift(Ctx &c);
+cudaError_t launch_kick(Ctx &c);
+cudaError_t launch_kinetic(Ctx &c);
+cudaError_t launch_totals(Ctx &c);
+cudaError_t launch_set_step(Ctx &c, uint64_t step);
+cudaError_t launch_step_advance(Ctx &c);
+cudaError_t launch_scatter_forces(Ctx &c, bool to_double);
+cudaError_t launch_scatter_state(Ctx &c, int what);  // 0: positions, 1: velocities, 2: s
+cudaError_t launch_set_positions(Ctx &c);
+cudaError_t launch_scatter_int(Ctx &c, const int32_t *src_sorted, int32_t *dst_id, int width);
+
+// Scalars in Ctx::scal (device doubles).
+enum : int {
+  S_UREAL = 0, S_ULJ, S_UK, S_USELF, S_UTOT, S_KE, S_WREAL, S_WLJ, S_WK, S_WTOT, S_COUNT
+};
+
+}  // namespace rbe

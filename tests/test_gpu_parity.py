@@ -1,0 +1,316 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Integer results (mode sets, cells and their order, neighbour and RBL set sizes, RBL
+draws) must match bit for bit. Forces must match within 1e-5 relative L2 in the FP32
+forms on the same sampled mode set (FP64 form: 1e-10), and energies and virials within
+the tolerances stated beside each check. Inputs come from the seeded generator; the
+oracle never sees the GPU's output.
+"""
+import numpy as np
+import pytest
+
+from paper_2609_02694_gb300 import binding, build, synth
+
+pytestmark = pytest.mark.gpu
+
+C = synth.COULOMB_C
+ALPHA = synth.ALPHA
+RC = synth.R_CUT
+TOL_F32 = 1e-5
+TOL_F64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    binding.lib()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def handle(sy, P, precision="fp32_comp", **kw):
+    return binding.from_system(sy, P=P, alpha=kw.pop("alpha", ALPHA), r_c=kw.pop("r_c", RC),
+                               precision=precision, coulomb_C=C, **kw)
+
+
+def oracle_all(orc, sy, m, S, alpha=ALPHA, rc=RC):
+    return orc.total_forces(sy.s, sy.q, sy.types, sy.box, alpha, rc, C, sy.eps, sy.sig, m, S)
+
+
+# -------------------------------------------------------------------------- sampler
+
+
+@pytest.mark.parametrize("box,P,seed,step", [
+    ((32.0, 32.0, 32.0), 100, 1, 0),
+    ((32.0, 32.0, 32.0), 2000, 7, 123456),
+    ((218.877, 218.877, 218.877), 1000, 2, 3),
+    ((25.3, 31.0, 47.9), 333, 2 ** 40 + 5, 2 ** 32 + 9),
+])
+def test_kset_bit_exact(orc, box, P, seed, step):
+    sy = synth.make_system(64, L=min(box), seed=5)
+    sy.box = np.array(box)
+    with handle(sy, P, seed=seed, r_c=min(10.0, min(box) / 3 - 0.1)) as h:
+        m, S = h.sample_k(step)
+    mo, So = orc.sample_k(seed, step, 0, np.array(box), ALPHA, P)
+    assert np.array_equal(m, mo)
+    assert S == So
+
+
+# -------------------------------------------------------------------------- cells
+
+
+@pytest.mark.parametrize("N,L,sub", [(3000, 32.0, 0), (20000, 58.48, 2), (20000, 58.48, 1),
+                                     (5000, 40.0, 3)])
+def test_cells_bit_exact(orc, N, L, sub):
+    sy = synth.make_system(N, L=L, frac_charged=0.1, seed=11)
+    with handle(sy, 50, cell_sub=sub) as h:
+        h.forces(0)
+        n, cs, ids = h.cells()
+    _, cso, idso = orc.cells(sy.s, n)
+    assert np.array_equal(cs, cso)
+    assert np.array_equal(ids, idso)
+
+
+# -------------------------------------------------------------------------- k-space
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32_comp", 2e-6), ("fp32", 2e-5), ("fp64", 1e-12)])
+def test_structure_factor(orc, precision, tol):
+    sy = synth.make_system(20000, density=0.1, frac_charged=0.1, seed=12)
+    with handle(sy, 200, precision=precision) as h:
+        h.forces(0)
+        rho, m = h.rho()
+    ro = orc.rho(sy.s, sy.q, sy.box, m)
+    assert rel_l2(rho, ro) < tol
+
+
+# -------------------------------------------------------------------------- forces
+
+
+CASES = [
+    # name, system kwargs, P, extra handle kwargs
+    ("n3000_all_charged", dict(N=3000, L=32.0, all_charged=True, seed=1), 100, {}),
+    ("n20k_10pct", dict(N=20000, density=0.1, frac_charged=0.1, seed=2), 200, {}),
+    ("n20k_10pct_sub1", dict(N=20000, density=0.1, frac_charged=0.1, seed=2), 200,
+     dict(cell_sub=1)),
+    ("n7777_ragged", dict(N=7777, density=0.08, frac_charged=0.3, seed=9), 57, {}),
+]
+
+
+@pytest.mark.parametrize("name,skw,P,hkw", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", ["fp32_comp", "fp64"])
+def test_forces_match_oracle(orc, name, skw, P, hkw, precision):
+    sy = synth.make_system(**skw)
+    with handle(sy, P, precision=precision, **hkw) as h:
+        F, E, W = h.forces_f64(0)
+        m, S = h.sample_k(0)
+        nbr, _ = h.neighbor_counts()
+    ref = oracle_all(orc, sy, m, S)
+    tol = TOL_F64 if precision == "fp64" else TOL_F32
+    assert rel_l2(F, ref["F"]) < tol
+    assert np.array_equal(nbr, ref["nbr"])
+    etol = 1e-10 if precision == "fp64" else 2e-6
+    assert E["real"] == pytest.approx(ref["U_real"], rel=etol, abs=1e-6)
+    assert E["lj"] == pytest.approx(ref["U_lj"], rel=etol)
+    assert E["kspace"] == pytest.approx(ref["U_k"], rel=etol)
+    assert E["self"] == pytest.approx(ref["U_self"], rel=1e-12)
+    assert W["real"] == pytest.approx(ref["W_real"], rel=etol, abs=1e-6)
+    assert W["lj"] == pytest.approx(ref["W_lj"], rel=etol)
+    assert W["kspace"] == pytest.approx(ref["W_k"], rel=etol)
+
+
+def test_orthorhombic_two_types(orc):
+    rng = np.random.default_rng(4)
+    sy = synth.make_system(6000, L=40.0, frac_charged=0.2, seed=4)
+    sy.box = np.array([40.0, 45.0, 52.0])
+    sy.types = (rng.uniform(size=sy.n) < 0.3).astype(np.int32)
+    sy.eps = np.array([0.1, 0.15, 0.15, 0.2])
+    sy.sig = np.array([3.0, 2.8, 2.8, 2.6])
+    with handle(sy, 150) as h:
+        F, E, W = h.forces_f64(4)
+        m, S = h.sample_k(4)
+        nbr, _ = h.neighbor_counts()
+    ref = oracle_all(orc, sy, m, S)
+    assert rel_l2(F, ref["F"]) < TOL_F32
+    assert np.array_equal(nbr, ref["nbr"])
+    assert E["lj"] == pytest.approx(ref["U_lj"], rel=2e-6)
+
+
+def test_plain_fp32_is_worse_than_compensated(orc):
+    sy = synth.make_system(40000, density=0.1, frac_charged=0.1, seed=21)
+    errs = {}
+    for prec in ("fp32", "fp32_comp"):
+        with handle(sy, 400, precision=prec) as h:
+            h.forces(0)
+            rho, m = h.rho()
+        errs[prec] = rel_l2(rho, orc.rho(sy.s, sy.q, sy.box, m))
+    assert errs["fp32_comp"] < errs["fp32"]
+
+
+def test_no_charges_and_single_mode(orc):
+    sy = synth.make_system(3000, density=0.1, frac_charged=0.0, seed=3)
+    with handle(sy, 1) as h:
+        F, E, W = h.forces_f64(0)
+    ref = orc.real_space(sy.s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig)
+    assert rel_l2(F, ref["F"]) < TOL_F32
+    assert E["kspace"] == 0.0 and E["real"] == 0.0
+
+
+def test_tiny_box_edge(orc):
+    """Smallest box the stencil allows (5 cells of r_c/2 per axis) with a few particles."""
+    sy = synth.make_system(12, L=25.1, all_charged=True, seed=8)
+    with handle(sy, 16) as h:
+        F, E, W = h.forces_f64(2)
+        m, S = h.sample_k(2)
+        nbr, _ = h.neighbor_counts()
+    ref = oracle_all(orc, sy, m, S)
+    assert rel_l2(F, ref["F"]) < TOL_F32
+    assert np.array_equal(nbr, ref["nbr"])
+
+
+def test_deterministic_across_runs():
+    sy = synth.make_system(20000, density=0.1, frac_charged=0.1, seed=2)
+    out = []
+    for _ in range(2):
+        with handle(sy, 200) as h:
+            F, E, W = h.forces_f64(5)
+            out.append((F, E["total"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_rbe_net_force_zero_on_gpu():
+    sy = synth.make_system(20000, density=0.1, frac_charged=0.1, seed=2)
+    with handle(sy, 200, precision="fp64") as h:
+        F, _, _ = h.forces_f64(0)
+    # total force: real space obeys Newton 3, RBE k-space sums to zero (Eq. F_long_RBE)
+    assert np.abs(F.sum(axis=0)).max() < 1e-9 * np.abs(F).sum()
+
+
+def test_invalid_input_rejected():
+    sy = synth.make_system(100, L=30.0, all_charged=True, seed=1)
+    q = sy.q.copy()
+    q[0] += 0.5
+    with pytest.raises(binding.RBEError):
+        binding.RBE(sy.box, sy.positions(), q, alpha=ALPHA, r_c=RC, P=10, eps=sy.eps,
+                    sigma=sy.sig)
+    with pytest.raises(binding.RBEError):
+        binding.RBE(sy.box, sy.positions(), sy.q, alpha=ALPHA, r_c=15.5, P=10, eps=sy.eps,
+                    sigma=sy.sig)
+
+
+# -------------------------------------------------------------------------- RBL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32_comp", TOL_F32), ("fp64", TOL_F64)])
+def test_rbl_bit_exact_sets_and_draws(orc, precision, tol):
+    sy = synth.make_system(12000, density=0.1, frac_charged=0.05, seed=5)
+    p, r_core, seed, step = 10, 5.0, 3, 7
+    with handle(sy, 100, precision=precision, r_core=r_core, p_rbl=p, seed=seed) as h:
+        F, E, W = h.forces_f64(step)
+        nc, ns = h.neighbor_counts()
+        partners = h.rbl_partners()
+        m, S = h.sample_k(step)
+    ref = orc.rbl(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, RC, p, seed, step, 0, C,
+                  sy.eps, sy.sig)
+    assert np.array_equal(nc, ref["n_core"])
+    assert np.array_equal(ns, ref["n_shell"])
+    assert np.array_equal(partners, ref["partners"])
+    Fk, Uk, Wk = orc.rbe_kspace(sy.s, sy.q, sy.box, ALPHA, C, m, S)
+    assert rel_l2(F, ref["F"] + Fk) < tol
+    etol = 1e-10 if precision == "fp64" else 2e-6
+    assert E["lj"] == pytest.approx(ref["U_lj"], rel=etol)
+    assert E["real"] == pytest.approx(ref["U_real"], rel=etol, abs=1e-6)
+
+
+def test_rbl_small_shell_takes_all(orc):
+    """p >= #S_i: every shell partner enters with weight 1 (exact cutoff sum)."""
+    sy = synth.make_system(4000, density=0.1, frac_charged=0.1, seed=6)
+    with handle(sy, 50, r_core=8.0, p_rbl=32, r_c=8.1) as h:
+        F, E, W = h.forces_f64(0)
+        m, S = h.sample_k(0)
+    ex = oracle_all(orc, sy, m, S, rc=8.1)
+    assert rel_l2(F, ex["F"]) < TOL_F32
+
+
+# -------------------------------------------------------------------------- Verlet
+
+
+def test_verlet_one_step_matches_oracle(orc):
+    sy = synth.make_system(3000, L=32.0, all_charged=True, seed=1)
+    dt, kappa = 1.0, synth.ACCEL_KAPPA
+    with handle(sy, 100, precision="fp64", dt=dt, kappa=kappa) as h:
+        h.step(1)
+        pos, vel, s1 = h.state()
+    m0, S0 = orc.sample_k(1, 0, 0, sy.box, ALPHA, 100)
+    m1, S1 = orc.sample_k(1, 1, 0, sy.box, ALPHA, 100)
+    s, v = sy.s.copy(), sy.v.copy()
+    F0 = oracle_all(orc, sy, m0, S0)["F"]
+    orc.vv_drift(s, v, F0, sy.mass, sy.box, dt, kappa)
+    F1 = orc.total_forces(s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig, m1, S1)["F"]
+    orc.vv_kick(v, F1, sy.mass, dt, kappa)
+    ds = (s1.astype(np.int64) - s.astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31
+    assert np.abs(ds).max() <= 1
+    # the FP64 form keeps 1/m in FP32 (relative 1.5e-8 for m = 20)
+    assert rel_l2(vel, v) < 1e-7
+
+
+def test_verlet_shadowing_fp32(orc):
+    """After 20 graph-replayed steps, the GPU forces on the GPU's own state match the
+    oracle's forces on that state (the trajectory itself is chaotic)."""
+    sy = synth.make_system(3000, L=32.0, all_charged=True, seed=1)
+    with handle(sy, 100, dt=1.0, kappa=synth.ACCEL_KAPPA) as h:
+        h.step(20)
+        assert h.step_count() == 20
+        pos, vel, s = h.state()
+        F, E, W = h.forces_f64(20)
+        m, S = h.sample_k(20)
+    sy2 = synth.System(box=sy.box, s=s, q=sy.q, types=sy.types, mass=sy.mass, v=vel,
+                       eps=sy.eps, sig=sy.sig)
+    ref = oracle_all(orc, sy2, m, S)
+    assert rel_l2(F, ref["F"]) < TOL_F32
+    assert np.isfinite(E["kinetic"]) and E["kinetic"] > 0
+
+
+def test_graph_replay_equals_single_steps():
+    sy = synth.make_system(5000, density=0.1, frac_charged=0.1, seed=2)
+    with handle(sy, 64) as a, handle(sy, 64) as b:
+        a.step(6)
+        for _ in range(6):
+            b.step(1)
+        pa, va, _ = a.state()
+        pb, vb, _ = b.state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+
+
+# -------------------------------------------------------------------------- full size
+
+
+@pytest.mark.slow
+def test_full_size_one_million_sampled(orc):
+    """1,048,576 particles (10% charged, density 0.1, P = 200), the launch configuration
+    of the benchmark: forces on 48 sampled particles against the oracle's O(N) sums."""
+    sy = synth.make_system(1 << 20, density=0.1, frac_charged=0.1, seed=2)
+    with handle(sy, 200) as h:
+        F, E, W = h.forces_f64(0)
+        m, S = h.sample_k(0)
+        rho, _ = h.rho()
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(sy.n, 48, replace=False))
+    charged = np.flatnonzero(sy.q != 0)
+    idx = np.unique(np.concatenate([idx, charged[:16]]))
+    rs = orc.real_space(sy.s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig, i_list=idx)
+    rho_o = orc.rho(sy.s, sy.q, sy.box, m)
+    assert rel_l2(rho, rho_o) < 2e-6
+    # k-space force of the sampled particles from the oracle's rho (Eq. F_long_RBE)
+    k = 2 * np.pi * m / sy.box
+    k2 = (k * k).sum(1)
+    V = np.prod(sy.box)
+    r = sy.positions()[idx]
+    th = r @ k.T
+    im = rho_o.imag[None, :] * np.cos(th) - rho_o.real[None, :] * np.sin(th)
+    c = (S / len(m)) * 4 * np.pi * C / (V * k2)
+    Fk = -(sy.q[idx][:, None, None] * (c * im)[:, :, None] * k[None, :, :]).sum(1)
+    Fo = rs["F"][idx] + Fk
+    assert rel_l2(F[idx], Fo) < TOL_F32
