@@ -20,13 +20,15 @@
 //     matches the oracle's decision bit for bit. Then it evaluates the pair force.
 // Forces are summed per i in a fixed j order with no atomics, so results are run-to-run
 // reproducible. The hot loop is FP32 ALU / SFU bound.
+#include <algorithm>
 #include <climits>
+#include <cmath>
 
 #include "pair_common.cuh"
 
 namespace rbe {
 
-template <typename real, bool LJ, bool COUL, bool MULTI>
+template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP>
 __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a) {
   __shared__ float4 stage[kPairWarps][32];
   __shared__ int32_t list[kPairWarps][kListK][32];
@@ -40,6 +42,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
   const LJTable *tab = a.table;
   PairAcc<real> acc;
   acc.fx = acc.fy = acc.fz = acc.ulj = acc.wlj = acc.uc = acc.wc = (real)0;
+  acc.cuc = acc.cwc = (real)0;
   acc.nbr = 0;
   if (i0 < n) {
     const int n0 = a.grid.n[0], n1 = a.grid.n[1], n2 = a.grid.n[2];
@@ -67,7 +70,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
     while (remaining) {
       const int leader = __ffs(remaining) - 1;
       const int gy = __shfl_sync(FULL, cy, leader), gz = __shfl_sync(FULL, cz, leader);
-      const bool in = valid && cy == gy && cz == gz && ((remaining >> lane) & 1u);
+      const int gx0 = __shfl_sync(FULL, cx, leader);
+      const bool in = valid && cy == gy && cz == gz && (WRAP || cx - gx0 < a.smax) &&
+                      ((remaining >> lane) & 1u);
       const unsigned gmask = __ballot_sync(FULL, in);
       remaining &= ~gmask;
       const int cxlo = __reduce_min_sync(FULL, in ? cx : INT_MAX);
@@ -108,7 +113,12 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
               const int nj = (int)min((int64_t)32, j1 - base);
               for (int t = 0; t < nj; ++t) {
                 const float4 p = stage[wid][t];
-                const float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
+                float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
+                if (WRAP) {
+                  ddx = fold(ddx, a.L[0], a.invL[0]);
+                  ddy = fold(ddy, a.L[1], a.invL[1]);
+                  ddz = fold(ddz, a.L[2], a.invL[2]);
+                }
                 const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                 const bool hit = in && r2 < a.pc.rc2_hi && (base + t) != i;
                 list[wid][cnt][lane] = (int32_t)(base + t);
@@ -135,7 +145,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
     }
   }
   // block partials of the energies and virials (halves of the per-i sums)
-  double v[NQ_PAIR] = {(double)acc.uc, (double)acc.ulj, (double)acc.wc, (double)acc.wlj};
+  double v[NQ_PAIR] = {(double)acc.uc - (double)acc.cuc, (double)acc.ulj,
+                       (double)acc.wc - (double)acc.cwc, (double)acc.wlj};
 #pragma unroll
   for (int k = 0; k < NQ_PAIR; ++k) {
     const double w = warp_sum(v[k]);
@@ -150,11 +161,29 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
 }
 
 template <typename real, bool LJ, bool COUL>
-static void launch_one(const PairArgs &a, int64_t n, bool multi, cudaStream_t st) {
+static void launch_one(const PairArgs &a, int64_t n, bool multi, bool wrap, cudaStream_t st) {
   const unsigned blocks = (unsigned)((n + 32 * kPairWarps - 1) / (32 * kPairWarps));
   if (blocks == 0) return;
-  if (multi) pair_kernel<real, LJ, COUL, true><<<blocks, kPairWarps * 32, 0, st>>>(a);
-  else pair_kernel<real, LJ, COUL, false><<<blocks, kPairWarps * 32, 0, st>>>(a);
+  const dim3 g(blocks), b(kPairWarps * 32);
+  if (wrap) {
+    if (multi) pair_kernel<real, LJ, COUL, true, true><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, true><<<g, b, 0, st>>>(a);
+  } else {
+    if (multi) pair_kernel<real, LJ, COUL, true, false><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, false><<<g, b, 0, st>>>(a);
+  }
+}
+
+// Largest x-extent (in cells) of a group whose leader frame stays a valid minimum image;
+// 0 when even one cell is too wide (the wrapping variant is used then).
+int frame_span_cells(const Ctx &c) {
+  for (int d = 1; d < 3; ++d) {
+    const double a = c.box[d] / c.grid.n[d];
+    if (!(a + c.rc < 0.5 * c.box[d] * (1.0 - 1e-9))) return 0;
+  }
+  const double ax = c.box[0] / c.grid.n[0];
+  const int s = (int)std::floor((0.5 * c.box[0] * (1.0 - 1e-9) - c.rc) / ax);
+  return s >= 1 ? std::min(s, 1 << 20) : 0;
 }
 
 int64_t pair_blocks(int64_t n) { return (n + 32 * kPairWarps - 1) / (32 * kPairWarps); }
@@ -177,13 +206,20 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   a.accumulate = 0;
   a.epart = c.epart + c.off_pair;
   a.nbr = want_counts ? c.nbr : nullptr;
+  a.smax = frame_span_cells(c);
+  a.comp = c.precision == RBE_FP32_COMP;
+  const bool wrap = a.smax == 0;
+  for (int d = 0; d < 3; ++d) {
+    a.L[d] = (float)c.box[d];
+    a.invL[d] = (float)(1.0 / c.box[d]);
+  }
   const bool fp64 = c.precision == RBE_FP64;
   if (fused) {
-    if (fp64) launch_one<double, true, true>(a, c.N, multi, c.stream);
-    else launch_one<float, true, true>(a, c.N, multi, c.stream);
+    if (fp64) launch_one<double, true, true>(a, c.N, multi, wrap, c.stream);
+    else launch_one<float, true, true>(a, c.N, multi, wrap, c.stream);
   } else {
-    if (fp64) launch_one<double, true, false>(a, c.N, multi, c.stream);
-    else launch_one<float, true, false>(a, c.N, multi, c.stream);
+    if (fp64) launch_one<double, true, false>(a, c.N, multi, wrap, c.stream);
+    else launch_one<float, true, false>(a, c.N, multi, wrap, c.stream);
   }
   mark(c, RBE_PH_PAIR2);
   if (!fused) {
@@ -195,8 +231,8 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
       b2.accumulate = 1;
       b2.epart = c.epart + c.off_coul;
       b2.nbr = nullptr;
-      if (fp64) launch_one<double, false, true>(b2, c.Nq, false, c.stream);
-      else launch_one<float, false, true>(b2, c.Nq, false, c.stream);
+      if (fp64) launch_one<double, false, true>(b2, c.Nq, false, wrap, c.stream);
+      else launch_one<float, false, true>(b2, c.Nq, false, wrap, c.stream);
     }
   }
   return cudaGetLastError();

@@ -70,7 +70,7 @@ __device__ __forceinline__ void rbl_pair(const RblArgs &a, const LJTable *tab, u
   pair_force<real, true, COUL, MULTI>(a.pa, tab, dx, dy, dz, r2, qi, ti, j, acc);
 }
 
-template <typename real, bool COUL, bool MULTI>
+template <typename real, bool COUL, bool MULTI, bool WRAP>
 __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   __shared__ float4 stage[kRblWarps][32];
   __shared__ int32_t list[kRblWarps][kListK][32];
@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   const LJTable *tab = a.pa.table;
   PairAcc<real> core, shell;
   core.fx = core.fy = core.fz = core.ulj = core.wlj = core.uc = core.wc = (real)0;
+  core.cuc = core.cwc = (real)0;
   shell = core;
   core.nbr = shell.nbr = 0;
   real fx = 0, fy = 0, fz = 0;
@@ -167,7 +168,12 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
                 const int nj = (int)min((int64_t)32, j1 - base);
                 for (int t = 0; t < nj; ++t) {
                   const float4 pj = stage[wid][t];
-                  const float ddx = xi - pj.x, ddy = yi - pj.y, ddz = zi - pj.z;
+                  float ddx = xi - pj.x, ddy = yi - pj.y, ddz = zi - pj.z;
+                  if (WRAP) {
+                    ddx = fold(ddx, a.pa.L[0], a.pa.invL[0]);
+                    ddy = fold(ddy, a.pa.L[1], a.pa.invL[1]);
+                    ddz = fold(ddz, a.pa.L[2], a.pa.invL[2]);
+                  }
                   const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                   const int64_t j = base + t;
                   const int cls = (in && j != i && r2 <= a.rs2_hi) ? rbl_classify(a, r2, sxi, syi, szi, j) : 0;
@@ -202,9 +208,11 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
       fx = core.fx + w * shell.fx;
       fy = core.fy + w * shell.fy;
       fz = core.fz + w * shell.fz;
-      en[Q_UREAL] = (double)(core.uc + w * shell.uc);
+      en[Q_UREAL] = ((double)core.uc - (double)core.cuc) +
+                    (double)w * ((double)shell.uc - (double)shell.cuc);
       en[Q_ULJ] = (double)(core.ulj + w * shell.ulj);
-      en[Q_WREAL] = (double)(core.wc + w * shell.wc);
+      en[Q_WREAL] = ((double)core.wc - (double)core.cwc) +
+                    (double)w * ((double)shell.wc - (double)shell.cwc);
       en[Q_WLJ] = (double)(core.wlj + w * shell.wlj);
       const int64_t St = a.pa.Fstride;
       if (sizeof(real) == 8) { a.pa.Fd[i] = (double)fx; a.pa.Fd[St + i] = (double)fy; a.pa.Fd[2 * St + i] = (double)fz; }
@@ -258,9 +266,15 @@ __global__ void rbl_subtract_kernel(real *__restrict__ F, int64_t N, const doubl
 int64_t rbl_blocks(int64_t n) { return (n + 32 * kRblWarps - 1) / (32 * kRblWarps); }
 
 template <typename real, bool COUL>
-static void rbl_launch(const RblArgs &a, int64_t blocks, bool multi, cudaStream_t st) {
-  if (multi) rbl_kernel<real, COUL, true><<<(unsigned)blocks, kRblWarps * 32, 0, st>>>(a);
-  else rbl_kernel<real, COUL, false><<<(unsigned)blocks, kRblWarps * 32, 0, st>>>(a);
+static void rbl_launch(const RblArgs &a, int64_t blocks, bool multi, bool wrap, cudaStream_t st) {
+  const dim3 g((unsigned)blocks), b(kRblWarps * 32);
+  if (wrap) {
+    if (multi) rbl_kernel<real, COUL, true, true><<<g, b, 0, st>>>(a);
+    else rbl_kernel<real, COUL, false, true><<<g, b, 0, st>>>(a);
+  } else {
+    if (multi) rbl_kernel<real, COUL, true, false><<<g, b, 0, st>>>(a);
+    else rbl_kernel<real, COUL, false, false><<<g, b, 0, st>>>(a);
+  }
 }
 
 cudaError_t launch_rbl(Ctx &c, bool want_debug) {
@@ -292,12 +306,21 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   a.partners = want_debug ? c.partners : nullptr;
   const int64_t blocks = rbl_blocks(c.N);
   const bool multi = c.nt > 1, coul = c.Nq > 0;
+  // groups share one cell: the leader frame is a valid minimum image while a + r_s < L/2
+  bool wrap = false;
+  for (int d = 0; d < 3; ++d) {
+    pa.L[d] = (float)c.box[d];
+    pa.invL[d] = (float)(1.0 / c.box[d]);
+    if (!(c.box[d] / c.grid.n[d] + c.rc < 0.5 * c.box[d] * (1.0 - 1e-9))) wrap = true;
+  }
+  pa.smax = 1;
+  pa.comp = c.precision == RBE_FP32_COMP;
   if (c.precision == RBE_FP64) {
-    if (coul) rbl_launch<double, true>(a, blocks, multi, c.stream);
-    else rbl_launch<double, false>(a, blocks, multi, c.stream);
+    if (coul) rbl_launch<double, true>(a, blocks, multi, wrap, c.stream);
+    else rbl_launch<double, false>(a, blocks, multi, wrap, c.stream);
   } else {
-    if (coul) rbl_launch<float, true>(a, blocks, multi, c.stream);
-    else rbl_launch<float, false>(a, blocks, multi, c.stream);
+    if (coul) rbl_launch<float, true>(a, blocks, multi, wrap, c.stream);
+    else rbl_launch<float, false>(a, blocks, multi, wrap, c.stream);
   }
   mark(c, RBE_PH_PAIR2);
   rbl_mean_kernel<<<1, 256, 0, c.stream>>>(c.rbl_part, blocks, c.N, c.rbl_mean);

@@ -22,13 +22,34 @@ struct PairArgs {
   int accumulate;    // add to F instead of overwriting
   double *epart;     // per-block partials (NQ_PAIR doubles each)
   int32_t *nbr;      // per-particle neighbour counts (sorted order of the set), nullable
+  // Coarse-test frame: coordinates relative to the group leader are a valid minimum
+  // image only while (distance of a member from the leader) + r_c < L/2 on every axis.
+  // A group spans at most `smax` cells in x (one cell in y and z); boxes too small for
+  // even one cell use the wrapping variant, which folds every difference into [-L/2, L/2).
+  int smax;
+  float L[3], invL[3];
+  int comp;  // compensated (Kahan) Coulomb energy and virial sums
 };
+
+// Fold a coordinate difference into [-L/2, L/2) (only the small-box variants use it).
+__device__ __forceinline__ float fold(float d, float L, float invL) {
+  return d - L * rintf(d * invL);
+}
 
 template <typename real>
 struct PairAcc {
   real fx, fy, fz, ulj, wlj, uc, wc;
+  real cuc, cwc;  // Kahan compensations of uc, wc (compensated form)
   int nbr;
 };
+
+template <typename real>
+__device__ __forceinline__ void kahan_add(real &s, real &c, real x) {
+  const real y = x - c;
+  const real t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 
 // Squared distance of the exact cutoff decision (the oracle's definition): dx_d =
 // (int32)(s_i - s_j) * (L_d / 2^32) and r2 = dx^2 + dy^2 + dz^2 in FP64, no FMA.
@@ -92,8 +113,14 @@ __device__ __forceinline__ void pair_force(const PairArgs &a, const LJTable *tab
       const real rinv2 = rinv * rinv;
       const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
       g += gc;
-      acc.uc += Cqq * erfcv * rinv;
-      acc.wc += gc * r2;
+      // erfc-Coulomb pair energies of both signs cancel heavily: compensate the sums
+      if (a.comp) {
+        kahan_add(acc.uc, acc.cuc, Cqq * erfcv * rinv);
+        kahan_add(acc.wc, acc.cwc, gc * r2);
+      } else {
+        acc.uc += Cqq * erfcv * rinv;
+        acc.wc += gc * r2;
+      }
     }
   }
   acc.fx += g * dx;

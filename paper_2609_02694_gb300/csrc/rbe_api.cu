@@ -90,7 +90,13 @@ uint32_t quantise(double r, double L) {
 namespace rbe {
 void mark(Ctx &c, int k) {
   if (!c.timing || !c.ev[k]) return;
-  cudaEventRecord(c.ev[k], c.stream);
+  // during graph capture only an external record becomes an event node of the graph
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c.stream, &st);
+  if (st == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(c.ev[k], c.stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(c.ev[k], c.stream);
   c.ev_used[k] = true;
 }
 }  // namespace rbe
