@@ -28,10 +28,16 @@
 
 namespace rbe {
 
+constexpr int kMaxRows = 49;            // (2R+1)^2 stencil rows for R <= 3
+constexpr int kMaxSeg = 2 * kMaxRows;   // a row wraps into at most two runs of cells
+
 template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP>
 __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a) {
   __shared__ float4 stage[kPairWarps][32];
+  __shared__ int32_t stage_j[kPairWarps][32];
   __shared__ int32_t list[kPairWarps][kListK][32];
+  __shared__ int32_t seg_beg[kPairWarps][kMaxSeg];
+  __shared__ int32_t seg_pre[kPairWarps][kMaxSeg + 1];
   __shared__ double wred[kPairWarps][NQ_PAIR];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
@@ -54,18 +60,20 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
     if (COUL && valid) qi = sizeof(real) == 8 ? (real)a.set.qd[i] : (real)a.set.qf[i];
     const int ti = (MULTI && valid) ? a.set.type[i] : 0;
     const int cx = cell_of(sxi, n0), cy = cell_of(syi, n1), cz = cell_of(szi, n2);
+    const float rc2_hi = a.pc.rc2_hi;
     int cnt = 0;
     auto flush = [&]() {
       const int maxc = __reduce_max_sync(FULL, cnt);
       for (int t = 0; t < maxc; ++t) {
         if (t < cnt) {
           const int64_t j = list[wid][t][lane];
-          pair_body<real, LJ, COUL, MULTI>(a, tab, sxi, syi, szi, qi, ti, j, acc);
+          if (j != i) pair_body<real, LJ, COUL, MULTI>(a, tab, sxi, syi, szi, qi, ti, j, acc);
         }
       }
       cnt = 0;
       __syncwarp();
     };
+    const int ny = 2 * R1 + 1, nrows = ny * (2 * R2 + 1);
     unsigned remaining = __ballot_sync(FULL, valid);
     while (remaining) {
       const int leader = __ffs(remaining) - 1;
@@ -84,50 +92,91 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
       const float yi = (float)(int)(syi - oy) * a.pc.h[1];
       const float zi = (float)(int)(szi - oz) * a.pc.h[2];
       const int span = cxhi - cxlo + 2 * R0 + 1;
-      for (int dz = -R2; dz <= R2; ++dz) {
-        const int rz = ((gz + dz) % n2 + n2) % n2;
-        for (int dy = -R1; dy <= R1; ++dy) {
+      // 1. Runs of candidates: one lane per stencil row (dz, dy) loads the row's cell
+      //    range(s) in parallel; a warp scan turns the run lengths into offsets.
+      int carry = 0;
+      for (int rb = 0; rb < nrows; rb += 32) {
+        const int r = rb + lane;
+        int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
+        if (r < nrows) {
+          const int dz = r / ny - R2, dy = r % ny - R1;
+          const int rz = ((gz + dz) % n2 + n2) % n2;
           const int ry = ((gy + dy) % n1 + n1) % n1;
           const int64_t rowbase = (int64_t)n0 * (ry + (int64_t)n1 * rz);
-          int sa[2], sb[2], nseg;
-          if (span >= n0) {
-            sa[0] = 0; sb[0] = n0 - 1; nseg = 1;
-          } else {
+          int sa0, sb0, sa1 = 0, sb1 = -1;
+          if (span >= n0) { sa0 = 0; sb0 = n0 - 1; }
+          else {
             const int lo = cxlo - R0, hi = cxhi + R0;
-            if (lo < 0) { sa[0] = lo + n0; sb[0] = n0 - 1; sa[1] = 0; sb[1] = hi; nseg = 2; }
-            else if (hi >= n0) { sa[0] = lo; sb[0] = n0 - 1; sa[1] = 0; sb[1] = hi - n0; nseg = 2; }
-            else { sa[0] = lo; sb[0] = hi; nseg = 1; }
+            if (lo < 0) { sa0 = lo + n0; sb0 = n0 - 1; sa1 = 0; sb1 = hi; }
+            else if (hi >= n0) { sa0 = lo; sb0 = n0 - 1; sa1 = 0; sb1 = hi - n0; }
+            else { sa0 = lo; sb0 = hi; }
           }
-          for (int sgi = 0; sgi < nseg; ++sgi) {
-            const int64_t j0 = a.set.cell_start[rowbase + sa[sgi]];
-            const int64_t j1 = a.set.cell_start[rowbase + sb[sgi] + 1];
-            for (int64_t base = j0; base < j1; base += 32) {
-              if (__any_sync(FULL, cnt > kListK - 32)) flush();
-              const int64_t jj = base + lane;
-              if (jj < j1) {
-                stage[wid][lane] = make_float4((float)(int)(a.set.sx[jj] - ox) * a.pc.h[0],
-                                               (float)(int)(a.set.sy[jj] - oy) * a.pc.h[1],
-                                               (float)(int)(a.set.sz[jj] - oz) * a.pc.h[2], 0.f);
-              }
-              __syncwarp();
-              const int nj = (int)min((int64_t)32, j1 - base);
-              for (int t = 0; t < nj; ++t) {
-                const float4 p = stage[wid][t];
-                float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
-                if (WRAP) {
-                  ddx = fold(ddx, a.L[0], a.invL[0]);
-                  ddy = fold(ddy, a.L[1], a.invL[1]);
-                  ddz = fold(ddz, a.L[2], a.invL[2]);
-                }
-                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                const bool hit = in && r2 < a.pc.rc2_hi && (base + t) != i;
-                list[wid][cnt][lane] = (int32_t)(base + t);
-                cnt += hit ? 1 : 0;
-              }
-              __syncwarp();
-            }
+          b0 = a.set.cell_start[rowbase + sa0];
+          l0 = a.set.cell_start[rowbase + sb0 + 1] - b0;
+          if (sb1 >= sa1) {
+            b1 = a.set.cell_start[rowbase + sa1];
+            l1 = a.set.cell_start[rowbase + sb1 + 1] - b1;
           }
         }
+        const int tot = l0 + l1;
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int excl = carry + incl - tot;
+        if (r < nrows) {
+          seg_beg[wid][2 * r] = b0;
+          seg_pre[wid][2 * r] = excl;
+          seg_beg[wid][2 * r + 1] = b1;
+          seg_pre[wid][2 * r + 1] = excl + l0;
+        }
+        carry += __shfl_sync(FULL, incl, 31);
+      }
+      if (lane == 0) seg_pre[wid][2 * nrows] = carry;
+      __syncwarp();
+      const int T = carry;
+      // 2. Candidates in full chunks of 32 across run boundaries: stage, bitmask test,
+      //    append the hits to the per-lane list.
+      int sg = 0;
+      for (int base = 0; base < T; base += 32) {
+        if (__any_sync(FULL, cnt > kListK - 32)) flush();
+        const int c = base + lane;
+        int s = sg;
+        if (c < T) {
+          while (seg_pre[wid][s + 1] <= c) ++s;
+          const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
+          stage[wid][lane] = make_float4((float)(int)(a.set.sx[j] - ox) * a.pc.h[0],
+                                         (float)(int)(a.set.sy[j] - oy) * a.pc.h[1],
+                                         (float)(int)(a.set.sz[j] - oz) * a.pc.h[2], 0.f);
+          stage_j[wid][lane] = (int32_t)j;
+        }
+        sg = __shfl_sync(FULL, s, 31);
+        __syncwarp();
+        uint32_t mask = 0u;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const float4 p = stage[wid][t];
+          float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
+          if (WRAP) {
+            ddx = fold(ddx, a.L[0], a.invL[0]);
+            ddy = fold(ddy, a.L[1], a.invL[1]);
+            ddz = fold(ddz, a.L[2], a.invL[2]);
+          }
+          const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+          mask |= (r2 < rc2_hi) ? (1u << t) : 0u;
+        }
+        const int nj = min(32, T - base);
+        if (nj < 32) mask &= (1u << nj) - 1u;
+        if (!in) mask = 0u;
+        while (mask) {
+          const int t = __ffs(mask) - 1;
+          mask &= mask - 1u;
+          list[wid][cnt][lane] = stage_j[wid][t];
+          ++cnt;
+        }
+        __syncwarp();
       }
     }
     flush();
