@@ -188,6 +188,28 @@ int rbe_check_device(rbe_handle h);
 /* Free every device buffer and the handle. NULL is accepted. */
 int rbe_destroy(rbe_handle h);
 
+/* Structure factor rho_l = sum_j q_j exp(2 pi i sum_d m_ld s_jd / 2^32) of N particles for P
+ * given modes, computed without allocating any device memory.
+ * The paper has no counterpart to this entry point. It exists for callers that cannot
+ * allocate device memory: a host application that owns one fixed device pool and forbids
+ * libraries to allocate outside it, or a latency-bound loop that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ *  s     device, 3 x N uint32 fractional coordinates, one block per axis (x, then y, then z)
+ *  q     device, N float charges
+ *  m     device, P x 3 int32 mode integers (row-major)
+ *  rho   device, P x 2 double output (Re, Im)
+ *  cuda_stream  the stream to run on (NULL = legacy default stream)
+ * Sums are Kahan-compensated FP32 per thread, combined in FP64 in a fixed order.
+ * Limits: 1 <= P <= 65536 (RBE_ERR_INVALID beyond; nothing is launched then); any N >= 0.
+ * The scratch (per-block partial sums) is a fixed 8 MiB device array inside the library,
+ * held by every GPU that loads the library until the process exits, and shared by all
+ * calls on that GPU: calls that overlap on the GPU race and must be ordered by the
+ * caller. The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. Asynchronous:
+ * synchronise the stream before reading rho. */
+int rbe_structure_factor_noalloc(const uint32_t *s, const float *q, int64_t N,
+                                 const int32_t *m, int P, double *rho, void *cuda_stream);
+
 /* Static description of an error code. */
 const char *rbe_error_string(int code);
 

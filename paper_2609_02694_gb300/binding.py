@@ -81,6 +81,7 @@ def lib(build_if_missing: bool = False):
     L.rbe_set_profiling.argtypes = [h, ct.c_int]
     L.rbe_get_profile.argtypes = [h, _vp, _vp]
     L.rbe_check_device.argtypes = [h]
+    L.rbe_structure_factor_noalloc.argtypes = [_vp, _vp, ct.c_int64, _vp, ct.c_int, _vp, _vp]
     L.rbe_destroy.argtypes = [h]
     L.rbe_error_string.argtypes = [ct.c_int]
     L.rbe_error_string.restype = ct.c_char_p
