@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 form, e2e, error and CPU legs (profiling runs)")
+    ap.add_argument("--config", default="main",
+                    choices=["main", "batch96", "sweep16m", "rbl134m", "n3000"],
+                    help="main: the benchmark line; the others print per-config JSON lines")
     return ap.parse_args()
 
 
@@ -336,10 +339,194 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _timed(fn, K, stream):
+    """Per-call device time (CUDA events on `stream`, synchronised) summed over K calls."""
+    import torch
+    tot = 0.0
+    for _ in range(K):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        e.synchronize()
+        tot += s.elapsed_time(e)
+    return tot
+
+
+def run_batch96(args):
+    """96 replicas of log-uniform size (2,000..250,000), 10% charged, density 0.1: one graph
+    launch per step for all replicas against per-box sequential graph launches."""
+    import torch
+    from paper_2609_02694_gb300 import binding, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sizes = synth.replica_sizes(96)
+    hs = []
+    for r, n in enumerate(sizes):
+        sy = synth.make_system(n, density=0.1, frac_charged=0.1, seed=1000 + r)
+        hs.append(binding.from_system(sy, P=args.P, alpha=synth.ALPHA, r_c=synth.R_CUT,
+                                      coulomb_C=synth.COULOMB_C, dt=1.0,
+                                      kappa=synth.ACCEL_KAPPA, replica=r,
+                                      stream=stream.cuda_stream))
+    total_n = sum(sizes)
+    with binding.Batch(hs, stream=stream.cuda_stream) as b:
+        b.step(args.warmup)
+        torch.cuda.synchronize()
+        ms_b = _timed(lambda: b.step(1), args.steps, stream)
+    torch.cuda.synchronize()
+    for h in hs:
+        h.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def seq():
+        for h in hs:
+            h.step(1)
+    ms_s = _timed(seq, args.steps, stream)
+    print(json.dumps({"config": "batch96", "replicas": 96, "particles": total_n,
+                      "size_range": [min(sizes), max(sizes)], "P": args.P,
+                      "batched_graph": {"value": total_n * args.steps / (ms_b / 1e3),
+                                        "unit": UNIT, "ms_per_step": ms_b / args.steps},
+                      "sequential_per_box": {"value": total_n * args.steps / (ms_s / 1e3),
+                                             "unit": UNIT, "ms_per_step": ms_s / args.steps},
+                      "steps": args.steps}), flush=True)
+    for h in hs:
+        h.close()
+
+
+def run_sweep16m(args):
+    """Precision sweep: throughput at 16,777,216 particles for each form and P, and force /
+    energy / virial errors on a 65,536-particle box of the same composition against the
+    FP64 oracle on the same modes."""
+    import torch
+    import oracle
+    from paper_2609_02694_gb300 import binding, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    big = synth.make_system(1 << 24, density=0.1, frac_charged=0.1, seed=3)
+    small = synth.sub_box()
+    rs = oracle.real_space(small.s, small.q, small.types, small.box, synth.ALPHA, synth.R_CUT,
+                           synth.COULOMB_C, small.eps, small.sig)
+    ke = 0.5 * (small.mass[:, None] * small.v ** 2).sum() / synth.ACCEL_KAPPA
+    V = float(np.prod(small.box))
+    for P in (100, 500, 2000):
+        m, S = oracle.sample_k(1, 0, 0, small.box, synth.ALPHA, P)
+        Fk, Uk, Wk = oracle.rbe_kspace(small.s, small.q, small.box, synth.ALPHA, synth.COULOMB_C,
+                                       m, S)
+        Fo = rs["F"] + Fk
+        Uo = rs["U_real"] + rs["U_lj"] + Uk - oracle.self_energy(small.q, synth.ALPHA,
+                                                                 synth.COULOMB_C)
+        Wo = rs["W_real"] + rs["W_lj"] + Wk
+        for form in ("fp32_comp", "fp32", "fp64"):
+            kw = dict(P=P, alpha=synth.ALPHA, r_c=synth.R_CUT, coulomb_C=synth.COULOMB_C,
+                      dt=1.0, kappa=synth.ACCEL_KAPPA, precision=form, stream=stream.cuda_stream)
+            with binding.from_system(small, **kw) as h:
+                F, E, W = h.forces_f64(0)
+            errs = {"force_rel_l2": float(np.linalg.norm(F - Fo) / np.linalg.norm(Fo)),
+                    "energy_rel": abs(E["total"] - Uo) / abs(Uo),
+                    "pressure_rel": abs((2 * ke + W["total"]) - (2 * ke + Wo)) / abs(2 * ke + Wo)}
+            h = binding.from_system(big, **kw)
+            h.step(1)
+            torch.cuda.synchronize()
+            K = 2 if form == "fp64" else 3
+            ms = _timed(lambda: h.step(1), K, stream)
+            h.close()
+            print(json.dumps({"config": "sweep16m", "form": form, "P": P,
+                              "value": big.n * K / (ms / 1e3), "unit": UNIT,
+                              "ms_per_step": ms / K, "errors_65536_box": errs,
+                              "pressure_A3": (2 * ke + Wo) / (3 * V)}), flush=True)
+
+
+def run_rbl134m(args):
+    """2^27 particles (5% charged, density 0.1) with the random batch list (r_core = 5 A,
+    r_s = 10 A, p = 10), P = 500, FP32-compensated: throughput and device bytes/particle."""
+    import torch
+    from paper_2609_02694_gb300 import binding, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    N = args.N if args.N != (1 << 20) else (1 << 27)
+    sy = synth.make_system(N, density=0.1, frac_charged=0.05, seed=5)
+    t0 = time.perf_counter()
+    h = binding.from_system(sy, P=500, alpha=synth.ALPHA, r_c=synth.R_CUT,
+                            coulomb_C=synth.COULOMB_C, dt=1.0, kappa=synth.ACCEL_KAPPA,
+                            r_core=5.0, p_rbl=10, stream=stream.cuda_stream)
+    init_s = time.perf_counter() - t0
+    h.set_profiling(True)
+    F, E, W = h.forces(0)
+    net = np.abs(F.astype(np.float64).sum(0)).max() / np.abs(F).sum()
+    for _ in range(max(1, args.warmup)):
+        h.step(1)
+    torch.cuda.synchronize()
+    K = max(1, min(args.steps, 5))
+    ph_tot = None
+    tot = 0.0
+    for _ in range(K):
+        tot += _timed(lambda: h.step(1), 1, stream)
+        ph, _ = h.profile()
+        ph_tot = ph if ph_tot is None else {k: ph_tot[k] + ph[k] for k in ph}
+    print(json.dumps({"config": "rbl134m", "N": N, "value": N * K / (tot / 1e3), "unit": UNIT,
+                      "ms_per_step": tot / K, "steps": K,
+                      "device_bytes_per_particle": h.memory_bytes() / N,
+                      "phases_ms_per_step": {k: v / K for k, v in ph_tot.items()},
+                      "net_force_over_sum_abs": float(net), "init_s": init_s}), flush=True)
+    h.close()
+
+
+def run_n3000(args):
+    """3,000 point charges (1,500 each sign) in L = 32 A, FP64 form: one force evaluation
+    against the oracle on the same modes and against the full Ewald sum (RBE sampling
+    error), then 100 graph-replayed Verlet steps (dt = 1 fs) with the energy drift."""
+    import torch
+    import oracle
+    from paper_2609_02694_gb300 import binding, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sy = synth.make_system(3000, L=32.0, all_charged=True, seed=1)
+    out = {"config": "n3000"}
+    for form in ("fp64", "fp32_comp"):
+        with binding.from_system(sy, P=100, alpha=synth.ALPHA, r_c=synth.R_CUT,
+                                 coulomb_C=synth.COULOMB_C, dt=1.0, kappa=synth.ACCEL_KAPPA,
+                                 precision=form, stream=stream.cuda_stream) as h:
+            F, E, W = h.forces_f64(0)
+            m, S = h.sample_k(0)
+            ref = oracle.total_forces(sy.s, sy.q, sy.types, sy.box, synth.ALPHA, synth.R_CUT,
+                                      synth.COULOMB_C, sy.eps, sy.sig, m, S)
+            Fe, Ue, We = oracle.ewald_kspace(sy.s, sy.q, sy.box, synth.ALPHA, synth.COULOMB_C)
+            rs = oracle.real_space(sy.s, sy.q, sy.types, sy.box, synth.ALPHA, synth.R_CUT,
+                                   synth.COULOMB_C, sy.eps, sy.sig)
+            Fewald = rs["F"] + Fe
+            h.step(1)
+            torch.cuda.synchronize()
+            E0, _ = h.energies()
+            ms = _timed(lambda: h.step(1), 100, stream)
+            E1, _ = h.energies()
+            out[form] = {"force_rel_l2_vs_oracle_same_modes":
+                         float(np.linalg.norm(F - ref["F"]) / np.linalg.norm(ref["F"])),
+                         "force_rel_l2_vs_full_ewald":
+                         float(np.linalg.norm(F - Fewald) / np.linalg.norm(Fewald)),
+                         "energy_rel_vs_oracle": abs(E["total"] - ref["U_total"]) / abs(ref["U_total"]),
+                         "value": 3000 * 100 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / 100,
+                         "E_total_step1": E0["total"] + E0["kinetic"],
+                         "E_total_step101": E1["total"] + E1["kinetic"]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch96":
+        run_batch96(args)
+    elif args.config == "sweep16m":
+        run_sweep16m(args)
+    elif args.config == "rbl134m":
+        run_rbl134m(args)
+    elif args.config == "n3000":
+        run_n3000(args)
     else:
         run_ours(args)
 

@@ -188,6 +188,19 @@ int rbe_check_device(rbe_handle h);
 /* Free every device buffer and the handle. NULL is accepted. */
 int rbe_destroy(rbe_handle h);
 
+/* Batched replicas: independent systems (each its own rbe_init handle, typically with its
+ * own `replica` key) advanced together. One CUDA graph holds one Verlet step of every
+ * replica as parallel branches, so one graph launch per step advances the whole batch
+ * and small replicas run concurrently.
+ *  handles  n handles created on the same device; the batch does not own them
+ *  cuda_stream  stream the graph is launched on (NULL = legacy default stream)
+ * rbe_batch_step is asynchronous; each handle's own getters read its state afterwards
+ * (they synchronise the handle's stream, so synchronise cuda_stream first). */
+typedef struct rbe_batch_s *rbe_batch;
+int rbe_batch_create(rbe_batch *b, int n, const rbe_handle *handles, void *cuda_stream);
+int rbe_batch_step(rbe_batch b, int nsteps);
+int rbe_batch_destroy(rbe_batch b);
+
 /* Structure factor rho_l = sum_j q_j exp(2 pi i sum_d m_ld s_jd / 2^32) of N particles for P
  * given modes, computed without allocating any device memory.
  * The paper has no counterpart to this entry point. It exists for callers that cannot

@@ -81,6 +81,9 @@ def lib(build_if_missing: bool = False):
     L.rbe_set_profiling.argtypes = [h, ct.c_int]
     L.rbe_get_profile.argtypes = [h, _vp, _vp]
     L.rbe_check_device.argtypes = [h]
+    L.rbe_batch_create.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p), _vp]
+    L.rbe_batch_step.argtypes = [ct.c_void_p, ct.c_int]
+    L.rbe_batch_destroy.argtypes = [ct.c_void_p]
     L.rbe_structure_factor_noalloc.argtypes = [_vp, _vp, ct.c_int64, _vp, ct.c_int, _vp, _vp]
     L.rbe_destroy.argtypes = [h]
     L.rbe_error_string.argtypes = [ct.c_int]
@@ -287,6 +290,39 @@ class RBE:
 
     def check_device(self):
         _check(lib().rbe_check_device(self._h), "rbe_check_device")
+
+
+class Batch:
+    """Replicas advanced together: one CUDA graph launch per Verlet step for all of them."""
+
+    def __init__(self, handles, stream=None):
+        self.handles = list(handles)
+        arr = (ct.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        if stream is None:
+            stream = _current_stream()
+        self._b = ct.c_void_p()
+        _check(lib().rbe_batch_create(ct.byref(self._b), len(self.handles), arr, stream),
+               "rbe_batch_create")
+
+    def step(self, n: int = 1):
+        _check(lib().rbe_batch_step(self._b, n), "rbe_batch_step")
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            lib().rbe_batch_destroy(self._b)
+            self._b = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def from_system(sy, *, P: int, alpha: float, r_c: float, **kw) -> RBE:

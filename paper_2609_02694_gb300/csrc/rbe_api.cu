@@ -765,6 +765,133 @@ int rbe_get_memory(rbe_handle h, int64_t *bytes) {
   return RBE_OK;
 }
 
+struct rbe_batch_s {
+  std::vector<rbe_handle> h;
+  std::vector<cudaStream_t> br;   // capture branches
+  std::vector<cudaEvent_t> ev;    // join events
+  cudaEvent_t fork = nullptr;
+  cudaStream_t stream = nullptr;  // launch stream
+  cudaStream_t cap = nullptr;     // capture origin
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int phase = 0;
+};
+
+static int batch_free(rbe_batch b) {
+  for (auto s : b->br) if (s) cudaStreamDestroy(s);
+  for (auto e : b->ev) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (int k = 0; k < 2; ++k) if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+  delete b;
+  return RBE_OK;
+}
+
+// One graph: fork from the origin stream, each replica's Verlet step on its own branch,
+// join. `flip` selects the buffer parity after an odd number of steps.
+static int batch_capture(rbe_batch b, int flip, cudaGraphExec_t *out) {
+  const int n = (int)b->h.size();
+  std::vector<int> saved_cur(n);
+  std::vector<cudaStream_t> saved_stream(n);
+  for (int r = 0; r < n; ++r) {
+    saved_cur[r] = b->h[r]->cur;
+    saved_stream[r] = b->h[r]->stream;
+    b->h[r]->cur = flip ? 1 - saved_cur[r] : saved_cur[r];
+    b->h[r]->stream = b->br[r];
+  }
+  int rc = RBE_OK;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaEventRecord(b->fork, b->cap);
+    for (int r = 0; r < n && rc == RBE_OK; ++r) {
+      Ctx &c = *b->h[r];
+      if (cudaStreamWaitEvent(b->br[r], b->fork, 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      if (launch_kick_drift(c) != cudaSuccess || launch_step_advance(c) != cudaSuccess) {
+        rc = RBE_ERR_CUDA;
+        break;
+      }
+      rc = force_pipeline(c, false);
+      if (rc != RBE_OK) break;
+      if (launch_kick(c) != cudaSuccess || launch_totals(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      cudaEventRecord(b->ev[r], b->br[r]);
+      cudaStreamWaitEvent(b->cap, b->ev[r], 0);
+    }
+    e = cudaStreamEndCapture(b->cap, &g);
+  }
+  for (int r = 0; r < n; ++r) {
+    b->h[r]->cur = saved_cur[r];
+    b->h[r]->stream = saved_stream[r];
+  }
+  if (rc != RBE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  RBE_CUDA_TRY(e);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  RBE_CUDA_TRY(e);
+  return RBE_OK;
+}
+
+int rbe_batch_create(rbe_batch *out, int n, const rbe_handle *handles, void *cuda_stream) {
+  if (!out || n < 1 || !handles) return RBE_ERR_INVALID;
+  *out = nullptr;
+  for (int r = 0; r < n; ++r)
+    if (!handles[r]) return RBE_ERR_INVALID;
+  rbe_batch b = new (std::nothrow) rbe_batch_s();
+  if (!b) return RBE_ERR_OOM;
+  b->h.assign(handles, handles + n);
+  b->stream = (cudaStream_t)cuda_stream;
+  b->br.assign(n, nullptr);
+  b->ev.assign(n, nullptr);
+  bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int r = 0; r < n && ok; ++r)
+    ok = cudaStreamCreateWithFlags(&b->br[r], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev[r], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    batch_free(b);
+    return RBE_ERR_CUDA;
+  }
+  *out = b;
+  return RBE_OK;
+}
+
+int rbe_batch_step(rbe_batch b, int nsteps) {
+  if (!b || nsteps < 0) return RBE_ERR_INVALID;
+  if (nsteps == 0) return RBE_OK;
+  // initial forces of every replica on its own stream, then order the batch stream after them
+  for (auto h : b->h) {
+    if (!h->have_forces) {
+      int rc = forces_common(h, h->step, false);
+      if (rc != RBE_OK) return rc;
+    }
+    RBE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  for (int k = 0; k < 2; ++k)
+    if (!b->graph[k]) {
+      int rc = batch_capture(b, (b->phase + k) & 1, &b->graph[k]);
+      if (rc != RBE_OK) return rc;
+    }
+  for (int s = 0; s < nsteps; ++s) {
+    RBE_CUDA_TRY(cudaGraphLaunch(b->graph[b->phase], b->stream));
+    b->phase ^= 1;
+    for (auto h : b->h) {
+      h->cur = 1 - h->cur;
+      h->step += 1;
+      h->have_forces = true;
+    }
+  }
+  return RBE_OK;
+}
+
+int rbe_batch_destroy(rbe_batch b) {
+  if (!b) return RBE_OK;
+  cudaStreamSynchronize(b->stream);
+  return batch_free(b);
+}
+
 int rbe_check_device(rbe_handle h) {
   if (!h) return RBE_ERR_INVALID;
   return read_device_flags(*h);
