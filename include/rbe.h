@@ -179,6 +179,19 @@ int rbe_set_profiling(rbe_handle h, int enable);
  * or Verlet step, and the number of kernels one Verlet step launches. Synchronises. */
 int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kernels_per_step);
 
+/* Tunables of the launch shapes (none changes results beyond FP32 rounding order):
+ *  RBE_TUNE_PAIR_TEST16  1: packed half-precision candidate pre-test in the cell-list pair
+ *                        kernel (exact decision still at evaluation), 0: FP32 pre-test
+ *  RBE_TUNE_SF_TILE      particles per block tile of the structure factor (32..1024, x32) */
+enum { RBE_TUNE_PAIR_TEST16 = 0, RBE_TUNE_SF_TILE = 1 };
+int rbe_set_tuning(rbe_handle h, int key, int value);
+int rbe_get_tuning(rbe_handle h, int key, int *value);
+
+/* Autotuner: times each candidate setting of the tunables above on the handle's own system
+ * (force evaluations, CUDA events, `reps` repetitions each) and keeps the fastest.
+ * Discards the captured step graph. Writes the chosen values to chosen[2] (nullable). */
+int rbe_autotune(rbe_handle h, int reps, int *chosen);
+
 /* Bytes of device memory held by the handle. */
 int rbe_get_memory(rbe_handle h, int64_t *bytes);
 

@@ -21,6 +21,7 @@ RBE_OK = 0
 PRECISION = {"fp32_comp": 0, "fp32": 1, "fp64": 2}
 ENERGY_KEYS = ("real", "lj", "kspace", "self", "total", "kinetic")
 VIRIAL_KEYS = ("real", "lj", "kspace", "total")
+TUNABLES = {"pair_test16": 0, "sf_tile": 1}
 PHASES = ("kick_drift", "bin", "sample", "sf", "pair", "pair2", "gather", "tail")
 
 
@@ -84,6 +85,9 @@ def lib(build_if_missing: bool = False):
     L.rbe_batch_create.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p), _vp]
     L.rbe_batch_step.argtypes = [ct.c_void_p, ct.c_int]
     L.rbe_batch_destroy.argtypes = [ct.c_void_p]
+    L.rbe_set_tuning.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
+    L.rbe_get_tuning.argtypes = [ct.c_void_p, ct.c_int, _vp]
+    L.rbe_autotune.argtypes = [ct.c_void_p, ct.c_int, _vp]
     L.rbe_structure_factor_noalloc.argtypes = [_vp, _vp, ct.c_int64, _vp, ct.c_int, _vp, _vp]
     L.rbe_destroy.argtypes = [h]
     L.rbe_error_string.argtypes = [ct.c_int]
@@ -282,6 +286,19 @@ class RBE:
         k = ct.c_int64()
         _check(lib().rbe_get_profile(self._h, None, ct.addressof(k)), "rbe_get_profile")
         return k.value
+
+    def set_tuning(self, key: str, value: int):
+        _check(lib().rbe_set_tuning(self._h, TUNABLES[key], int(value)), "rbe_set_tuning")
+
+    def get_tuning(self, key: str) -> int:
+        v = ct.c_int()
+        _check(lib().rbe_get_tuning(self._h, TUNABLES[key], ct.addressof(v)), "rbe_get_tuning")
+        return v.value
+
+    def autotune(self, reps: int = 3) -> dict:
+        ch = np.zeros(2, np.int32)
+        _check(lib().rbe_autotune(self._h, reps, ch.ctypes.data), "rbe_autotune")
+        return {"pair_test16": int(ch[0]), "sf_tile": int(ch[1])}
 
     def memory_bytes(self) -> int:
         b = ct.c_int64()

@@ -30,12 +30,15 @@ namespace rbe {
 
 constexpr int kMaxRows = 49;            // (2R+1)^2 stencil rows for R <= 3
 constexpr int kMaxSeg = 2 * kMaxRows;   // a row wraps into at most two runs of cells
+constexpr int kWin = 4;                 // chunks of 32 candidates staged per window
 
-template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP>
+template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16>
 __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a) {
-  __shared__ float4 stage[kPairWarps][32];
-  __shared__ int32_t stage_j[kPairWarps][32];
-  __shared__ int32_t list[kPairWarps][kListK][32];
+  __shared__ float4 stage[kPairWarps][kWin][T16 ? 1 : 32];     // FP32 test coordinates
+  __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
+  __shared__ int4 stage_d[kPairWarps][kWin][32];               // exact integer frame coords, type
+  __shared__ float stage_q[kPairWarps][kWin][32];
+  __shared__ int32_t stage_j[kPairWarps][kWin][32];
   __shared__ int32_t seg_beg[kPairWarps][kMaxSeg];
   __shared__ int32_t seg_pre[kPairWarps][kMaxSeg + 1];
   __shared__ double wred[kPairWarps][NQ_PAIR];
@@ -61,25 +64,14 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
     const int ti = (MULTI && valid) ? a.set.type[i] : 0;
     const int cx = cell_of(sxi, n0), cy = cell_of(syi, n1), cz = cell_of(szi, n2);
     const float rc2_hi = a.pc.rc2_hi;
-    int cnt = 0;
-    auto flush = [&]() {
-      const int maxc = __reduce_max_sync(FULL, cnt);
-      for (int t = 0; t < maxc; ++t) {
-        if (t < cnt) {
-          const int64_t j = list[wid][t][lane];
-          if (j != i) pair_body<real, LJ, COUL, MULTI>(a, tab, sxi, syi, szi, qi, ti, j, acc);
-        }
-      }
-      cnt = 0;
-      __syncwarp();
-    };
     const int ny = 2 * R1 + 1, nrows = ny * (2 * R2 + 1);
     unsigned remaining = __ballot_sync(FULL, valid);
     while (remaining) {
       const int leader = __ffs(remaining) - 1;
       const int gy = __shfl_sync(FULL, cy, leader), gz = __shfl_sync(FULL, cz, leader);
       const int gx0 = __shfl_sync(FULL, cx, leader);
-      const bool in = valid && cy == gy && cz == gz && (WRAP || cx - gx0 < a.smax) &&
+      const bool in = valid && cy == gy && cz == gz &&
+                      (WRAP || cx - gx0 < (T16 ? a.smax16 : a.smax)) &&
                       ((remaining >> lane) & 1u);
       const unsigned gmask = __ballot_sync(FULL, in);
       remaining &= ~gmask;
@@ -88,9 +80,15 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
       const uint32_t ox = __shfl_sync(FULL, sxi, leader);
       const uint32_t oy = __shfl_sync(FULL, syi, leader);
       const uint32_t oz = __shfl_sync(FULL, szi, leader);
-      const float xi = (float)(int)(sxi - ox) * a.pc.h[0];
-      const float yi = (float)(int)(syi - oy) * a.pc.h[1];
-      const float zi = (float)(int)(szi - oz) * a.pc.h[2];
+      // integer frame coordinates relative to the leader (exact); float / half test copies
+      const int dxi = (int)(sxi - ox), dyi = (int)(syi - oy), dzi = (int)(szi - oz);
+      const float xi = (float)dxi * a.pc.h[0];
+      const float yi = (float)dyi * a.pc.h[1];
+      const float zi = (float)dzi * a.pc.h[2];
+      const __half2 xi2 = __float2half2_rn(xi * a.scale16);
+      const __half2 yi2 = __float2half2_rn(yi * a.scale16);
+      const __half2 zi2 = __float2half2_rn(zi * a.scale16);
+      const __half2 thr2 = __float2half2_rn(66.5f);
       const int span = cxhi - cxlo + 2 * R0 + 1;
       // 1. Runs of candidates: one lane per stencil row (dz, dy) loads the row's cell
       //    range(s) in parallel; a warp scan turns the run lengths into offsets.
@@ -137,49 +135,108 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
       if (lane == 0) seg_pre[wid][2 * nrows] = carry;
       __syncwarp();
       const int T = carry;
-      // 2. Candidates in full chunks of 32 across run boundaries: stage, bitmask test,
-      //    append the hits to the per-lane list.
+      // 2. Windows of kWin chunks of 32 candidates: stage (one candidate per lane and
+      //    chunk), test every staged candidate against the lane's own i (bit masks), then
+      //    evaluate the hits directly from the staged exact coordinates.
       int sg = 0;
-      for (int base = 0; base < T; base += 32) {
-        if (__any_sync(FULL, cnt > kListK - 32)) flush();
-        const int c = base + lane;
-        int s = sg;
-        if (c < T) {
-          while (seg_pre[wid][s + 1] <= c) ++s;
-          const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
-          stage[wid][lane] = make_float4((float)(int)(a.set.sx[j] - ox) * a.pc.h[0],
-                                         (float)(int)(a.set.sy[j] - oy) * a.pc.h[1],
-                                         (float)(int)(a.set.sz[j] - oz) * a.pc.h[2], 0.f);
-          stage_j[wid][lane] = (int32_t)j;
-        }
-        sg = __shfl_sync(FULL, s, 31);
-        __syncwarp();
-        uint32_t mask = 0u;
+      for (int base = 0; base < T; base += 32 * kWin) {
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          const float4 p = stage[wid][t];
-          float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
-          if (WRAP) {
-            ddx = fold(ddx, a.L[0], a.invL[0]);
-            ddy = fold(ddy, a.L[1], a.invL[1]);
-            ddz = fold(ddz, a.L[2], a.invL[2]);
+        for (int w = 0; w < kWin; ++w) {
+          const int c = base + 32 * w + lane;
+          int s = sg;
+          if (c < T) {
+            while (seg_pre[wid][s + 1] <= c) ++s;
+            const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
+            const int dxj = (int)(a.set.sx[j] - ox), dyj = (int)(a.set.sy[j] - oy),
+                      dzj = (int)(a.set.sz[j] - oz);
+            const float fx = (float)dxj * a.pc.h[0];
+            const float fy = (float)dyj * a.pc.h[1];
+            const float fz = (float)dzj * a.pc.h[2];
+            if (T16) {
+              __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane >> 1]);
+              const int o = lane & 1;
+              h[o] = __float2half_rn(fx * a.scale16);
+              h[2 + o] = __float2half_rn(fy * a.scale16);
+              h[4 + o] = __float2half_rn(fz * a.scale16);
+            } else {
+              stage[wid][w][lane] = make_float4(fx, fy, fz, 0.f);
+            }
+            stage_d[wid][w][lane] = make_int4(dxj, dyj, dzj, MULTI ? a.set.type[j] : 0);
+            if (COUL) stage_q[wid][w][lane] = a.set.qf[j];
+            stage_j[wid][w][lane] = (int32_t)j;
           }
-          const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-          mask |= (r2 < rc2_hi) ? (1u << t) : 0u;
+          sg = __shfl_sync(FULL, s, 31);
         }
-        const int nj = min(32, T - base);
-        if (nj < 32) mask &= (1u << nj) - 1u;
-        if (!in) mask = 0u;
-        while (mask) {
-          const int t = __ffs(mask) - 1;
-          mask &= mask - 1u;
-          list[wid][cnt][lane] = stage_j[wid][t];
-          ++cnt;
+        __syncwarp();
+        uint32_t m[kWin];
+#pragma unroll
+        for (int w = 0; w < kWin; ++w) {
+          const int nj = max(0, min(32, T - base - 32 * w));
+          uint32_t mask = 0u;
+          if (nj > 0) {
+            if (T16) {
+              // bit p: candidate 2p, bit 16 + p: candidate 2p + 1
+#pragma unroll
+              for (int pp = 0; pp < 16; ++pp) {
+                const uint4 v = stage16[wid][w][pp];
+                const __half2 dx2 = __hsub2(xi2, *reinterpret_cast<const __half2 *>(&v.x));
+                const __half2 dy2 = __hsub2(yi2, *reinterpret_cast<const __half2 *>(&v.y));
+                const __half2 dz2 = __hsub2(zi2, *reinterpret_cast<const __half2 *>(&v.z));
+                const __half2 r2 = __hfma2(dx2, dx2, __hfma2(dy2, dy2, __hmul2(dz2, dz2)));
+                mask |= (__hlt2_mask(r2, thr2) & 0x00010001u) << pp;
+              }
+              const uint32_t ve = (1u << ((nj + 1) >> 1)) - 1u;
+              const uint32_t vo = nj >= 32 ? 0xFFFF0000u : ((1u << (nj >> 1)) - 1u) << 16;
+              mask &= ve | vo;
+            } else {
+#pragma unroll
+              for (int tt = 0; tt < 32; ++tt) {
+                const float4 p = stage[wid][w][tt];
+                float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
+                if (WRAP) {
+                  ddx = fold(ddx, a.L[0], a.invL[0]);
+                  ddy = fold(ddy, a.L[1], a.invL[1]);
+                  ddz = fold(ddz, a.L[2], a.invL[2]);
+                }
+                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                mask |= (r2 < rc2_hi) ? (1u << tt) : 0u;
+              }
+              if (nj < 32) mask &= (1u << nj) - 1u;
+            }
+          }
+          m[w] = in ? mask : 0u;
+        }
+        // evaluate the hits of the window (each lane its own, in candidate order); idle
+        // lanes run a masked dummy so the loop body has no divergent branch
+        uint64_t mA = (uint64_t)m[0] | ((uint64_t)m[1] << 32);
+        uint64_t mB = (uint64_t)m[2] | ((uint64_t)m[3] << 32);
+        const int4 *sd = &stage_d[wid][0][0];
+        const float *sq = &stage_q[wid][0][0];
+        const int32_t *sj = &stage_j[wid][0][0];
+        while (__any_sync(FULL, (mA | mB) != 0ull)) {
+          const bool useA = mA != 0ull;
+          const uint64_t bits = useA ? mA : mB;
+          const bool act = bits != 0ull;
+          const int b = act ? __ffsll((long long)bits) - 1 : 0;
+          const uint64_t rest = bits & (bits - 1ull);
+          mA = useA ? rest : mA;
+          mB = useA ? mB : rest;
+          const int wb = (useA ? 0 : 64) + b;
+          const int bb = wb & 31;
+          const int tt = T16 ? (((bb & 15) << 1) | (bb >> 4)) : bb;
+          const int slot = (wb & ~31) + tt;
+          const int32_t j = sj[slot];
+          const int4 d = sd[slot];
+          real qj = (real)0;
+          if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[j] : (real)sq[slot];
+          pair_eval_masked<real, LJ, COUL, MULTI>(
+              a, tab, act && j != (int32_t)i, (int)((uint32_t)dxi - (uint32_t)d.x),
+              (int)((uint32_t)dyi - (uint32_t)d.y), (int)((uint32_t)dzi - (uint32_t)d.z), qi,
+              ti, qj, d.w, acc);
         }
         __syncwarp();
       }
     }
-    flush();
     if (valid) {
       const int64_t o = a.set.map ? (int64_t)a.set.map[i] : i;
       const int64_t S = a.Fstride;
@@ -215,12 +272,28 @@ static void launch_one(const PairArgs &a, int64_t n, bool multi, bool wrap, cuda
   if (blocks == 0) return;
   const dim3 g(blocks), b(kPairWarps * 32);
   if (wrap) {
-    if (multi) pair_kernel<real, LJ, COUL, true, true><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, true><<<g, b, 0, st>>>(a);
+    if (multi) pair_kernel<real, LJ, COUL, true, true, false><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, true, false><<<g, b, 0, st>>>(a);
+  } else if (a.smax16 > 0) {
+    if (multi) pair_kernel<real, LJ, COUL, true, false, true><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, false, true><<<g, b, 0, st>>>(a);
   } else {
-    if (multi) pair_kernel<real, LJ, COUL, true, false><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, false><<<g, b, 0, st>>>(a);
+    if (multi) pair_kernel<real, LJ, COUL, true, false, false><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, false, false><<<g, b, 0, st>>>(a);
   }
+}
+
+// Group x-extent (cells) for the half-precision test: every frame coordinate of a group and
+// its candidates stays below 64 scaled units (r_c = 8), i.e. 8 r_c in length; 0 disables
+// the half test (the FP32 test is used).
+int frame_span_cells_half(const Ctx &c, int smax) {
+  if (smax < 1) return 0;
+  const double lim = 8.0 * c.rc * (1.0 - 1e-6);
+  for (int d = 1; d < 3; ++d)
+    if ((2 * c.grid.R[d] + 2) * (c.box[d] / c.grid.n[d]) >= lim) return 0;
+  const double ax = c.box[0] / c.grid.n[0];
+  const int s = (int)std::floor(lim / ax) - 2 * c.grid.R[0] - 1;
+  return s >= 1 ? std::min(s, smax) : 0;
 }
 
 // Largest x-extent (in cells) of a group whose leader frame stays a valid minimum image;
@@ -257,6 +330,8 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   a.nbr = want_counts ? c.nbr : nullptr;
   a.smax = frame_span_cells(c);
   a.comp = c.precision == RBE_FP32_COMP;
+  a.scale16 = (float)(8.0 / c.rc);
+  a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax) : 0;
   const bool wrap = a.smax == 0;
   for (int d = 0; d < 3; ++d) {
     a.L[d] = (float)c.box[d];

@@ -1,6 +1,8 @@
 // pair_common.cuh -- pair interaction of the real-space part (Eqs. F_i, G_short, LJ) shared
 // by the cell-list kernel and the random batch list kernel.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "rbe_internal.cuh"
 
 namespace rbe {
@@ -29,6 +31,12 @@ struct PairArgs {
   int smax;
   float L[3], invL[3];
   int comp;  // compensated (Kahan) Coulomb energy and virial sums
+  // Packed half-precision candidate test: frame coordinates scaled by scale16 = 8 / r_c
+  // (the cutoff maps to 8), compared with thr16 = 66.5 > 64 + the worst rounding of the
+  // test (2.06 for |coordinate| < 64 scaled units, which smax16 guarantees). No true
+  // neighbour is rejected; the exact decision is taken again when the pair is evaluated.
+  float scale16;
+  int smax16;
 };
 
 // Fold a coordinate difference into [-L/2, L/2) (only the small-box variants use it).
@@ -63,15 +71,14 @@ __device__ __forceinline__ double exact_r2(const PairConst &pc, int dsx, int dsy
 // Pair force, energies and virial of one pair that is inside the cutoff (Eqs. F_i,
 // G_short, LJ), added to acc.
 template <typename real, bool LJ, bool COUL, bool MULTI>
-__device__ __forceinline__ void pair_force(const PairArgs &a, const LJTable *tab, real dx,
-                                           real dy, real dz, real r2, real qi, int ti,
-                                           int64_t j, PairAcc<real> &acc) {
+__device__ __forceinline__ void pair_force_v(const PairArgs &a, const LJTable *tab, real dx,
+                                             real dy, real dz, real r2, real qi, int ti,
+                                             real qj, int tj, PairAcc<real> &acc) {
   const PairConst &pc = a.pc;
   real g = (real)0;
   if (LJ) {
     real e24, e4, s2;
     if (MULTI) {
-      const int tj = a.set.type[j];
       const int pt = ti * tab->nt + tj;
       if (sizeof(real) == 8) { e24 = (real)tab->eps24d[pt]; e4 = (real)tab->eps4d[pt]; s2 = (real)tab->sig2d[pt]; }
       else { e24 = (real)tab->eps24[pt]; e4 = (real)tab->eps4[pt]; s2 = (real)tab->sig2[pt]; }
@@ -90,9 +97,6 @@ __device__ __forceinline__ void pair_force(const PairArgs &a, const LJTable *tab
     acc.wlj += gl * r2;
   }
   if (COUL) {
-    real qj;
-    if (sizeof(real) == 8) qj = (real)a.set.qd[j];
-    else qj = (real)a.set.qf[j];
     const real qq = qi * qj;
     if (qq != (real)0) {
       real r, rinv, erfcv, expv;
@@ -126,6 +130,135 @@ __device__ __forceinline__ void pair_force(const PairArgs &a, const LJTable *tab
   acc.fx += g * dx;
   acc.fy += g * dy;
   acc.fz += g * dz;
+}
+
+// Same, with the charge and type of j read from the set.
+template <typename real, bool LJ, bool COUL, bool MULTI>
+__device__ __forceinline__ void pair_force(const PairArgs &a, const LJTable *tab, real dx,
+                                           real dy, real dz, real r2, real qi, int ti,
+                                           int64_t j, PairAcc<real> &acc) {
+  real qj = (real)0;
+  if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[j] : (real)a.set.qf[j];
+  const int tj = MULTI ? a.set.type[j] : 0;
+  pair_force_v<real, LJ, COUL, MULTI>(a, tab, dx, dy, dz, r2, qi, ti, qj, tj, acc);
+}
+
+// Branch-light evaluation for the cell-list kernel: `act` says whether this lane holds a
+// candidate pair at all (idle lanes compute a masked dummy). The cutoff decision is exact:
+// FP32 outside the +-1e-5 band around r_c^2, the oracle's FP64 expression inside it (a
+// rare, divergent branch); in the FP64 form always the FP64 expression. Every
+// contribution is multiplied by the 0/1 decision, so no early return diverges the warp.
+template <typename real, bool LJ, bool COUL, bool MULTI>
+__device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTable *tab,
+                                                 bool act, int dsx, int dsy, int dsz, real qi,
+                                                 int ti, real qj, int tj,
+                                                 PairAcc<real> &acc) {
+  const PairConst &pc = a.pc;
+  real dx, dy, dz, r2;
+  bool inside;
+  if (sizeof(real) == 8) {
+    dx = (real)__dmul_rn((double)dsx, pc.hd[0]);
+    dy = (real)__dmul_rn((double)dsy, pc.hd[1]);
+    dz = (real)__dmul_rn((double)dsz, pc.hd[2]);
+    r2 = (real)__dadd_rn(__dadd_rn(__dmul_rn((double)dx, (double)dx),
+                                   __dmul_rn((double)dy, (double)dy)),
+                         __dmul_rn((double)dz, (double)dz));
+    inside = act && (double)r2 <= pc.rc2d;
+  } else {
+    dx = (real)((float)dsx * pc.h[0]);
+    dy = (real)((float)dsy * pc.h[1]);
+    dz = (real)((float)dsz * pc.h[2]);
+    r2 = dx * dx + dy * dy + dz * dz;
+    inside = act && (float)r2 < pc.rc2_lo;
+    const bool band = act && (float)r2 >= pc.rc2_lo && (float)r2 <= pc.rc2_hi;
+    if (band) inside = exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d;
+  }
+  acc.nbr += inside ? 1 : 0;
+  const real on = inside ? (real)1 : (real)0;
+  const real r2s = inside ? r2 : (real)1;  // keeps idle and rejected lanes finite
+  real g = (real)0;
+  if (LJ) {
+    real e24, e4, s2;
+    if (MULTI) {
+      const int pt = ti * tab->nt + tj;
+      if (sizeof(real) == 8) { e24 = (real)tab->eps24d[pt]; e4 = (real)tab->eps4d[pt]; s2 = (real)tab->sig2d[pt]; }
+      else { e24 = (real)tab->eps24[pt]; e4 = (real)tab->eps4[pt]; s2 = (real)tab->sig2[pt]; }
+    } else {
+      if (sizeof(real) == 8) { e24 = (real)a.eps24d; e4 = (real)a.eps4d; s2 = (real)a.sig2d; }
+      else { e24 = (real)a.eps24; e4 = (real)a.eps4; s2 = (real)a.sig2; }
+    }
+    real rinv2;
+    if (sizeof(real) == 8) rinv2 = (real)(1.0 / (double)r2s);
+    else rinv2 = (real)__frcp_rn((float)r2s);
+    const real sr2 = s2 * rinv2;
+    const real sr6 = sr2 * sr2 * sr2;
+    const real gl = on * e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);
+    g += gl;
+    acc.ulj += on * e4 * sr6 * (sr6 - (real)1);
+    acc.wlj += gl * r2s;
+  }
+  if (COUL) {
+    const real qq = qi * qj;
+    if (inside && qq != (real)0) {
+      real r, rinv, erfcv, expv;
+      if (sizeof(real) == 8) {
+        r = (real)sqrt((double)r2);
+        rinv = (real)1 / r;
+        erfcv = (real)erfc(pc.sqrt_alpha_d * (double)r);
+        expv = (real)exp(-pc.alpha_d * (double)r2);
+      } else {
+        r = (real)sqrtf((float)r2);
+        rinv = (real)__frcp_rn((float)r);
+        erfcv = (real)erfcf(pc.sqrt_alpha * (float)r);
+        expv = (real)expf(-pc.alpha * (float)r2);
+      }
+      const real Cqq = (sizeof(real) == 8 ? (real)pc.C_d : (real)pc.C) * qq;
+      const real tsp = sizeof(real) == 8 ? (real)pc.two_sqrt_alpha_over_sqrt_pi_d
+                                         : (real)pc.two_sqrt_alpha_over_sqrt_pi;
+      const real rinv2 = rinv * rinv;
+      const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
+      g += gc;
+      if (a.comp) {
+        kahan_add(acc.uc, acc.cuc, Cqq * erfcv * rinv);
+        kahan_add(acc.wc, acc.cwc, gc * r2);
+      } else {
+        acc.uc += Cqq * erfcv * rinv;
+        acc.wc += gc * r2;
+      }
+    }
+  }
+  acc.fx += g * dx;
+  acc.fy += g * dy;
+  acc.fz += g * dz;
+}
+
+// Exact cutoff decision from the integer displacement ds = s_i - s_j (mod 2^32, the
+// minimum image), then the pair force. FP32 decides outside the +-1e-5 band around r_c^2;
+// inside it (and always in the FP64 form) the oracle's FP64 expression decides.
+template <typename real, bool LJ, bool COUL, bool MULTI>
+__device__ __forceinline__ void pair_body_ds(const PairArgs &a, const LJTable *tab, int dsx,
+                                             int dsy, int dsz, real qi, int ti, real qj,
+                                             int tj, PairAcc<real> &acc) {
+  const PairConst &pc = a.pc;
+  real dx, dy, dz, r2;
+  if (sizeof(real) == 8) {
+    dx = (real)__dmul_rn((double)dsx, pc.hd[0]);
+    dy = (real)__dmul_rn((double)dsy, pc.hd[1]);
+    dz = (real)__dmul_rn((double)dsz, pc.hd[2]);
+    r2 = (real)__dadd_rn(__dadd_rn(__dmul_rn((double)dx, (double)dx),
+                                   __dmul_rn((double)dy, (double)dy)),
+                         __dmul_rn((double)dz, (double)dz));
+    if (!((double)r2 <= pc.rc2d)) return;
+  } else {
+    dx = (real)((float)dsx * pc.h[0]);
+    dy = (real)((float)dsy * pc.h[1]);
+    dz = (real)((float)dsz * pc.h[2]);
+    r2 = dx * dx + dy * dy + dz * dz;
+    if ((float)r2 > pc.rc2_hi) return;
+    if ((float)r2 >= pc.rc2_lo && !(exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d)) return;
+  }
+  acc.nbr += 1;
+  pair_force_v<real, LJ, COUL, MULTI>(a, tab, dx, dy, dz, r2, qi, ti, qj, tj, acc);
 }
 
 

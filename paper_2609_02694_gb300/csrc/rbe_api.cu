@@ -374,6 +374,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
     tile = std::max<int64_t>(32, std::min<int64_t>(512, ((tile + 31) / 32) * 32));
     c.sf_tile = (int)tile;
     c.sf_nblk_p = (int)std::max<int64_t>(1, (Nq + tile - 1) / tile);
+    c.sf_part_blocks = std::max<int64_t>(1, (Nq + 31) / 32);  // room for the smallest tile
   }
 
   // reductions layout
@@ -417,7 +418,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   rc |= dalloc(c, &c.m, c.P);
   rc |= dalloc(c, &c.kcf, c.P);
   rc |= dalloc(c, &c.kcd, c.P);
-  rc |= dalloc(c, &c.sf_part, (int64_t)c.sf_nblk_p * c.P * 2);
+  rc |= dalloc(c, &c.sf_part, c.sf_part_blocks * c.P * 2);
   rc |= dalloc(c, &c.rho, c.P);
   rc |= dalloc(c, &c.abf, c.P);
   rc |= dalloc(c, &c.abd, c.P);
@@ -756,6 +757,110 @@ int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kps) {
       phase_ms[k] = ms;
     }
   }
+  return RBE_OK;
+}
+
+static void drop_graphs(Ctx &c) {
+  for (int b = 0; b < 2; ++b)
+    if (c.graph[b]) {
+      cudaGraphExecDestroy(c.graph[b]);
+      c.graph[b] = nullptr;
+    }
+}
+
+// Structure-factor launch shape for a tile of `tile` particles per block.
+static void set_sf_tile(Ctx &c, int64_t tile) {
+  c.sf_tile = (int)tile;
+  c.sf_nblk_p = (int)std::max<int64_t>(1, (c.Nq + tile - 1) / tile);
+}
+
+int rbe_set_tuning(rbe_handle h, int key, int value) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  if (key == RBE_TUNE_PAIR_TEST16) {
+    if (value != 0 && value != 1) return RBE_ERR_INVALID;
+    c.pair_test16 = value != 0;
+  } else if (key == RBE_TUNE_SF_TILE) {
+    if (value < 32 || value > 1024 || value % 32) return RBE_ERR_INVALID;
+    // the partial buffer was sized for the initial tile; smaller tiles need more blocks
+    const int64_t nblk = std::max<int64_t>(1, (c.Nq + value - 1) / value);
+    if (nblk > c.sf_part_blocks) return RBE_ERR_INVALID;
+    set_sf_tile(c, value);
+  } else {
+    return RBE_ERR_INVALID;
+  }
+  drop_graphs(c);
+  return RBE_OK;
+}
+
+int rbe_get_tuning(rbe_handle h, int key, int *value) {
+  if (!h || !value) return RBE_ERR_INVALID;
+  if (key == RBE_TUNE_PAIR_TEST16) *value = h->pair_test16 ? 1 : 0;
+  else if (key == RBE_TUNE_SF_TILE) *value = h->sf_tile;
+  else return RBE_ERR_INVALID;
+  return RBE_OK;
+}
+
+static int time_forces(Ctx &c, int reps, float *ms_out) {
+  cudaEvent_t e0, e1;
+  RBE_CUDA_TRY(cudaEventCreate(&e0));
+  RBE_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = force_pipeline(c, false);  // warm
+  RBE_CUDA_TRY(cudaEventRecord(e0, c.stream));
+  for (int r = 0; r < reps && rc == RBE_OK; ++r) rc = force_pipeline(c, false);
+  RBE_CUDA_TRY(cudaEventRecord(e1, c.stream));
+  RBE_CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms;
+  return rc;
+}
+
+int rbe_autotune(rbe_handle h, int reps, int *chosen) {
+  if (!h || reps < 1) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  const bool saved_timing = c.timing;
+  c.timing = false;
+  RBE_CUDA_TRY(launch_set_step(c, c.step));
+  float best = 0.f;
+  int best16 = c.pair_test16 ? 1 : 0;
+  for (int v = 0; v <= 1; ++v) {
+    c.pair_test16 = v != 0;
+    float ms = 0.f;
+    int rc = time_forces(c, reps, &ms);
+    if (rc != RBE_OK) { c.timing = saved_timing; return rc; }
+    if (v == 0 || ms < best) { best = ms; best16 = v; }
+  }
+  c.pair_test16 = best16 != 0;
+  int best_tile = c.sf_tile;
+  best = 0.f;
+  bool first = true;
+  for (int tile = 32; tile <= 1024; tile *= 2) {
+    const int64_t nblk = std::max<int64_t>(1, (c.Nq + tile - 1) / tile);
+    if (nblk > c.sf_part_blocks) continue;
+    set_sf_tile(c, tile);
+    cudaEvent_t e0, e1;
+    RBE_CUDA_TRY(cudaEventCreate(&e0));
+    RBE_CUDA_TRY(cudaEventCreate(&e1));
+    RBE_CUDA_TRY(launch_structure_factor(c));
+    RBE_CUDA_TRY(cudaEventRecord(e0, c.stream));
+    for (int r = 0; r < reps; ++r) RBE_CUDA_TRY(launch_structure_factor(c));
+    RBE_CUDA_TRY(cudaEventRecord(e1, c.stream));
+    RBE_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (first || ms < best) { best = ms; best_tile = tile; first = false; }
+  }
+  set_sf_tile(c, best_tile);
+  c.timing = saved_timing;
+  drop_graphs(c);
+  c.have_forces = false;
+  if (chosen) { chosen[0] = best16; chosen[1] = best_tile; }
   return RBE_OK;
 }
 

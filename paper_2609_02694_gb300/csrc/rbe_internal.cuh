@@ -72,6 +72,7 @@ struct Ctx {
   double box[3] = {0, 0, 0};
   double alpha = 0, rc = 0, r_core = 0, C = 0, dt = 0, kappa = 0;
   int P = 0, p_rbl = 0, precision = RBE_FP32_COMP, nt = 1, sub = 2;
+  bool pair_test16 = true;  // packed half-precision candidate pre-test in the pair kernel
   uint64_t seed = 0;
   uint32_t replica = 0;
   bool rbl = false;
@@ -112,6 +113,7 @@ struct Ctx {
   double4 *kcd = nullptr;
   double *sf_part = nullptr; // sf blocks x P x 2
   int sf_tile = 256, sf_mb = 128, sf_nblk_p = 0, sf_nblk_m = 0;
+  int64_t sf_part_blocks = 0;  // capacity of sf_part in particle blocks
   double2 *rho = nullptr;
   float2 *abf = nullptr;     // (c Im rho, c Re rho)
   double2 *abd = nullptr;

@@ -314,3 +314,35 @@ def test_full_size_one_million_sampled(orc):
     Fk = -(sy.q[idx][:, None, None] * (c * im)[:, :, None] * k[None, :, :]).sum(1)
     Fo = rs["F"][idx] + Fk
     assert rel_l2(F[idx], Fo) < TOL_F32
+
+
+# -------------------------------------------------------------------------- tuning
+
+
+@pytest.mark.parametrize("test16", [0, 1])
+@pytest.mark.parametrize("skw", [dict(N=20000, density=0.1, frac_charged=0.1, seed=2),
+                                 dict(N=30000, density=0.05, frac_charged=0.6, seed=4)])
+def test_pair_pretest_variants_match_oracle(orc, test16, skw):
+    """Both candidate pre-tests (FP32, packed FP16x2) give the oracle's neighbour sets."""
+    sy = synth.make_system(**skw)
+    with handle(sy, 100) as h:
+        h.set_tuning("pair_test16", test16)
+        assert h.get_tuning("pair_test16") == test16
+        F, E, W = h.forces_f64(0)
+        m, S = h.sample_k(0)
+        nbr, _ = h.neighbor_counts()
+    ref = oracle_all(orc, sy, m, S)
+    assert np.array_equal(nbr, ref["nbr"])
+    assert rel_l2(F, ref["F"]) < TOL_F32
+
+
+def test_autotune_keeps_results(orc):
+    sy = synth.make_system(20000, density=0.1, frac_charged=0.1, seed=2)
+    with handle(sy, 200) as h:
+        chosen = h.autotune(2)
+        assert chosen["pair_test16"] in (0, 1) and chosen["sf_tile"] % 32 == 0
+        F, E, W = h.forces_f64(0)
+        m, S = h.sample_k(0)
+        h.step(3)
+    ref = oracle_all(orc, sy, m, S)
+    assert rel_l2(F, ref["F"]) < TOL_F32
