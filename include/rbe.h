@@ -46,7 +46,8 @@ enum {
   RBE_ERR_CUDA = -6,        /* a CUDA runtime error; the handle should be destroyed */
   RBE_ERR_SAMPLER = -7,     /* 64 redraws of a mode all gave k = 0 (device flag) */
   RBE_ERR_NONFINITE = -8,   /* a non-finite velocity or position update (device flag) */
-  RBE_ERR_STATE = -9        /* call not valid in this state (e.g. no forces computed yet) */
+  RBE_ERR_STATE = -9,       /* call not valid in this state (e.g. no forces computed yet) */
+  RBE_ERR_CAPACITY = -10    /* an RBL stencil (27 cells) held more than 6144 candidates */
 };
 
 enum {

@@ -15,8 +15,10 @@
 // cell's 27 neighbours together. Candidates are staged in shared memory in FP32
 // coordinates relative to the group leader. Membership is decided exactly: FP32 outside
 // a +-1e-5 band around r_core^2 and r_s^2, the FP64 oracle expression inside it.
-// Pass 1 counts #S_i and queues core pairs, which are evaluated from exact integer
-// displacements. Pass 2 walks the same order again and evaluates the drawn shell pairs.
+// Pass 1 classifies every candidate once in canonical order, evaluates the core pairs from
+// the staged exact integer displacements (branch-light), and keeps per lane the number of
+// shell members of each 32-candidate chunk. Pass 2 draws, sorts the draws, and re-walks
+// only the chunks that hold them (same classification) to evaluate the drawn pairs.
 // The mean-force correction is a fixed-order FP64 reduction followed by a subtraction.
 #include <climits>
 
@@ -26,6 +28,8 @@ namespace rbe {
 
 constexpr int kRblWarps = 4;
 constexpr int kRblMaxP = 32;
+constexpr int kRblWin = 4;          // chunks of 32 candidates per window
+constexpr int kRblMaxChunks = 192;  // candidates per group <= 6144 (27 cells)
 
 struct RblArgs {
   PairArgs pa;
@@ -37,29 +41,26 @@ struct RblArgs {
   const uint64_t *step;
   double *fsum_part;   // per block: sum of F~ (3 doubles)
   int32_t *ncore, *nshell, *partners;  // sorted order, nullable
+  int *err;
 };
 
-// 0: outside r_s, 1: core, 2: shell. Exact at both radii.
-__device__ __forceinline__ int rbl_classify(const RblArgs &a, float r2, uint32_t sxi, uint32_t syi,
-                                            uint32_t szi, int64_t j) {
+// Coarse FP32 classes with the exact FP64 decision inside the +-1e-5 bands of r_core^2 and
+// r_s^2: 0 outside, 1 core (r <= r_core), 2 shell (r_core < r <= r_s).
+__device__ __forceinline__ int rbl_class(const RblArgs &a, float r2, int dsx, int dsy, int dsz) {
   if (r2 < a.rcore2_lo) return 1;
   if (r2 > a.rs2_hi) return 0;
   if (r2 > a.rcore2_hi && r2 < a.rs2_lo) return 2;
-  const double e2 = exact_r2(a.pa.pc, (int)(sxi - a.pa.set.sx[j]), (int)(syi - a.pa.set.sy[j]),
-                             (int)(szi - a.pa.set.sz[j]));
+  const double e2 = exact_r2(a.pa.pc, dsx, dsy, dsz);
   if (e2 <= a.rcore2d) return 1;
   if (e2 <= a.rs2d) return 2;
   return 0;
 }
 
 template <typename real, bool COUL, bool MULTI>
-__device__ __forceinline__ void rbl_pair(const RblArgs &a, const LJTable *tab, uint32_t sxi,
-                                         uint32_t syi, uint32_t szi, real qi, int ti, int64_t j,
-                                         PairAcc<real> &acc) {
+__device__ __forceinline__ void rbl_pair_ds(const RblArgs &a, const LJTable *tab, int dsx,
+                                            int dsy, int dsz, real qi, int ti, real qj, int tj,
+                                            PairAcc<real> &acc) {
   const PairConst &pc = a.pa.pc;
-  const int dsx = (int)(sxi - a.pa.set.sx[j]);
-  const int dsy = (int)(syi - a.pa.set.sy[j]);
-  const int dsz = (int)(szi - a.pa.set.sz[j]);
   real dx, dy, dz;
   if (sizeof(real) == 8) {
     dx = (real)((double)dsx * pc.hd[0]); dy = (real)((double)dsy * pc.hd[1]); dz = (real)((double)dsz * pc.hd[2]);
@@ -67,13 +68,49 @@ __device__ __forceinline__ void rbl_pair(const RblArgs &a, const LJTable *tab, u
     dx = (real)((float)dsx * pc.h[0]); dy = (real)((float)dsy * pc.h[1]); dz = (real)((float)dsz * pc.h[2]);
   }
   const real r2 = dx * dx + dy * dy + dz * dz;
-  pair_force<real, true, COUL, MULTI>(a.pa, tab, dx, dy, dz, r2, qi, ti, j, acc);
+  pair_force_v<real, true, COUL, MULTI>(a.pa, tab, dx, dy, dz, r2, qi, ti, qj, tj, acc);
+}
+
+// Core or drawn-shell pair with a 0/1 activity mask (idle lanes compute a finite dummy).
+template <typename real, bool COUL, bool MULTI>
+__device__ __forceinline__ void rbl_pair_masked(const RblArgs &a, const LJTable *tab, bool act,
+                                                int dsx, int dsy, int dsz, real qi, int ti,
+                                                real qj, int tj, PairAcc<real> &acc) {
+  const PairConst &pc = a.pa.pc;
+  real dx, dy, dz;
+  if (sizeof(real) == 8) {
+    dx = (real)((double)dsx * pc.hd[0]); dy = (real)((double)dsy * pc.hd[1]); dz = (real)((double)dsz * pc.hd[2]);
+  } else {
+    dx = (real)((float)dsx * pc.h[0]); dy = (real)((float)dsy * pc.h[1]); dz = (real)((float)dsz * pc.h[2]);
+  }
+  const real r2 = dx * dx + dy * dy + dz * dz;
+  const real on = act ? (real)1 : (real)0;
+  const real r2s = act ? r2 : (real)1;
+  PairAcc<real> t;
+  t.fx = t.fy = t.fz = t.ulj = t.wlj = t.uc = t.wc = t.cuc = t.cwc = (real)0;
+  t.nbr = 0;
+  pair_force_v<real, true, COUL, MULTI>(a.pa, tab, dx * on, dy * on, dz * on, r2s, qi, ti,
+                                        act ? qj : (real)0, tj, t);
+  acc.fx += t.fx; acc.fy += t.fy; acc.fz += t.fz;
+  acc.ulj += on * t.ulj; acc.wlj += on * t.wlj;
+  if (a.pa.comp) {  // zero for idle lanes (q_j = 0)
+    kahan_add(acc.uc, acc.cuc, t.uc);
+    kahan_add(acc.wc, acc.cwc, t.wc);
+  } else {
+    acc.uc += t.uc;
+    acc.wc += t.wc;
+  }
 }
 
 template <typename real, bool COUL, bool MULTI, bool WRAP>
 __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
-  __shared__ float4 stage[kRblWarps][32];
-  __shared__ int32_t list[kRblWarps][kListK][32];
+  __shared__ float4 stage[kRblWarps][kRblWin][32];
+  __shared__ int4 stage_d[kRblWarps][kRblWin][32];
+  __shared__ float stage_q[kRblWarps][kRblWin][32];
+  __shared__ int32_t stage_j[kRblWarps][kRblWin][32];
+  __shared__ int32_t seg_beg[kRblWarps][27];
+  __shared__ int32_t seg_pre[kRblWarps][28];
+  __shared__ uint8_t ccount[kRblWarps][kRblMaxChunks][32];  // shell members per chunk, per lane
   __shared__ double wred[kRblWarps][NQ_PAIR + 3];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
@@ -99,14 +136,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
     const int ti = (MULTI && valid) ? S.type[i] : 0;
     const uint32_t idi = valid ? (uint32_t)a.id[i] : 0u;
     const int cx = cell_of(sxi, n0), cy = cell_of(syi, n1), cz = cell_of(szi, n2);
-    int ncore = 0, nsh = 0, cnt = 0;
-    auto flush = [&]() {
-      const int maxc = __reduce_max_sync(FULL, cnt);
-      for (int t = 0; t < maxc; ++t)
-        if (t < cnt) rbl_pair<real, COUL, MULTI>(a, tab, sxi, syi, szi, qi, ti, list[wid][t][lane], core);
-      cnt = 0;
-      __syncwarp();
-    };
+    int ncore = 0, nsh = 0;
     unsigned remaining = __ballot_sync(FULL, valid);
     while (remaining) {
       const int leader = __ffs(remaining) - 1;
@@ -116,90 +146,189 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
       remaining &= ~__ballot_sync(FULL, in);
       const uint32_t ox = __shfl_sync(FULL, sxi, leader), oy = __shfl_sync(FULL, syi, leader),
                      oz = __shfl_sync(FULL, szi, leader);
-      const float xi = (float)(int)(sxi - ox) * a.pa.pc.h[0];
-      const float yi = (float)(int)(syi - oy) * a.pa.pc.h[1];
-      const float zi = (float)(int)(szi - oz) * a.pa.pc.h[2];
-      // draws of pass 2, kept sorted by index (stable in t)
-      uint32_t idx[kRblMaxP];
-      int ord[kRblMaxP];
-      int ndraw = 0;
-      for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-          flush();
-          if (in) {
-            for (int t = 0; t < a.p; ++t)
-              if (a.partners) a.partners[i * a.p + t] = -1;
-            if (nsh > a.p) {
-              const uint32_t st = (uint32_t)(*a.step);
-              for (int t = 0; t < a.p; t += 4) {
-                const uint4 w = philox4x32_10(make_uint4(idi, (uint32_t)(t / 4), st, 1u), a.key);
-                const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-                for (int u = 0; u < 4 && t + u < a.p; ++u)
-                  idx[t + u] = (uint32_t)(((uint64_t)ww[u] * (uint64_t)nsh) >> 32);
+      const int dxi = (int)(sxi - ox), dyi = (int)(syi - oy), dzi = (int)(szi - oz);
+      const float xi = __fmul_rn((float)dxi, a.pa.pc.h[0]);
+      const float yi = __fmul_rn((float)dyi, a.pa.pc.h[1]);
+      const float zi = __fmul_rn((float)dzi, a.pa.pc.h[2]);
+      // the 27 neighbour cells in canonical (dz, dy, dx) order, one lane each
+      {
+        int b0 = 0, l0 = 0;
+        if (lane < 27) {
+          const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+          const int rx = ((gx + dx) % n0 + n0) % n0, ry = ((gy + dy) % n1 + n1) % n1,
+                    rz = ((gz + dz) % n2 + n2) % n2;
+          const int64_t cell = rx + (int64_t)n0 * (ry + (int64_t)n1 * rz);
+          b0 = S.cell_start[cell];
+          l0 = S.cell_start[cell + 1] - b0;
+        }
+        int incl = l0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += v;
+        }
+        if (lane < 27) {
+          seg_beg[wid][lane] = b0;
+          seg_pre[wid][lane] = incl - l0;
+        }
+        if (lane == 26) seg_pre[wid][27] = incl;
+      }
+      __syncwarp();
+      const int T = seg_pre[wid][27];
+      const int nchunks = (T + 31) / 32;
+      if (nchunks > kRblMaxChunks) {  // capacity of the per-lane chunk counts
+        if (lane == 0) atomicOr(a.err, ERRBIT_CAPACITY);
+        continue;
+      }
+      // ---- pass 1: classify every candidate in canonical order, evaluate the core pairs,
+      //      keep the number of shell members of each 32-candidate chunk
+      int sg = 0;
+      for (int base = 0; base < T; base += 32 * kRblWin) {
+#pragma unroll
+        for (int w = 0; w < kRblWin; ++w) {
+          const int c = base + 32 * w + lane;
+          int s = sg;
+          if (c < T) {
+            while (seg_pre[wid][s + 1] <= c) ++s;
+            const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
+            const int dxj = (int)(S.sx[j] - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
+            // products rounded explicitly: pass 2 recomputes them and must classify identically
+            stage[wid][w][lane] = make_float4(__fmul_rn((float)dxj, a.pa.pc.h[0]),
+                                              __fmul_rn((float)dyj, a.pa.pc.h[1]),
+                                              __fmul_rn((float)dzj, a.pa.pc.h[2]), 0.f);
+            stage_d[wid][w][lane] = make_int4(dxj, dyj, dzj, MULTI ? S.type[j] : 0);
+            if (COUL) stage_q[wid][w][lane] = S.qf[j];
+            stage_j[wid][w][lane] = (int32_t)j;
+          }
+          sg = __shfl_sync(FULL, s, 31);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int w = 0; w < kRblWin; ++w) {
+          const int nj = max(0, min(32, T - base - 32 * w));
+          uint32_t mcore = 0u, mshell = 0u, mamb = 0u;
+          if (nj > 0) {
+#pragma unroll
+            for (int tt = 0; tt < 32; ++tt) {
+              const float4 pj = stage[wid][w][tt];
+              float ddx = xi - pj.x, ddy = yi - pj.y, ddz = zi - pj.z;
+              if (WRAP) {
+                ddx = fold(ddx, a.pa.L[0], a.pa.invL[0]);
+                ddy = fold(ddy, a.pa.L[1], a.pa.invL[1]);
+                ddz = fold(ddz, a.pa.L[2], a.pa.invL[2]);
               }
-              ndraw = a.p;
-              for (int t = 0; t < ndraw; ++t) ord[t] = t;
-              for (int t = 1; t < ndraw; ++t) {  // insertion sort by idx, stable
-                const int v = ord[t];
-                int u = t - 1;
-                while (u >= 0 && idx[ord[u]] > idx[v]) { ord[u + 1] = ord[u]; --u; }
-                ord[u + 1] = v;
-              }
+              const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+              const uint32_t bit = 1u << tt;
+              mcore |= r2 < a.rcore2_lo ? bit : 0u;
+              mshell |= (r2 > a.rcore2_hi && r2 < a.rs2_lo) ? bit : 0u;
+              mamb |= ((r2 >= a.rcore2_lo && r2 <= a.rcore2_hi) ||
+                       (r2 >= a.rs2_lo && r2 <= a.rs2_hi)) ? bit : 0u;
             }
+            uint32_t vmask = nj >= 32 ? 0xFFFFFFFFu : ((1u << nj) - 1u);
+            if (!in) vmask = 0u;
+            mcore &= vmask; mshell &= vmask; mamb &= vmask;
+            while (mamb) {  // rare: exact decision inside the bands
+              const int tt = __ffs(mamb) - 1;
+              mamb &= mamb - 1u;
+              const int4 d = stage_d[wid][w][tt];
+              const int cls = rbl_class(a, a.rs2_hi, (int)((uint32_t)dxi - (uint32_t)d.x),
+                                        (int)((uint32_t)dyi - (uint32_t)d.y),
+                                        (int)((uint32_t)dzi - (uint32_t)d.z));
+              if (cls == 1) mcore |= 1u << tt;
+              if (cls == 2) mshell |= 1u << tt;
+            }
+          }
+          const int chunk = (base >> 5) + w;
+          if (chunk < nchunks) ccount[wid][chunk][lane] = (uint8_t)__popc(mshell);
+          nsh += __popc(mshell);
+          // core pairs, branch-light (the particle itself, r = 0, is skipped)
+          uint32_t bits = mcore;
+          while (__any_sync(FULL, bits != 0u)) {
+            const bool act = bits != 0u;
+            const int tt = act ? __ffs(bits) - 1 : 0;
+            bits &= bits - 1u;
+            const int32_t j = stage_j[wid][w][tt];
+            const bool use = act && j != (int32_t)i;
+            const int4 d = stage_d[wid][w][tt];
+            real qj = (real)0;
+            if (COUL) qj = sizeof(real) == 8 ? (use ? (real)S.qd[j] : (real)0) : (real)stage_q[wid][w][tt];
+            ncore += use ? 1 : 0;
+            rbl_pair_masked<real, COUL, MULTI>(a, tab, use, (int)((uint32_t)dxi - (uint32_t)d.x),
+                                               (int)((uint32_t)dyi - (uint32_t)d.y),
+                                               (int)((uint32_t)dzi - (uint32_t)d.z), qi, ti, qj,
+                                               d.w, core);
           }
         }
-        int kshell = 0, ptr = 0;
-        for (int dz = -1; dz <= 1; ++dz) {
-          const int rz = ((gz + dz) % n2 + n2) % n2;
-          for (int dy = -1; dy <= 1; ++dy) {
-            const int ry = ((gy + dy) % n1 + n1) % n1;
-            for (int dx = -1; dx <= 1; ++dx) {
-              const int rx = ((gx + dx) % n0 + n0) % n0;
-              const int64_t cell = rx + (int64_t)n0 * (ry + (int64_t)n1 * rz);
-              const int64_t j0 = S.cell_start[cell], j1 = S.cell_start[cell + 1];
-              for (int64_t base = j0; base < j1; base += 32) {
-                if (pass == 0 && __any_sync(FULL, cnt > kListK - 32)) flush();
-                const int64_t jj = base + lane;
-                if (jj < j1)
-                  stage[wid][lane] = make_float4((float)(int)(S.sx[jj] - ox) * a.pa.pc.h[0],
-                                                 (float)(int)(S.sy[jj] - oy) * a.pa.pc.h[1],
-                                                 (float)(int)(S.sz[jj] - oz) * a.pa.pc.h[2], 0.f);
-                __syncwarp();
-                const int nj = (int)min((int64_t)32, j1 - base);
-                for (int t = 0; t < nj; ++t) {
-                  const float4 pj = stage[wid][t];
-                  float ddx = xi - pj.x, ddy = yi - pj.y, ddz = zi - pj.z;
-                  if (WRAP) {
-                    ddx = fold(ddx, a.pa.L[0], a.pa.invL[0]);
-                    ddy = fold(ddy, a.pa.L[1], a.pa.invL[1]);
-                    ddz = fold(ddz, a.pa.L[2], a.pa.invL[2]);
-                  }
-                  const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                  const int64_t j = base + t;
-                  const int cls = (in && j != i && r2 <= a.rs2_hi) ? rbl_classify(a, r2, sxi, syi, szi, j) : 0;
-                  if (pass == 0) {
-                    list[wid][cnt][lane] = (int32_t)j;
-                    cnt += cls == 1 ? 1 : 0;
-                    ncore += cls == 1 ? 1 : 0;
-                    nsh += cls == 2 ? 1 : 0;
-                  } else if (cls == 2) {
-                    if (nsh <= a.p) {
-                      rbl_pair<real, COUL, MULTI>(a, tab, sxi, syi, szi, qi, ti, j, shell);
-                      if (a.partners) a.partners[i * a.p + kshell] = a.id[j];
-                    } else {
-                      while (ptr < ndraw && idx[ord[ptr]] == (uint32_t)kshell) {
-                        rbl_pair<real, COUL, MULTI>(a, tab, sxi, syi, szi, qi, ti, j, shell);
-                        if (a.partners) a.partners[i * a.p + ord[ptr]] = a.id[j];
-                        ++ptr;
-                      }
-                    }
-                    ++kshell;
-                  }
-                }
-                __syncwarp();
-              }
-            }
+        __syncwarp();
+      }
+      // ---- pass 2: the drawn shell partners (all of them when #S_i <= p)
+      if (in) {
+        uint32_t idx[kRblMaxP];
+        int ord[kRblMaxP];
+        int ndraw;
+        if (a.partners)
+          for (int t = 0; t < a.p; ++t) a.partners[i * a.p + t] = -1;
+        if (nsh > a.p) {
+          const uint32_t st = (uint32_t)(*a.step);
+          for (int t = 0; t < a.p; t += 4) {
+            const uint4 w4 = philox4x32_10(make_uint4(idi, (uint32_t)(t / 4), st, 1u), a.key);
+            const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+            for (int u = 0; u < 4 && t + u < a.p; ++u)
+              idx[t + u] = (uint32_t)(((uint64_t)ww[u] * (uint64_t)nsh) >> 32);
           }
+          ndraw = a.p;
+          for (int t = 0; t < ndraw; ++t) ord[t] = t;
+          for (int t = 1; t < ndraw; ++t) {  // insertion sort by index, stable in t
+            const int v = ord[t];
+            int u = t - 1;
+            while (u >= 0 && idx[ord[u]] > idx[v]) { ord[u + 1] = ord[u]; --u; }
+            ord[u + 1] = v;
+          }
+        } else {
+          ndraw = nsh;
+          for (int t = 0; t < ndraw; ++t) { idx[t] = (uint32_t)t; ord[t] = t; }
+        }
+        int ptr = 0, chunk = 0, before = 0;
+        while (ptr < ndraw) {
+          const uint32_t target = idx[ord[ptr]];
+          while (before + (int)ccount[wid][chunk][lane] <= (int)target) {
+            before += ccount[wid][chunk][lane];
+            ++chunk;
+          }
+          // walk this chunk's candidates with the classification of pass 1
+          int k = before;
+          int s = 0;
+          while (seg_pre[wid][s + 1] <= chunk * 32) ++s;  // run of the chunk's first candidate
+          for (int tt = 0; tt < 32 && ptr < ndraw; ++tt) {
+            const int c = chunk * 32 + tt;
+            if (c >= T) break;
+            while (seg_pre[wid][s + 1] <= c) ++s;
+            const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
+            const int dxj = (int)(S.sx[j] - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
+            float ddx = xi - __fmul_rn((float)dxj, a.pa.pc.h[0]),
+                  ddy = yi - __fmul_rn((float)dyj, a.pa.pc.h[1]),
+                  ddz = zi - __fmul_rn((float)dzj, a.pa.pc.h[2]);
+            if (WRAP) {
+              ddx = fold(ddx, a.pa.L[0], a.pa.invL[0]);
+              ddy = fold(ddy, a.pa.L[1], a.pa.invL[1]);
+              ddz = fold(ddz, a.pa.L[2], a.pa.invL[2]);
+            }
+            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            const int dsx = (int)((uint32_t)dxi - (uint32_t)dxj), dsy = (int)((uint32_t)dyi - (uint32_t)dyj),
+                      dsz = (int)((uint32_t)dzi - (uint32_t)dzj);
+            if (rbl_class(a, r2, dsx, dsy, dsz) != 2) continue;
+            while (ptr < ndraw && idx[ord[ptr]] == (uint32_t)k) {
+              real qj = (real)0;
+              if (COUL) qj = sizeof(real) == 8 ? (real)S.qd[j] : (real)S.qf[j];
+              rbl_pair_masked<real, COUL, MULTI>(a, tab, true, dsx, dsy, dsz, qi, ti, qj,
+                                                 MULTI ? S.type[j] : 0, shell);
+              if (a.partners) a.partners[i * a.p + ord[ptr]] = a.id[j];
+              ++ptr;
+            }
+            ++k;
+          }
+          before = k;
+          ++chunk;
         }
       }
     }
@@ -301,6 +430,7 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   a.key = make_uint2((uint32_t)c.seed, (uint32_t)(c.seed >> 32) ^ c.replica);
   a.step = c.step_dev;
   a.fsum_part = c.rbl_part;
+  a.err = c.err;
   a.ncore = want_debug ? c.nbr : nullptr;
   a.nshell = want_debug ? c.nshell : nullptr;
   a.partners = want_debug ? c.partners : nullptr;

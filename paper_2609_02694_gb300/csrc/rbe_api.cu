@@ -168,6 +168,7 @@ int read_device_flags(Ctx &c) {
     RBE_CUDA_TRY(cudaMemsetAsync(c.err, 0, sizeof(int), c.stream));
     if (flags & ERRBIT_SAMPLER) return RBE_ERR_SAMPLER;
     if (flags & ERRBIT_NONFINITE) return RBE_ERR_NONFINITE;
+    if (flags & ERRBIT_CAPACITY) return RBE_ERR_CAPACITY;
   }
   return RBE_OK;
 }
@@ -252,6 +253,7 @@ const char *rbe_error_string(int code) {
     case RBE_ERR_SAMPLER: return "mode sampler drew k = 0 in 64 consecutive attempts";
     case RBE_ERR_NONFINITE: return "non-finite or runaway position update";
     case RBE_ERR_STATE: return "call not valid in the current state";
+    case RBE_ERR_CAPACITY: return "an RBL neighbour stencil held more than 6144 candidates";
     default: return "unknown error";
   }
 }

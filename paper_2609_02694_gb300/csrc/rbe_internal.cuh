@@ -24,7 +24,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxTypes = 16;
 
 // Device error bits (OR-ed into ctx.err).
-enum : int { ERRBIT_SAMPLER = 1, ERRBIT_NONFINITE = 2 };
+enum : int { ERRBIT_SAMPLER = 1, ERRBIT_NONFINITE = 2, ERRBIT_CAPACITY = 4 };
 
 // Partial-sum slots (doubles per block) of the energy / virial reductions.
 enum : int { Q_UREAL = 0, Q_ULJ = 1, Q_WREAL = 2, Q_WLJ = 3, NQ_PAIR = 4 };
