@@ -135,6 +135,17 @@ int rbe_step(rbe_handle h, int nsteps);
  * RBE_N_ENERGY and RBE_N_VIRIAL doubles). Synchronises the stream. */
 int rbe_get_energies(rbe_handle h, double *energies, double *virial);
 
+/* Nose-Hoover NVT thermostat for rbe_step (a chain of one thermostat, Trotter-split
+ * around each velocity-Verlet step: half step before the first half-kick and after the
+ * second). Q = N_f kB T tau^2 with N_f = 3N - 3. tau <= 0 switches it off (NVE, the
+ * default). kB is in the caller's energy unit per kelvin (0.0019872067 for kcal/mol).
+ * The friction xi and the integral eta start at 0; calling again resets them. */
+int rbe_set_thermostat(rbe_handle h, double T_target, double tau, double kB);
+
+/* Thermostat state after the last step: out[0] = xi, out[1] = eta,
+ * out[2] = Q xi^2 / 2 + N_f kB T eta (add it to U + K for the conserved quantity). */
+int rbe_get_thermostat(rbe_handle h, double out[3]);
+
 /* Current step counter (number of completed rbe_step steps). */
 int rbe_get_step(rbe_handle h, uint64_t *step);
 

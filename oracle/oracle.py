@@ -56,10 +56,12 @@ def lib():
         L.orc_vv_drift.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, _f64p, _f64p, ct.c_double,
                                    ct.c_double]
         L.orc_vv_kick.argtypes = [ct.c_int64, _f64p, _f64p, _f64p, ct.c_double, ct.c_double]
+        L.orc_nh_half.argtypes = [ct.c_int64, _f64p, _f64p, ct.c_double, ct.c_double,
+                                  ct.c_double, ct.c_double, ct.c_double, _f64p]
         L.orc_num_threads.restype = ct.c_int
         for name in ("orc_kdim_table", "orc_sample_k", "orc_rho", "orc_rbe_kspace",
                      "orc_ewald_kspace", "orc_real_space", "orc_cells", "orc_rbl",
-                     "orc_brute_coulomb", "orc_vv_drift", "orc_vv_kick"):
+                     "orc_brute_coulomb", "orc_vv_drift", "orc_vv_kick", "orc_nh_half"):
             getattr(L, name).restype = ct.c_int
         _LIB = L
     return _LIB
@@ -229,6 +231,12 @@ def vv_drift(s, v, F, mass, box, dt, kappa):
 
 def vv_kick(v, F, mass, dt, kappa):
     _check(lib().orc_vv_kick(len(v), v, _f(F), _f(mass), float(dt), float(kappa)), "vv_kick")
+
+
+def nh_half(v, mass, kappa, Nf, kT, Q, dt, xi_eta):
+    """Nose-Hoover half step; v (N, 3) and xi_eta (2,) are updated in place."""
+    _check(lib().orc_nh_half(len(v), v, _f(mass), float(kappa), float(Nf), float(kT), float(Q),
+                             float(dt), xi_eta), "nh_half")
 
 
 def total_forces(s, q, types, box, alpha, rc, C, eps, sig, m, S):

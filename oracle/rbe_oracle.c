@@ -551,3 +551,21 @@ int orc_vv_kick(int64_t N, double *v, const double *F, const double *mass, doubl
     for (int d = 0; d < 3; ++d) v[3 * i + d] += F[3 * i + d] / mass[i] * (0.5 * dt) * kappa;
   return 0;
 }
+
+/* Nose-Hoover thermostat half step (chain of one), Trotter-split around the Verlet step. */
+int orc_nh_half(int64_t N, double *v, const double *mass, double kappa, double Nf, double kT,
+                double Q, double dt, double xi_eta[2]) {
+  if (N < 0 || !(Q > 0)) return -1;
+  double K2 = 0.0; /* 2K = sum m v^2 / kappa */
+  for (int64_t i = 0; i < N; ++i)
+    for (int d = 0; d < 3; ++d) K2 += mass[i] * v[3 * i + d] * v[3 * i + d] / kappa;
+  double xi = xi_eta[0];
+  xi += 0.25 * dt * (K2 - Nf * kT) / Q;
+  double s = exp(-xi * 0.5 * dt);
+  for (int64_t i = 0; i < 3 * N; ++i) v[i] *= s;
+  K2 *= s * s;
+  xi_eta[1] += xi * 0.5 * dt;
+  xi += 0.25 * dt * (K2 - Nf * kT) / Q;
+  xi_eta[0] = xi;
+  return 0;
+}

@@ -136,6 +136,14 @@ int orc_vv_drift(int64_t N, uint32_t *s, double *v, const double *F, const doubl
 int orc_vv_kick(int64_t N, double *v, const double *F, const double *mass, double dt,
                 double kappa);
 
+/* Nose-Hoover half step (chain of one thermostat, Trotter splitting of the Liouville
+ * operator): xi += dt/4 (2K - Nf kT)/Q; v *= exp(-xi dt/2); eta += xi dt/2;
+ * xi += dt/4 (2K' - Nf kT)/Q, with K = 1/2 sum m v^2 / kappa before and K' after the
+ * scaling. xi_eta[2] = {xi, eta} is updated in place. Applied before the first half-kick
+ * and after the second of every velocity-Verlet step. */
+int orc_nh_half(int64_t N, double *v, const double *mass, double kappa, double Nf, double kT,
+                double Q, double dt, double xi_eta[2]);
+
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int orc_num_threads(void);
 

@@ -85,6 +85,8 @@ def lib(build_if_missing: bool = False):
     L.rbe_batch_create.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p), _vp]
     L.rbe_batch_step.argtypes = [ct.c_void_p, ct.c_int]
     L.rbe_batch_destroy.argtypes = [ct.c_void_p]
+    L.rbe_set_thermostat.argtypes = [ct.c_void_p, ct.c_double, ct.c_double, ct.c_double]
+    L.rbe_get_thermostat.argtypes = [ct.c_void_p, _vp]
     L.rbe_set_tuning.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
     L.rbe_get_tuning.argtypes = [ct.c_void_p, ct.c_int, _vp]
     L.rbe_autotune.argtypes = [ct.c_void_p, ct.c_int, _vp]
@@ -286,6 +288,17 @@ class RBE:
         k = ct.c_int64()
         _check(lib().rbe_get_profile(self._h, None, ct.addressof(k)), "rbe_get_profile")
         return k.value
+
+    def set_thermostat(self, T: float, tau: float, kB: float = 0.0019872067):
+        """Nose-Hoover NVT at temperature T with relaxation time tau (tau <= 0: NVE)."""
+        _check(lib().rbe_set_thermostat(self._h, float(T), float(tau), float(kB)),
+               "rbe_set_thermostat")
+
+    def thermostat(self):
+        """(xi, eta, extended-energy term Q xi^2/2 + Nf kB T eta)."""
+        out = np.zeros(3, np.float64)
+        _check(lib().rbe_get_thermostat(self._h, out.ctypes.data), "rbe_get_thermostat")
+        return tuple(out)
 
     def set_tuning(self, key: str, value: int):
         _check(lib().rbe_set_tuning(self._h, TUNABLES[key], int(value)), "rbe_set_tuning")

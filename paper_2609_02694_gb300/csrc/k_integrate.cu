@@ -14,15 +14,17 @@ template <typename V, typename FT>
 __global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
                                   const float *__restrict__ invm, uint32_t *__restrict__ s,
                                   int64_t N, double hdk, double dt, double Lx, double Ly,
-                                  double Lz, int *__restrict__ err) {
+                                  double Lz, int *__restrict__ err,
+                                  const double *__restrict__ scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double L[3] = {Lx, Ly, Lz};
   const V im = (V)invm[i];
+  const V sc = scale ? (V)*scale : (V)1;  // Nose-Hoover start-of-step scaling
   bool bad = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    V vv = v[d * N + i] + (V)F[d * N + i] * im * (V)hdk;
+    V vv = v[d * N + i] * sc + (V)F[d * N + i] * im * (V)hdk;
     v[d * N + i] = vv;
     const double inc = __ddiv_rn(__dmul_rn(__dmul_rn((double)vv, dt), kTwo32), L[d]);
     bad |= !isfinite(inc) || fabs(inc) > 2.0e9;
@@ -63,7 +65,54 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) ke_part[blockIdx.x] = sh[0];
 }
 
+// Nose-Hoover half steps (chain of one): from 2K = 2 sum(kinetic partials) the end-of-step
+// half (mode 0) gives the velocity scale s_end and the start-of-next-step half gives
+// s_start, applied by the next kick-drift; mode 1 only does the start half (first step).
+__global__ void __launch_bounds__(256)
+    thermostat_kernel(const double *__restrict__ ke_part, int64_t n, double Nf, double kT,
+                      double Q, double dt, double *__restrict__ th, int mode) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t b = threadIdx.x; b < n; b += blockDim.x) acc += ke_part[b];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  double K2 = 2.0 * sh[0];
+  double xi = th[0], eta = th[1], s_end = 1.0;
+  if (mode == 0) {
+    xi += 0.25 * dt * (K2 - Nf * kT) / Q;
+    s_end = exp(-xi * 0.5 * dt);
+    K2 *= s_end * s_end;
+    eta += xi * 0.5 * dt;
+    xi += 0.25 * dt * (K2 - Nf * kT) / Q;
+  }
+  th[3] = 0.5 * K2;
+  th[4] = s_end;
+  th[5] = xi;   // state at the end of the step (reported)
+  th[6] = eta;
+  xi += 0.25 * dt * (K2 - Nf * kT) / Q;
+  const double s_start = exp(-xi * 0.5 * dt);
+  K2 *= s_start * s_start;
+  eta += xi * 0.5 * dt;
+  xi += 0.25 * dt * (K2 - Nf * kT) / Q;
+  th[0] = xi;
+  th[1] = eta;
+  th[2] = s_start;
+}
+
+template <typename V>
+__global__ void scale_v_kernel(V *__restrict__ v, int64_t N, const double *__restrict__ scale) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 3 * N) return;
+  v[k] *= (V)*scale;
+}
+
 struct TotalsArgs {
+  const double *ke_override;
   const double *pair, *coul, *rbl, *ke, *emode;
   int64_t n_pair, n_coul, n_rbl, n_ke;
   int P;
@@ -99,7 +148,8 @@ __global__ void __launch_bounds__(256) totals_kernel(TotalsArgs a) {
   if (threadIdx.x == 0) {
     const double ur = (double)sh[Q_UREAL][0], ul = (double)sh[Q_ULJ][0];
     const double wr = (double)sh[Q_WREAL][0], wl = (double)sh[Q_WLJ][0];
-    const double uk = (double)sh[4][0], wk = (double)sh[5][0], ke = (double)sh[6][0];
+    const double uk = (double)sh[4][0], wk = (double)sh[5][0];
+    const double ke = a.ke_override ? *a.ke_override : (double)sh[6][0];
     a.scal[S_UREAL] = ur;
     a.scal[S_ULJ] = ul;
     a.scal[S_UK] = uk;
@@ -176,12 +226,28 @@ cudaError_t launch_kick_drift(Ctx &c) {
   const int b = c.cur;
   const double hdk = 0.5 * c.dt * c.kappa;
   if (c.N == 0) return cudaSuccess;
+  const double *scale = c.nvt ? c.thermo + 2 : nullptr;
   if (c.precision == RBE_FP64)
     kick_drift_kernel<double, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vd[b], c.Fd, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err);
+        c.vd[b], c.Fd, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err,
+        scale);
   else
     kick_drift_kernel<float, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vf[b], c.F, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err);
+        c.vf[b], c.F, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err,
+        scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thermostat(Ctx &c, int mode) {
+  const int b = c.cur;
+  thermostat_kernel<<<1, 256, 0, c.stream>>>(c.epart + c.off_ke, c.n_ke_blk, c.Nf, c.kB * c.T0,
+                                             c.Qnh, c.dt, c.thermo, mode);
+  if (mode == 0) {
+    if (c.precision == RBE_FP64)
+      scale_v_kernel<double><<<nblk(3 * c.N, 256), 256, 0, c.stream>>>(c.vd[b], c.N, c.thermo + 4);
+    else
+      scale_v_kernel<float><<<nblk(3 * c.N, 256), 256, 0, c.stream>>>(c.vf[b], c.N, c.thermo + 4);
+  }
   return cudaGetLastError();
 }
 
@@ -210,6 +276,7 @@ cudaError_t launch_totals(Ctx &c) {
   a.emode = c.emode; a.P = c.P;
   a.U_self = c.U_self;
   a.scal = c.scal;
+  a.ke_override = c.nvt ? c.thermo + 3 : nullptr;
   if (c.precision == RBE_FP32) totals_kernel<float><<<1, 256, 0, c.stream>>>(a);
   else totals_kernel<double><<<1, 256, 0, c.stream>>>(a);
   return cudaGetLastError();

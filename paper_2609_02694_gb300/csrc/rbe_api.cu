@@ -123,6 +123,7 @@ int free_all(Ctx &c) {
   dfree(c.abd); dfree(c.emode); dfree(c.epart); dfree(c.scal); dfree(c.step_dev);
   dfree(c.err); dfree(c.nbr); dfree(c.nshell); dfree(c.partners); dfree(c.rbl_mean);
   dfree(c.rbl_part); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
+  dfree(c.thermo);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   c.cap_stream = nullptr;
   if (c.scal_host) cudaFreeHost(c.scal_host);
@@ -157,6 +158,7 @@ int64_t kernels_per_step(const Ctx &c) {
   else k += (c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2;  // pair passes
   k += c.Nq > 0 ? 1 : 0;                 // gather
   k += 2;                                // kick (+kinetic), totals
+  if (c.nvt) k += 2;                     // thermostat, end-of-step velocity scaling
   return k;
 }
 
@@ -218,6 +220,7 @@ int capture_step_graph(Ctx &c, int parity, cudaGraphExec_t *out) {
     rc = force_pipeline(c, false);
     if (rc != RBE_OK) break;
     if (launch_kick(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+    if (c.nvt && launch_thermostat(c, 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
     if (launch_totals(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
     mark(c, RBE_N_PHASE);
   } while (0);
@@ -599,6 +602,11 @@ int rbe_step(rbe_handle h, int nsteps) {
     int rc = forces_common(h, c.step, false);
     if (rc != RBE_OK) return rc;
   }
+  if (c.nvt && !c.nvt_primed) {  // start half of the first thermostatted step
+    RBE_CUDA_TRY(launch_kinetic(c));
+    RBE_CUDA_TRY(launch_thermostat(c, 1));
+    c.nvt_primed = true;
+  }
   for (int b = 0; b < 2; ++b)
     if (!c.graph[b]) {
       int rc = capture_step_graph(c, b, &c.graph[b]);
@@ -610,6 +618,43 @@ int rbe_step(rbe_handle h, int nsteps) {
     c.step += 1;
   }
   c.have_forces = true;
+  return RBE_OK;
+}
+
+static void drop_graphs(Ctx &c);
+
+int rbe_set_thermostat(rbe_handle h, double T_target, double tau, double kB) {
+  if (!h || !std::isfinite(T_target) || !std::isfinite(tau) || !std::isfinite(kB))
+    return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  const bool on = tau > 0;
+  if (on && (!(T_target > 0) || !(kB > 0) || c.N < 2)) return RBE_ERR_INVALID;
+  if (!c.thermo && dalloc(c, &c.thermo, 7) != RBE_OK) return RBE_ERR_OOM;
+  const double init[7] = {0.0, 0.0, 1.0, 0.0, 1.0, 0.0, 0.0};
+  RBE_CUDA_TRY(cudaMemcpy(c.thermo, init, sizeof(init), cudaMemcpyHostToDevice));
+  c.nvt = on;
+  c.nvt_primed = false;
+  c.T0 = T_target; c.tau = tau; c.kB = kB;
+  c.Nf = 3.0 * (double)c.N - 3.0;
+  c.Qnh = c.Nf * kB * T_target * tau * tau;
+  drop_graphs(c);
+  return RBE_OK;
+}
+
+int rbe_get_thermostat(rbe_handle h, double out[3]) {
+  if (!h || !out) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  double th[7] = {0.0, 0.0, 1.0, 0.0, 1.0, 0.0, 0.0};
+  if (c.thermo) {
+    RBE_CUDA_TRY(cudaMemcpyAsync(th, c.thermo, sizeof(th), cudaMemcpyDeviceToHost, c.stream));
+    RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  }
+  // xi and eta at the end of the last step (the device copy already holds the next step's
+  // start half, whose velocity scaling is still pending)
+  out[0] = th[5];
+  out[1] = th[6];
+  out[2] = c.nvt ? 0.5 * c.Qnh * th[5] * th[5] + c.Nf * c.kB * c.T0 * th[6] : 0.0;
   return RBE_OK;
 }
 
@@ -919,7 +964,9 @@ static int batch_capture(rbe_batch b, int flip, cudaGraphExec_t *out) {
       }
       rc = force_pipeline(c, false);
       if (rc != RBE_OK) break;
-      if (launch_kick(c) != cudaSuccess || launch_totals(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      if (launch_kick(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      if (c.nvt && launch_thermostat(c, 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      if (launch_totals(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
       cudaEventRecord(b->ev[r], b->br[r]);
       cudaStreamWaitEvent(b->cap, b->ev[r], 0);
     }
@@ -968,11 +1015,17 @@ int rbe_batch_create(rbe_batch *out, int n, const rbe_handle *handles, void *cud
 int rbe_batch_step(rbe_batch b, int nsteps) {
   if (!b || nsteps < 0) return RBE_ERR_INVALID;
   if (nsteps == 0) return RBE_OK;
-  // initial forces of every replica on its own stream, then order the batch stream after them
+  // initial forces (and thermostat start halves) of every replica on its own stream, then
+  // order the batch stream after them
   for (auto h : b->h) {
     if (!h->have_forces) {
       int rc = forces_common(h, h->step, false);
       if (rc != RBE_OK) return rc;
+    }
+    if (h->nvt && !h->nvt_primed) {
+      RBE_CUDA_TRY(launch_kinetic(*h));
+      RBE_CUDA_TRY(launch_thermostat(*h, 1));
+      h->nvt_primed = true;
     }
     RBE_CUDA_TRY(cudaStreamSynchronize(h->stream));
   }

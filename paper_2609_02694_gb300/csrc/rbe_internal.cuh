@@ -139,6 +139,10 @@ struct Ctx {
   float *out_host = nullptr;   // pinned
   double *pos_stage = nullptr; // 3N doubles (set_positions)
   bool have_forces = false;
+  // Nose-Hoover thermostat (NVT); thermo = {xi, eta, s_start, K_end, s_end, xi_end, eta_end}
+  bool nvt = false, nvt_primed = false;
+  double T0 = 0, tau = 0, kB = 0, Qnh = 0, Nf = 0;
+  double *thermo = nullptr;
   // graph
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per starting buffer parity
   cudaStream_t cap_stream = nullptr;  // internal non-blocking stream used only for capture
@@ -212,6 +216,7 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug);
 cudaError_t launch_kick_drift(Ctx &c);
 cudaError_t launch_kick(Ctx &c);
 cudaError_t launch_kinetic(Ctx &c);
+cudaError_t launch_thermostat(Ctx &c, int mode);  // 0: end + next start half, 1: start half only
 cudaError_t launch_totals(Ctx &c);
 cudaError_t launch_set_step(Ctx &c, uint64_t step);
 cudaError_t launch_step_advance(Ctx &c);

@@ -346,3 +346,59 @@ def test_autotune_keeps_results(orc):
         h.step(3)
     ref = oracle_all(orc, sy, m, S)
     assert rel_l2(F, ref["F"]) < TOL_F32
+
+
+# -------------------------------------------------------------------------- NVT
+
+
+def test_nvt_one_step_matches_oracle(orc):
+    """One Nose-Hoover velocity-Verlet step in the FP64 form against the oracle's half
+    steps around its Verlet step (same modes at steps 0 and 1)."""
+    sy = synth.make_system(3000, L=32.0, all_charged=True, seed=1, T=200.0)
+    dt, kappa, kB, T0, tau = 1.0, synth.ACCEL_KAPPA, synth.BOLTZMANN_KB, 300.0, 20.0
+    with handle(sy, 100, precision="fp64", dt=dt, kappa=kappa) as h:
+        h.set_thermostat(T0, tau, kB)
+        h.step(1)
+        pos, vel, s1 = h.state()
+        xi, eta, _ = h.thermostat()
+    Nf = 3 * sy.n - 3
+    Q = Nf * kB * T0 * tau ** 2
+    xe = np.zeros(2)
+    m0, S0 = orc.sample_k(1, 0, 0, sy.box, ALPHA, 100)
+    m1, S1 = orc.sample_k(1, 1, 0, sy.box, ALPHA, 100)
+    s, v = sy.s.copy(), sy.v.copy()
+    F0 = oracle_all(orc, sy, m0, S0)["F"]
+    orc.nh_half(v, sy.mass, kappa, Nf, kB * T0, Q, dt, xe)
+    orc.vv_drift(s, v, F0, sy.mass, sy.box, dt, kappa)
+    F1 = orc.total_forces(s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig, m1, S1)["F"]
+    orc.vv_kick(v, F1, sy.mass, dt, kappa)
+    orc.nh_half(v, sy.mass, kappa, Nf, kB * T0, Q, dt, xe)
+    ds = (s1.astype(np.int64) - s.astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31
+    assert np.abs(ds).max() <= 1
+    assert rel_l2(vel, v) < 1e-7
+    # thermostat state at the end of the step equals the oracle's. Each quarter update is
+    # (dt/4)(2K - Nf kT)/Q, whose difference 2K - Nf kT cancels near the target, so the
+    # comparison is on the scale of one update, dt / tau^2
+    assert abs(xi - xe[0]) < 1e-7 * dt / tau ** 2
+    assert abs(eta - xe[1]) < 1e-7 * dt * dt / tau ** 2
+
+
+def test_nvt_thermalises_lj_system():
+    """LJ fluid without charges (deterministic forces): the temperature is driven from
+    150 K to the 300 K target and the extended energy stays constant."""
+    sy = synth.make_system(4000, density=0.03, frac_charged=0.0, seed=2, T=150.0)
+    kB = synth.BOLTZMANN_KB
+    with handle(sy, 8, dt=1.0, kappa=synth.ACCEL_KAPPA, precision="fp64") as h:
+        h.set_thermostat(300.0, 50.0, kB)
+        Hs, Ts = [], []
+        for _ in range(30):
+            h.step(50)
+            E, _ = h.energies()
+            xi, eta, ext = h.thermostat()
+            Nf = 3 * sy.n - 3
+            Ts.append(2 * E["kinetic"] / (Nf * kB))
+            Hs.append(E["total"] + E["kinetic"] + ext)
+    Ts, Hs = np.array(Ts), np.array(Hs)
+    assert abs(Ts[-10:].mean() - 300.0) < 30.0
+    # plain truncation at r_c makes the extended energy jump by U(r_c) per crossing pair
+    assert np.abs(Hs - Hs[0]).max() < 0.02 * abs(Hs[0])

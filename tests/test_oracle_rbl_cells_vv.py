@@ -173,3 +173,49 @@ def test_vv_energy_conservation(orc):
     assert abs(np.array(Es) - E0).max() < 2e-4 * ke
     p = (sy.mass[:, None] * v).sum(0)
     assert np.abs(p).max() < 1e-9
+
+
+def _nvt_run(orc, steps, tau, T0=300.0, dt=1.0):
+    sy = synth.make_system(216, density=0.03, frac_charged=0.0, seed=2, T=150.0)
+    box, kappa, kB = sy.box, synth.ACCEL_KAPPA, synth.BOLTZMANN_KB
+    s, v = sy.s.copy(), sy.v.copy()
+    rc = 8.0
+    u_rc = 4 * sy.eps[0] * ((sy.sig[0] / rc) ** 12 - (sy.sig[0] / rc) ** 6)
+    Nf = 3 * sy.n - 3
+    Q = Nf * kB * T0 * tau ** 2
+    xe = np.zeros(2)
+
+    def forces(x):
+        r = orc.real_space(x, sy.q, sy.types, box, 0.09, rc, 1.0, sy.eps, sy.sig)
+        return r["F"], r["U_lj"] - 0.5 * r["nbr"].sum() * u_rc
+
+    F, U = forces(s)
+    H, T = [], []
+    for _ in range(steps):
+        orc.nh_half(v, sy.mass, kappa, Nf, kB * T0, Q, dt, xe)
+        orc.vv_drift(s, v, F, sy.mass, box, dt, kappa)
+        F, U = forces(s)
+        orc.vv_kick(v, F, sy.mass, dt, kappa)
+        orc.nh_half(v, sy.mass, kappa, Nf, kB * T0, Q, dt, xe)
+        K = 0.5 * (sy.mass[:, None] * v * v).sum() / kappa
+        H.append(U + K + 0.5 * Q * xe[0] ** 2 + Nf * kB * T0 * xe[1])
+        T.append(2 * K / (Nf * kB))
+    return np.array(H), np.array(T)
+
+
+def test_nose_hoover_conserves_extended_energy_and_thermalises(orc):
+    """With the Nose-Hoover half steps around Verlet, H = U + K + Q xi^2/2 + Nf kT eta is
+    conserved, and the temperature is driven from 150 K towards the 300 K target."""
+    H, T = _nvt_run(orc, 1500, tau=50.0)
+    assert np.abs(H - H[0]).max() < 2e-3 * abs(H[0])
+    assert abs(T[-500:].mean() - 300.0) < 45.0
+    assert T[:20].mean() < 200.0
+
+
+def test_nose_hoover_weak_coupling_limit_is_nve(orc):
+    """tau -> infinity (Q -> infinity) leaves the velocities untouched."""
+    sy = synth.make_system(64, density=0.03, frac_charged=0.0, seed=3)
+    v = sy.v.copy()
+    xe = np.zeros(2)
+    orc.nh_half(v, sy.mass, synth.ACCEL_KAPPA, 189, synth.BOLTZMANN_KB * 300, 1e300, 1.0, xe)
+    assert np.array_equal(v, sy.v) and abs(xe[0]) < 1e-290
