@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 form, e2e, error and CPU legs (profiling runs)")
     ap.add_argument("--config", default="main",
-                    choices=["main", "batch96", "sweep16m", "rbl134m", "n3000"],
+                    choices=["main", "batch96", "sweep16m", "rbl134m", "n3000", "ljelec", "peaks"],
                     help="main: the benchmark line; the others print per-config JSON lines")
     return ap.parse_args()
 
@@ -265,6 +265,8 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     kps = h.kernels_per_step()
+    peaks = measured_peaks()
+    nq_pairs = float((sy.q != 0).sum()) * args.P
     E1, _ = h.energies()
     value = sy.n * args.steps * ws / (total_ms / 1e3)
     pair_ms = phases["pair"] / args.steps
@@ -285,6 +287,17 @@ def run_ours(args):
                          "traffic": None, "pair_ms_per_launch": pair_ms,
                          "units": f"{pairs:.0f} unique pairs x {PAIR_FLOPS:.0f} flops",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"},
+            "rooflines_other": {
+                "structure_factor": {"bound": "sfu", "unit": "sincos pairs/s",
+                                     "achieved": nq_pairs / (phases["sf"] / args.steps / 1e3),
+                                     "peak": peaks["sincos_pairs"],
+                                     "frac": nq_pairs / (phases["sf"] / args.steps / 1e3) / peaks["sincos_pairs"]},
+                "gather": {"bound": "sfu", "unit": "sincos pairs/s",
+                           "achieved": nq_pairs / (phases["gather"] / args.steps / 1e3),
+                           "peak": peaks["sincos_pairs"],
+                           "frac": nq_pairs / (phases["gather"] / args.steps / 1e3) / peaks["sincos_pairs"]},
+                "pair_vs_measured_fp32": achieved * 1e12 / peaks["fp32_flops"] if achieved else None,
+                "peak_source": "own probes (rbe_measure_peak) at the run's clock"},
             "clocks": clk.summary(),
             "energy": {"total_step0": E0["total"], "total_after": E1["total"],
                        "kinetic_after": E1["kinetic"]}}
@@ -517,6 +530,69 @@ def run_n3000(args):
     print(json.dumps(out), flush=True)
 
 
+def measured_peaks():
+    """Measured FP32 flop/s, sincos pairs/s and FP64 flop/s of this GPU (own probes)."""
+    from paper_2609_02694_gb300 import binding
+    return {"fp32_flops": binding.measure_peak("fp32"),
+            "sincos_pairs": binding.measure_peak("sincos"),
+            "fp64_flops": binding.measure_peak("fp64")}
+
+
+def run_peaks(args):
+    import torch
+    from paper_2609_02694_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"config": "peaks", **measured_peaks()}), flush=True)
+
+
+def run_ljelec(args):
+    """LJ electrolyte in reduced units (all ions charged, density 200,000 / 271^3), random
+    batch list (r_s = 8, r_c = 4, p = 30), P = 200, Nose-Hoover T = 1: the O(N) sweep of the
+    full step, with the k-space kernels against the measured sincos throughput."""
+    import torch
+    from paper_2609_02694_gb300 import binding, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    prm = synth.LJ_ELECTROLYTE
+    for N in (200000, 1400000, 7000000, 28000000):
+        sy = synth.lj_electrolyte(N)
+        h = binding.from_system(sy, P=prm["P"], alpha=prm["alpha"], r_c=prm["r_c"],
+                                r_core=prm["r_core"], p_rbl=prm["p_rbl"],
+                                coulomb_C=prm["coulomb_C"], dt=prm["dt"], kappa=prm["kappa"],
+                                stream=stream.cuda_stream)
+        h.set_thermostat(prm["T"], prm["tau"], prm["kB"])
+        h.set_profiling(True)
+        h.step(max(2, args.warmup))
+        torch.cuda.synchronize()
+        K = 5
+        tot, ph_tot = 0.0, None
+        for _ in range(K):
+            tot += _timed(lambda: h.step(1), 1, stream)
+            ph, _ = h.profile()
+            ph_tot = ph if ph_tot is None else {k: ph_tot[k] + ph[k] for k in ph}
+        E, _ = h.energies()
+        T_inst = 2 * E["kinetic"] / ((3 * N - 3) * prm["kB"])
+        sf = ph_tot["sf"] / K
+        ga = ph_tot["gather"] / K
+        pairs = N * prm["P"]
+        print(json.dumps({"config": "ljelec", "N": N, "L": float(sy.box[0]),
+                          "value": N * K / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / K,
+                          "phases_ms_per_step": {k: v / K for k, v in ph_tot.items()},
+                          "kspace_rooflines": {
+                              "structure_factor": {"bound": "sfu", "achieved": pairs / (sf / 1e3),
+                                                   "peak": peaks["sincos_pairs"],
+                                                   "unit": "sincos pairs/s",
+                                                   "frac": pairs / (sf / 1e3) / peaks["sincos_pairs"]},
+                              "gather": {"bound": "sfu", "achieved": pairs / (ga / 1e3),
+                                         "peak": peaks["sincos_pairs"], "unit": "sincos pairs/s",
+                                         "frac": pairs / (ga / 1e3) / peaks["sincos_pairs"]}},
+                          "temperature": T_inst}), flush=True)
+        h.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -529,6 +605,10 @@ def main():
         run_rbl134m(args)
     elif args.config == "n3000":
         run_n3000(args)
+    elif args.config == "ljelec":
+        run_ljelec(args)
+    elif args.config == "peaks":
+        run_peaks(args)
     else:
         run_ours(args)
 

@@ -204,6 +204,12 @@ int rbe_get_tuning(rbe_handle h, int key, int *value);
  * Discards the captured step graph. Writes the chosen values to chosen[2] (nullable). */
 int rbe_autotune(rbe_handle h, int reps, int *chosen);
 
+/* Throughput probe on the current device, for roofline denominators (it allocates 64
+ * bytes of scratch and synchronises the device): kind 0 = FP32 FMA (flop/s, 2 per FMA),
+ * 1 = __sincosf pairs per second (the SFU work of one phase of the k-space kernels),
+ * 2 = FP64 FMA (flop/s). *ms receives the best kernel time (nullable). */
+int rbe_measure_peak(int kind, double *ops_per_s, double *ms);
+
 /* Bytes of device memory held by the handle. */
 int rbe_get_memory(rbe_handle h, int64_t *bytes);
 

@@ -85,6 +85,7 @@ def lib(build_if_missing: bool = False):
     L.rbe_batch_create.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p), _vp]
     L.rbe_batch_step.argtypes = [ct.c_void_p, ct.c_int]
     L.rbe_batch_destroy.argtypes = [ct.c_void_p]
+    L.rbe_measure_peak.argtypes = [ct.c_int, _vp, _vp]
     L.rbe_set_thermostat.argtypes = [ct.c_void_p, ct.c_double, ct.c_double, ct.c_double]
     L.rbe_get_thermostat.argtypes = [ct.c_void_p, _vp]
     L.rbe_set_tuning.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
@@ -353,6 +354,14 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def measure_peak(kind: str) -> float:
+    """Measured device throughput: 'fp32' (flop/s), 'sincos' (pairs/s) or 'fp64' (flop/s)."""
+    v = ct.c_double()
+    _check(lib().rbe_measure_peak({"fp32": 0, "sincos": 1, "fp64": 2}[kind], ct.addressof(v), None),
+           "rbe_measure_peak")
+    return v.value
 
 
 def from_system(sy, *, P: int, alpha: float, r_c: float, **kw) -> RBE:

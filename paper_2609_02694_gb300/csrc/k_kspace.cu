@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256)
 template <int MODE>
 __global__ void __launch_bounds__(128)
     sf_combine_kernel(const double *__restrict__ part, int nblk, int P,
-                      const double4 *__restrict__ kcd, double alpha, double2 *__restrict__ rho,
+                      const double4_16a *__restrict__ kcd, double alpha, double2 *__restrict__ rho,
                       float2 *__restrict__ abf, double2 *__restrict__ abd,
                       double *__restrict__ emode) {
   __shared__ double sre[128], sim[128];
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(128)
   }
   if (threadIdx.x == 0) {
     const double re = sre[0], im = sim[0];
-    const double4 kc = kcd[l];
+    const double4_16a kc = kcd[l];
     const double k2 = kc.x * kc.x + kc.y * kc.y + kc.z * kc.z;
     const double E = 0.5 * kc.w * (re * re + im * im);
     rho[l] = make_double2(re, im);
@@ -142,14 +142,14 @@ template <int MODE>
 __global__ void __launch_bounds__(kGatherThreads)
     gather_kernel(const uint32_t *__restrict__ cs, const float *__restrict__ cqf,
                   const double *__restrict__ cqd, int64_t Nq, const int4 *__restrict__ m,
-                  const float4 *__restrict__ kcf, const double4 *__restrict__ kcd,
+                  const float4 *__restrict__ kcf, const double4_16a *__restrict__ kcd,
                   const float2 *__restrict__ abf, const double2 *__restrict__ abd, int P,
                   const int32_t *__restrict__ cmap, float *__restrict__ F,
                   double *__restrict__ Fd, int64_t N) {
   __shared__ int4 sm[kGatherChunk];
   __shared__ float4 skf[kGatherChunk];
   __shared__ float2 sabf[kGatherChunk];
-  __shared__ double4 skd[MODE == 2 ? kGatherChunk : 1];
+  __shared__ double4_16a skd[MODE == 2 ? kGatherChunk : 1];
   __shared__ double2 sabd[MODE == 2 ? kGatherChunk : 1];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < Nq;

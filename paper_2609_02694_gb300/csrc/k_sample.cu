@@ -21,7 +21,7 @@ struct SampleArgs {
   double cnum;           // 4 pi C S / (P V)
   int4 *m;
   float4 *kcf;
-  double4 *kcd;
+  double4_16a *kcd;
   int *err;
 };
 
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) sample_k_kernel(SampleArgs a) {
     const double c = a.cnum / k2;
     a.m[l] = make_int4(mx, my, mz, 0);
     a.kcf[l] = make_float4((float)kx, (float)ky, (float)kz, (float)c);
-    a.kcd[l] = make_double4(kx, ky, kz, c);
+    a.kcd[l] = make_double4_16a(kx, ky, kz, c);
   }
 }
 

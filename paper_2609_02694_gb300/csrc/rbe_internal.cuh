@@ -110,7 +110,7 @@ struct Ctx {
   int M[3] = {0, 0, 0};
   int4 *m = nullptr;
   float4 *kcf = nullptr;     // (kx, ky, kz, c_l)
-  double4 *kcd = nullptr;
+  double4_16a *kcd = nullptr;
   double *sf_part = nullptr; // sf blocks x P x 2
   int sf_tile = 256, sf_mb = 128, sf_nblk_p = 0, sf_nblk_m = 0;
   int64_t sf_part_blocks = 0;  // capacity of sf_part in particle blocks

@@ -77,9 +77,11 @@ def jittered_lattice(N: int, box, rng: np.random.Generator, jitter: float) -> np
     return s.astype(np.uint32)
 
 
-def maxwell_velocities(mass: np.ndarray, T: float, rng: np.random.Generator) -> np.ndarray:
-    """Maxwell-Boltzmann velocities (Angstrom/fs) at temperature T, zero total momentum."""
-    sd = np.sqrt(BOLTZMANN_KB * T * ACCEL_KAPPA / mass)
+def maxwell_velocities(mass: np.ndarray, T: float, rng: np.random.Generator,
+                       kB: float = BOLTZMANN_KB, kappa: float = ACCEL_KAPPA) -> np.ndarray:
+    """Maxwell-Boltzmann velocities at temperature T (kB, kappa give the unit system; the
+    defaults are real units, Angstrom/fs), zero total momentum."""
+    sd = np.sqrt(kB * T * kappa / mass)
     v = rng.standard_normal((mass.size, 3)) * sd[:, None]
     p = (v * mass[:, None]).sum(axis=0) / mass.sum()
     return v - p[None, :]
@@ -88,7 +90,8 @@ def maxwell_velocities(mass: np.ndarray, T: float, rng: np.random.Generator) -> 
 def make_system(N: int, *, density: float | None = None, L: float | None = None,
                 frac_charged: float = 0.1, all_charged: bool = False, seed: int = 1,
                 T: float = 300.0, mass: float = 20.0, eps: float = 0.1, sigma: float = 3.0,
-                jitter: float = 0.1) -> System:
+                jitter: float = 0.1, kB: float = BOLTZMANN_KB,
+                kappa: float = ACCEL_KAPPA) -> System:
     """A cubic box of N particles at the given number density (or side L)."""
     if L is None:
         if density is None:
@@ -107,7 +110,7 @@ def make_system(N: int, *, density: float | None = None, L: float | None = None,
     q[charged[nq:]] = -1.0
     types = np.zeros(N, np.int32)
     m = np.full(N, mass, np.float64)
-    v = maxwell_velocities(m, T, _rng(seed, 1))
+    v = maxwell_velocities(m, T, _rng(seed, 1), kB, kappa)
     return System(box=box, s=s, q=q, types=types, mass=m, v=v,
                   eps=np.array([eps], np.float64), sig=np.array([sigma], np.float64),
                   meta=dict(N=N, L=L, density=N / L ** 3, n_plus=nq, n_minus=nq, seed=seed,
@@ -118,6 +121,20 @@ def sub_box(N: int = 65536, density: float = 0.1, frac_charged: float = 0.1,
             seed: int = 3) -> System:
     """The 65,536-particle box of the same composition used for precision-sweep errors."""
     return make_system(N, density=density, frac_charged=frac_charged, seed=seed)
+
+
+def lj_electrolyte(N: int = 200000, density: float = 200000 / 271.0 ** 3, seed: int = 6) -> System:
+    """Implicit-solvent LJ electrolyte in LJ reduced units (Sec. 3.1): N monovalent ions, half
+    of each sign, eps = sigma = m = kB = 1, T = 1, at the density of 200,000 ions in L = 271."""
+    return make_system(N, density=density, all_charged=True, seed=seed, T=1.0, mass=1.0,
+                       eps=1.0, sigma=1.0, jitter=0.1, kB=1.0, kappa=1.0)
+
+
+# Reduced-unit parameters of the LJ electrolyte (Table 1: r_s = 8, r_c = 4, p = 30, P = 200).
+# The paper gives no Coulomb strength or splitting parameter for it: C = 1 (unit charges in
+# reduced units) and alpha = 0.15 (erfc(sqrt(alpha) r_s) = 1.2e-5) are this build's reading.
+LJ_ELECTROLYTE = dict(coulomb_C=1.0, alpha=0.15, r_c=8.0, r_core=4.0, p_rbl=30, P=200,
+                      dt=0.001, kappa=1.0, kB=1.0, T=1.0, tau=0.1)
 
 
 def replica_sizes(n_rep: int = 96, lo: int = 2000, hi: int = 250000, seed: int = 4) -> list[int]:

@@ -402,3 +402,23 @@ def test_nvt_thermalises_lj_system():
     assert abs(Ts[-10:].mean() - 300.0) < 30.0
     # plain truncation at r_c makes the extended energy jump by U(r_c) per crossing pair
     assert np.abs(Hs - Hs[0]).max() < 0.02 * abs(Hs[0])
+
+
+def test_lj_electrolyte_reduced_units(orc):
+    """LJ electrolyte settings in reduced units (all ions charged, r_s = 8, r_c = 4, p = 30):
+    RBL + RBE forces against the oracle on the same modes and draws."""
+    prm = synth.LJ_ELECTROLYTE
+    sy = synth.lj_electrolyte(3000)
+    with binding.from_system(sy, P=prm["P"], alpha=prm["alpha"], r_c=prm["r_c"],
+                             r_core=prm["r_core"], p_rbl=prm["p_rbl"],
+                             coulomb_C=prm["coulomb_C"], dt=prm["dt"], kappa=prm["kappa"],
+                             seed=9) as h:
+        F, E, W = h.forces_f64(3)
+        m, S = h.sample_k(3)
+        nc, ns = h.neighbor_counts()
+    ref = orc.rbl(sy.s, sy.q, sy.types, sy.box, prm["alpha"], prm["r_core"], prm["r_c"],
+                  prm["p_rbl"], 9, 3, 0, prm["coulomb_C"], sy.eps, sy.sig)
+    Fk, Uk, Wk = orc.rbe_kspace(sy.s, sy.q, sy.box, prm["alpha"], prm["coulomb_C"], m, S)
+    assert np.array_equal(nc, ref["n_core"]) and np.array_equal(ns, ref["n_shell"])
+    assert rel_l2(F, ref["F"] + Fk) < TOL_F32
+    assert E["kspace"] == pytest.approx(Uk, rel=2e-6)
