@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--P", type=int, default=200)
     ap.add_argument("--precision", default="fp32_comp")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--skin", type=float, default=None,
+                    help="Verlet-list skin (A); 0 = cell traversal; default: timed trial of "
+                         "0, 0.5, 1.0, 1.5 on the workload itself")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 form, e2e, error and CPU legs (profiling runs)")
     ap.add_argument("--config", default="main",
@@ -215,6 +218,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def pick_traversal(binding, sy, mk, args, stream):
+    """Short-range traversal: cells every step (skin 0) or a Verlet list with skin, each
+    timed over real Verlet steps (list builds included) from the same initial state."""
+    cands = [0.0, 0.5, 1.0, 1.5] if args.skin is None else [args.skin]
+    if len(cands) == 1:
+        return cands[0], None
+    res = {}
+    for skin in cands:
+        h = binding.from_system(sy, precision=args.precision, **mk)
+        h.set_neighbor_list(skin)
+        h.step(3)
+        res[skin] = _timed(lambda: h.step(1), 10, stream) / 10
+        h.close()
+    return min(res, key=res.get), {str(k): v for k, v in res.items()}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_info()
@@ -234,7 +253,9 @@ def run_ours(args):
               dt=1.0, kappa=synth.ACCEL_KAPPA, replica=rank, stream=stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    skin, trial = pick_traversal(binding, sy, mk, args, stream)
     h = binding.from_system(sy, precision=args.precision, **mk)
+    h.set_neighbor_list(skin)
     tuned = h.autotune(3)
     h.set_profiling(True)
     # exact unique-pair count of step 0 (the roofline's units) and the force sample
@@ -278,10 +299,15 @@ def run_ours(args):
             "config": {"workload": desc + f", {args.precision} form",
                        "l2": "flushed between timed steps (256 MiB write); per-step CUDA events",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "autotuned": tuned},
+                       "autotuned": tuned,
+                       "short_range": (f"Verlet list, skin {skin} A" if skin > 0
+                                       else "cell traversal every step"),
+                       "traversal_trial_ms_per_step": trial},
             "gpu_launches": kps * args.steps,
             "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
-            "roofline": {"bound": "alu", "kernel": "pair_kernel (cell-list LJ)",
+            "roofline": {"bound": "alu",
+                         "kernel": ("list_pair_kernel (Verlet-list LJ)" if skin > 0
+                                    else "pair_kernel (cell-list LJ)"),
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS if achieved else None,
                          "traffic": None, "pair_ms_per_launch": pair_ms,
@@ -299,6 +325,7 @@ def run_ours(args):
                 "pair_vs_measured_fp32": achieved * 1e12 / peaks["fp32_flops"] if achieved else None,
                 "peak_source": "own probes (rbe_measure_peak) at the run's clock"},
             "clocks": clk.summary(),
+            "neighbor_list": h.neighbor_list_stats() if skin > 0 else None,
             "energy": {"total_step0": E0["total"], "total_after": E1["total"],
                        "kinetic_after": E1["kinetic"]}}
     if rank == 0 and not args.no_extras:
@@ -310,6 +337,7 @@ def run_ours(args):
                                "sample": f"{ns} particles (step 0)"}
         # FP64 form on the same workload
         h64 = binding.from_system(sy, precision="fp64", **mk)
+        h64.set_neighbor_list(skin)
         h64.set_profiling(True)
         F64, _, _ = h64.forces_f64(0)
         for _ in range(2):
@@ -589,7 +617,8 @@ def run_ljelec(args):
                               "gather": {"bound": "sfu", "achieved": pairs / (ga / 1e3),
                                          "peak": peaks["sincos_pairs"], "unit": "sincos pairs/s",
                                          "frac": pairs / (ga / 1e3) / peaks["sincos_pairs"]}},
-                          "temperature": T_inst}), flush=True)
+                          "temperature": T_inst,
+                          "rbl_eager": h.get_tuning("rbl_eager")}), flush=True)
         h.close()
 
 

@@ -47,7 +47,8 @@ enum {
   RBE_ERR_SAMPLER = -7,     /* 64 redraws of a mode all gave k = 0 (device flag) */
   RBE_ERR_NONFINITE = -8,   /* a non-finite velocity or position update (device flag) */
   RBE_ERR_STATE = -9,       /* call not valid in this state (e.g. no forces computed yet) */
-  RBE_ERR_CAPACITY = -10    /* an RBL stencil (27 cells) held more than 6144 candidates */
+  RBE_ERR_CAPACITY = -10    /* an RBL stencil (27 cells) held more than 6144 candidates, or a
+                               Verlet list outgrew its capacity (device flag) */
 };
 
 enum {
@@ -173,14 +174,15 @@ int rbe_get_rbl_partners(rbe_handle h, int32_t *partners);
 /* Phases timed by the profiler (CUDA events recorded on the library's stream). */
 enum {
   RBE_PH_KICK_DRIFT = 0, /* first half-kick + drift (rbe_step only) */
-  RBE_PH_BIN = 1,        /* linked-cell binning and reordering */
+  RBE_PH_BIN = 1,        /* list displacement check, linked-cell binning and reordering */
   RBE_PH_SAMPLE = 2,     /* Philox mode sampler */
   RBE_PH_SF = 3,         /* structure factor + FP64 combine */
-  RBE_PH_PAIR = 4,       /* main real-space kernel (cell list LJ[+Coulomb], or RBL) */
-  RBE_PH_PAIR2 = 5,      /* charged-subset Coulomb pass, or the RBL mean-force correction */
-  RBE_PH_GATHER = 6,     /* k-space force gather */
-  RBE_PH_TAIL = 7,       /* second half-kick, kinetic energy and totals */
-  RBE_N_PHASE = 8
+  RBE_PH_LIST = 4,       /* Verlet-list build (zero on steps without one, and in cell mode) */
+  RBE_PH_PAIR = 5,       /* main real-space kernel (cell list or Verlet list LJ[+Coulomb], or RBL) */
+  RBE_PH_PAIR2 = 6,      /* charged-subset Coulomb pass, or the RBL mean-force correction */
+  RBE_PH_GATHER = 7,     /* k-space force gather */
+  RBE_PH_TAIL = 8,       /* second half-kick, kinetic energy and totals */
+  RBE_N_PHASE = 9
 };
 
 /* Turn per-phase event timing on or off (off by default). Toggling it discards the
@@ -194,15 +196,42 @@ int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kernels_per_step);
 /* Tunables of the launch shapes (none changes results beyond FP32 rounding order):
  *  RBE_TUNE_PAIR_TEST16  1: packed half-precision candidate pre-test in the cell-list pair
  *                        kernel (exact decision still at evaluation), 0: FP32 pre-test
- *  RBE_TUNE_SF_TILE      particles per block tile of the structure factor (32..1024, x32) */
-enum { RBE_TUNE_PAIR_TEST16 = 0, RBE_TUNE_SF_TILE = 1 };
+ *  RBE_TUNE_SF_TILE      particles per block tile of the structure factor (32..1024, x32)
+ *  RBE_TUNE_RBL_EAGER    random batch list only. 1: the classifying pass evaluates every shell
+ *                        pair too, and a particle with #S_i <= p keeps that sum (bit-identical
+ *                        to the draw pass); 0: shell pairs only in the draw pass. The default
+ *                        is 1 when the mean shell size N/V * 4/3 pi (r_s^3 - r_core^3) <= p. */
+enum { RBE_TUNE_PAIR_TEST16 = 0, RBE_TUNE_SF_TILE = 1, RBE_TUNE_RBL_EAGER = 2, RBE_N_TUNE = 3 };
 int rbe_set_tuning(rbe_handle h, int key, int value);
 int rbe_get_tuning(rbe_handle h, int key, int *value);
 
 /* Autotuner: times each candidate setting of the tunables above on the handle's own system
  * (force evaluations, CUDA events, `reps` repetitions each) and keeps the fastest.
- * Discards the captured step graph. Writes the chosen values to chosen[2] (nullable). */
+ * Discards the captured step graph. Writes the chosen values, indexed by RBE_TUNE_*, to
+ * chosen[RBE_N_TUNE] (nullable). */
 int rbe_autotune(rbe_handle h, int reps, int *chosen);
+
+/* Verlet neighbour list with skin (the short-range traversal that Sec. 3.1 pairs with RBE),
+ * an alternative to the per-step cell traversal of the cell-list real space; not available
+ * with the random batch list (RBE_ERR_STATE).
+ *  skin      > 0: lists at r_list = r_c + skin (length units), rebuilt on the device when
+ *            a particle has moved by skin / 2 since the last build; 0: back to cell traversal
+ *  capacity  list entries per particle; 0 = automatic: n + 6 sqrt(n) + 32 rounded up to 8,
+ *            n = (N / V) 4/3 pi r_list^3 (and the same with N_q for the charged subset's
+ *            lists). A longer list sets RBE_ERR_CAPACITY (reported by the next synchronising
+ *            call) and its excess entries are dropped.
+ * Errors: RBE_ERR_INVALID (skin < 0, not finite, capacity < 0), RBE_ERR_CUTOFF (r_list >= L/2
+ * on an axis), RBE_ERR_CELLS (the cell grid cannot hold the build stencil: more than 3
+ * cells per side of r_list, or fewer than 2 R + 1 cells on an axis), RBE_ERR_OOM.
+ * Forces, energies and neighbour counts are those of the cell traversal (the same exact
+ * cutoff decision; FP32 sums in another order). Between builds the particle order is kept,
+ * so rbe_get_cells reports the cells of the last build. Discards the captured step graph. */
+int rbe_set_neighbor_list(rbe_handle h, double skin, int capacity);
+
+/* List statistics: stats[0] builds and stats[1] force evaluations since the list was
+ * enabled, stats[2] / stats[3] longest list of the last build (all particles / charged
+ * subset), stats[4] / stats[5] the capacities. Zeros when the list is off. Synchronises. */
+int rbe_get_neighbor_list(rbe_handle h, int64_t stats[6]);
 
 /* Throughput probe on the current device, for roofline denominators (it allocates 64
  * bytes of scratch and synchronises the device): kind 0 = FP32 FMA (flop/s, 2 per FMA),

@@ -21,8 +21,8 @@ RBE_OK = 0
 PRECISION = {"fp32_comp": 0, "fp32": 1, "fp64": 2}
 ENERGY_KEYS = ("real", "lj", "kspace", "self", "total", "kinetic")
 VIRIAL_KEYS = ("real", "lj", "kspace", "total")
-TUNABLES = {"pair_test16": 0, "sf_tile": 1}
-PHASES = ("kick_drift", "bin", "sample", "sf", "pair", "pair2", "gather", "tail")
+TUNABLES = {"pair_test16": 0, "sf_tile": 1, "rbl_eager": 2}
+PHASES = ("kick_drift", "bin", "sample", "sf", "list", "pair", "pair2", "gather", "tail")
 
 
 class RBEError(RuntimeError):
@@ -91,6 +91,8 @@ def lib(build_if_missing: bool = False):
     L.rbe_set_tuning.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
     L.rbe_get_tuning.argtypes = [ct.c_void_p, ct.c_int, _vp]
     L.rbe_autotune.argtypes = [ct.c_void_p, ct.c_int, _vp]
+    L.rbe_set_neighbor_list.argtypes = [ct.c_void_p, ct.c_double, ct.c_int]
+    L.rbe_get_neighbor_list.argtypes = [ct.c_void_p, _vp]
     L.rbe_structure_factor_noalloc.argtypes = [_vp, _vp, ct.c_int64, _vp, ct.c_int, _vp, _vp]
     L.rbe_destroy.argtypes = [h]
     L.rbe_error_string.argtypes = [ct.c_int]
@@ -310,9 +312,21 @@ class RBE:
         return v.value
 
     def autotune(self, reps: int = 3) -> dict:
-        ch = np.zeros(2, np.int32)
+        ch = np.zeros(len(TUNABLES), np.int32)
         _check(lib().rbe_autotune(self._h, reps, ch.ctypes.data), "rbe_autotune")
-        return {"pair_test16": int(ch[0]), "sf_tile": int(ch[1])}
+        return {k: int(ch[v]) for k, v in TUNABLES.items()}
+
+    def set_neighbor_list(self, skin: float, capacity: int = 0):
+        """Verlet list at r_c + skin (skin 0: per-step cell traversal)."""
+        _check(lib().rbe_set_neighbor_list(self._h, float(skin), int(capacity)),
+               "rbe_set_neighbor_list")
+
+    def neighbor_list_stats(self) -> dict:
+        st = np.zeros(6, np.int64)
+        _check(lib().rbe_get_neighbor_list(self._h, st.ctypes.data), "rbe_get_neighbor_list")
+        return dict(builds=int(st[0]), evaluations=int(st[1]), max_len=int(st[2]),
+                    max_len_charged=int(st[3]), capacity=int(st[4]),
+                    capacity_charged=int(st[5]))
 
     def memory_bytes(self) -> int:
         b = ct.c_int64()

@@ -8,6 +8,11 @@
 // Pipeline: count (atomics give a provisional slot) -> exclusive scan of the counts ->
 // provisional scatter -> per-cell rank by id + permute of every field (one warp per cell).
 // Integer work, HBM-bound.
+// With a Verlet neighbour list the order must stay fixed between list builds: every kernel
+// of the pipeline then reads a device gate (1 = rebuild this step) and returns at once when
+// it is 0, and an identity copy into the other buffer runs instead, so the buffers still
+// alternate every step. Both paths also write the packed (s_x, s_y, s_z, q) copies the list
+// kernels gather from.
 #include <climits>
 
 #include "rbe_internal.cuh"
@@ -18,12 +23,16 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 
+// true when a gated kernel has nothing to do this step
+__device__ __forceinline__ bool gated_off(const int32_t *gate) { return gate && *gate == 0; }
+
 __global__ void bin_count_kernel(int64_t N, const uint32_t *__restrict__ s,
                                  const float *__restrict__ q, int n0, int n1, int n2,
                                  int32_t *__restrict__ count, int32_t *__restrict__ ccount,
-                                 int32_t *__restrict__ key, int32_t *__restrict__ off) {
+                                 int32_t *__restrict__ key, int32_t *__restrict__ off,
+                                 const int32_t *__restrict__ gate) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || gated_off(gate)) return;
   const int cx = cell_of(s[i], n0), cy = cell_of(s[N + i], n1), cz = cell_of(s[2 * N + i], n2);
   const int c = cx + n0 * (cy + n1 * cz);
   key[i] = c;
@@ -34,8 +43,10 @@ __global__ void bin_count_kernel(int64_t N, const uint32_t *__restrict__ s,
 // Exclusive scan, three passes. Arrays hold two independent sequences (blockIdx.y).
 __global__ void __launch_bounds__(kScanThreads)
     scan_block_kernel(const int32_t *__restrict__ cnt, int32_t *__restrict__ start,
-                      int32_t *__restrict__ blk, int64_t ncell, int64_t nblk) {
+                      int32_t *__restrict__ blk, int64_t ncell, int64_t nblk,
+                      const int32_t *__restrict__ gate) {
   __shared__ int32_t warp_tot[kScanThreads / 32];
+  if (gated_off(gate)) return;
   const int which = blockIdx.y;
   const int32_t *in = cnt + which * ncell;
   int32_t *out = start + which * (ncell + 1);
@@ -80,9 +91,10 @@ __global__ void __launch_bounds__(kScanThreads)
 
 __global__ void __launch_bounds__(1024)
     scan_top_kernel(int32_t *__restrict__ blk, int64_t nblk, int32_t *__restrict__ start,
-                    int64_t ncell) {
+                    int64_t ncell, const int32_t *__restrict__ gate) {
   __shared__ int32_t warp_tot[32];
   __shared__ int32_t carry_s;
+  if (gated_off(gate)) return;
   const int which = blockIdx.x;
   int32_t *b = blk + which * nblk;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -122,7 +134,8 @@ __global__ void __launch_bounds__(1024)
 
 __global__ void __launch_bounds__(kScanThreads)
     scan_add_kernel(int32_t *__restrict__ start, const int32_t *__restrict__ blk,
-                    int64_t ncell, int64_t nblk) {
+                    int64_t ncell, int64_t nblk, const int32_t *__restrict__ gate) {
+  if (gated_off(gate)) return;
   const int which = blockIdx.y;
   int32_t *out = start + which * (ncell + 1);
   const int32_t add = blk[which * nblk + blockIdx.x];
@@ -135,9 +148,10 @@ __global__ void __launch_bounds__(kScanThreads)
 
 __global__ void bin_scatter_kernel(int64_t N, const int32_t *__restrict__ key,
                                    const int32_t *__restrict__ off,
-                                   const int32_t *__restrict__ start, int32_t *__restrict__ tmp) {
+                                   const int32_t *__restrict__ start, int32_t *__restrict__ tmp,
+                                   const int32_t *__restrict__ gate) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  if (i >= N || gated_off(gate)) return;
   tmp[start[key[i]] + off[i]] = (int32_t)i;
 }
 
@@ -153,6 +167,8 @@ struct PermuteArgs {
   const int32_t *ty0; int32_t *ty1;
   const float *im0; float *im1;
   uint32_t *cs; float *cqf; double *cqd; int32_t *cmap;
+  uint4 *s4, *cs4;        // packed (s_x, s_y, s_z, q bits) copies, nullable
+  const int32_t *gate;    // nullable: always run
 };
 
 // One warp per cell: rank members by id (and charged members among themselves), then move
@@ -160,7 +176,7 @@ struct PermuteArgs {
 __global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (c >= a.ncell) return;
+  if (c >= a.ncell || gated_off(a.gate)) return;
   const int32_t beg = a.cell_start[c];
   const int32_t cnt = a.cell_start[c + 1] - beg;
   const int32_t cbeg = a.ccell_start[c];
@@ -196,36 +212,67 @@ __global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
       if (a.qd0) a.qd1[p] = a.qd0[o];
       if (a.ty0) a.ty1[p] = a.ty0[o];
       a.im1[p] = a.im0[o];
+      if (a.s4) a.s4[p] = make_uint4(sx, sy, sz, __float_as_uint(qv));
       if (mych) {
         const int64_t pc = cbeg + crank;
         a.cs[pc] = sx; a.cs[Nq + pc] = sy; a.cs[2 * Nq + pc] = sz;
         a.cqf[pc] = qv;
         if (a.cqd) a.cqd[pc] = a.qd0[o];
         a.cmap[pc] = (int32_t)p;
+        if (a.cs4) a.cs4[pc] = make_uint4(sx, sy, sz, __float_as_uint(qv));
       }
     }
+  }
+}
+
+// Order kept (no list build this step): copy every field to the same slot of the other
+// buffer and refresh the charged subset's coordinates through cmap. Threads [0, N) copy
+// particles, threads [N, N + Nq) charged slots.
+__global__ void __launch_bounds__(256) bin_identity_kernel(PermuteArgs a) {
+  if (a.gate && *a.gate != 0) return;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t N = a.N, Nq = a.Nq;
+  if (k < N) {
+    const uint32_t sx = a.s0[k], sy = a.s0[N + k], sz = a.s0[2 * N + k];
+    a.s1[k] = sx; a.s1[N + k] = sy; a.s1[2 * N + k] = sz;
+    if (a.vf0) { a.vf1[k] = a.vf0[k]; a.vf1[N + k] = a.vf0[N + k]; a.vf1[2 * N + k] = a.vf0[2 * N + k]; }
+    if (a.vd0) { a.vd1[k] = a.vd0[k]; a.vd1[N + k] = a.vd0[N + k]; a.vd1[2 * N + k] = a.vd0[2 * N + k]; }
+    a.id1[k] = a.id0[k];
+    const float qv = a.qf0[k];
+    a.qf1[k] = qv;
+    if (a.qd0) a.qd1[k] = a.qd0[k];
+    if (a.ty0) a.ty1[k] = a.ty0[k];
+    a.im1[k] = a.im0[k];
+    if (a.s4) a.s4[k] = make_uint4(sx, sy, sz, __float_as_uint(qv));
+  } else if (k < N + Nq) {
+    const int64_t pc = k - N;
+    const int64_t p = a.cmap[pc];
+    const uint32_t sx = a.s0[p], sy = a.s0[N + p], sz = a.s0[2 * N + p];
+    a.cs[pc] = sx; a.cs[Nq + pc] = sy; a.cs[2 * Nq + pc] = sz;
+    if (a.cs4) a.cs4[pc] = make_uint4(sx, sy, sz, __float_as_uint(a.cqf[pc]));
   }
 }
 
 cudaError_t launch_bin_sort(Ctx &c) {
   const int64_t N = c.N, nc = c.grid.ncell;
   const int b0 = c.cur, b1 = 1 - c.cur;
+  const int32_t *gate = c.vl_on ? c.vl_flags : nullptr;  // list mode: sort only on a build
   cudaError_t e = cudaMemsetAsync(c.cell_count, 0, sizeof(int32_t) * 2 * nc, c.stream);
   if (e != cudaSuccess) return e;
   if (N > 0) {
     bin_count_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(
         N, c.s[b0], c.qf[b0], c.grid.n[0], c.grid.n[1], c.grid.n[2], c.cell_count,
-        c.ccell_count, c.key, c.off);
+        c.ccell_count, c.key, c.off, gate);
   }
   const int64_t nblk = c.scan_nblk;
   scan_block_kernel<<<dim3((unsigned)nblk, 2), kScanThreads, 0, c.stream>>>(
-      c.cell_count, c.cell_start, c.scan_blk, nc, nblk);
-  scan_top_kernel<<<2, 1024, 0, c.stream>>>(c.scan_blk, nblk, c.cell_start, nc);
+      c.cell_count, c.cell_start, c.scan_blk, nc, nblk, gate);
+  scan_top_kernel<<<2, 1024, 0, c.stream>>>(c.scan_blk, nblk, c.cell_start, nc, gate);
   scan_add_kernel<<<dim3((unsigned)nblk, 2), kScanThreads, 0, c.stream>>>(c.cell_start,
-                                                                         c.scan_blk, nc, nblk);
+                                                                         c.scan_blk, nc, nblk, gate);
   if (N > 0) {
     bin_scatter_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(
-        N, c.key, c.off, c.cell_start, c.tmp);
+        N, c.key, c.off, c.cell_start, c.tmp, gate);
     PermuteArgs a;
     a.N = N; a.Nq = c.Nq; a.ncell = nc;
     a.cell_start = c.cell_start; a.ccell_start = c.ccell_start; a.tmp = c.tmp;
@@ -238,8 +285,13 @@ cudaError_t launch_bin_sort(Ctx &c) {
     a.ty0 = c.type[b0]; a.ty1 = c.type[b1];
     a.im0 = c.invm[b0]; a.im1 = c.invm[b1];
     a.cs = c.cs; a.cqf = c.cqf; a.cqd = c.cqd; a.cmap = c.cmap;
+    a.s4 = c.vl_on ? c.s4 : nullptr;
+    a.cs4 = c.vl_on ? c.cs4 : nullptr;
+    a.gate = gate;
     const int64_t threads = nc * 32;
     bin_rank_permute_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(a);
+    if (gate)
+      bin_identity_kernel<<<(unsigned)((N + c.Nq + 255) / 256), 256, 0, c.stream>>>(a);
   }
   c.cur = b1;
   return cudaGetLastError();

@@ -20,6 +20,8 @@
 //     matches the oracle's decision bit for bit. Then it evaluates the pair force.
 // Forces are summed per i in a fixed j order with no atomics, so results are run-to-run
 // reproducible. The hot loop is FP32 ALU / SFU bound.
+// The BUILD variant walks the same windows with the list radius r_c + skin and, instead of
+// evaluating, appends each hit j (in the same candidate order) to i's Verlet list.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -32,7 +34,7 @@ constexpr int kMaxRows = 49;            // (2R+1)^2 stencil rows for R <= 3
 constexpr int kMaxSeg = 2 * kMaxRows;   // a row wraps into at most two runs of cells
 constexpr int kWin = 4;                 // chunks of 32 candidates staged per window
 
-template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16>
+template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
 __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a) {
   __shared__ float4 stage[kPairWarps][kWin][T16 ? 1 : 32];     // FP32 test coordinates
   __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
@@ -49,10 +51,13 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
   const int64_t i = i0 + lane;
   const bool valid = i < n;
   const LJTable *tab = a.table;
+  if (BUILD && *a.gate == 0) return;  // no list build this step (uniform over the grid)
   PairAcc<real> acc;
   acc.fx = acc.fy = acc.fz = acc.ulj = acc.wlj = acc.uc = acc.wc = (real)0;
   acc.cuc = acc.cwc = (real)0;
   acc.nbr = 0;
+  int cnt = 0;  // BUILD: list length of i
+  int32_t *lst = BUILD ? a.list + (i0 >> 5) * (int64_t)a.K * 32 + lane : nullptr;
   if (i0 < n) {
     const int n0 = a.grid.n[0], n1 = a.grid.n[1], n2 = a.grid.n[2];
     const int R0 = a.grid.R[0], R1 = a.grid.R[1], R2 = a.grid.R[2];
@@ -227,17 +232,33 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
           const int slot = (wb & ~31) + tt;
           const int32_t j = sj[slot];
           const int4 d = sd[slot];
-          real qj = (real)0;
-          if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[j] : (real)sq[slot];
-          pair_eval_masked<real, LJ, COUL, MULTI>(
-              a, tab, act && j != (int32_t)i, (int)((uint32_t)dxi - (uint32_t)d.x),
-              (int)((uint32_t)dyi - (uint32_t)d.y), (int)((uint32_t)dzi - (uint32_t)d.z), qi,
-              ti, qj, d.w, acc);
+          if (BUILD) {
+            const float ex = (float)(int)((uint32_t)dxi - (uint32_t)d.x) * a.pc.h[0];
+            const float ey = (float)(int)((uint32_t)dyi - (uint32_t)d.y) * a.pc.h[1];
+            const float ez = (float)(int)((uint32_t)dzi - (uint32_t)d.z) * a.pc.h[2];
+            const bool hit = act && j != (int32_t)i && ex * ex + ey * ey + ez * ez <= a.pc.rc2_hi;
+            if (hit && cnt < a.K) lst[(int64_t)cnt * 32] = j;
+            cnt += hit ? 1 : 0;
+          } else {
+            real qj = (real)0;
+            if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[j] : (real)sq[slot];
+            pair_eval_masked<real, LJ, COUL, MULTI>(
+                a, tab, act && j != (int32_t)i, (int)((uint32_t)dxi - (uint32_t)d.x),
+                (int)((uint32_t)dyi - (uint32_t)d.y), (int)((uint32_t)dzi - (uint32_t)d.z), qi,
+                ti, qj, d.w, acc);
+          }
         }
         __syncwarp();
       }
     }
-    if (valid) {
+    if (BUILD) {
+      if (valid) a.len[i] = min(cnt, a.K);
+      const int mx = __reduce_max_sync(FULL, valid ? cnt : 0);
+      if (lane == 0) {
+        atomicMax(a.maxlen, mx);
+        if (mx > a.K) atomicOr(a.err, ERRBIT_CAPACITY);
+      }
+    } else if (valid) {
       const int64_t o = a.set.map ? (int64_t)a.set.map[i] : i;
       const int64_t S = a.Fstride;
       if (sizeof(real) == 8) {
@@ -250,6 +271,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
       if (a.nbr) a.nbr[i] = acc.nbr;
     }
   }
+  if (BUILD) return;
   // block partials of the energies and virials (halves of the per-i sums)
   double v[NQ_PAIR] = {(double)acc.uc - (double)acc.cuc, (double)acc.ulj,
                        (double)acc.wc - (double)acc.cwc, (double)acc.wlj};
@@ -266,45 +288,45 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
   }
 }
 
-template <typename real, bool LJ, bool COUL>
+template <typename real, bool LJ, bool COUL, bool BUILD = false>
 static void launch_one(const PairArgs &a, int64_t n, bool multi, bool wrap, cudaStream_t st) {
   const unsigned blocks = (unsigned)((n + 32 * kPairWarps - 1) / (32 * kPairWarps));
   if (blocks == 0) return;
   const dim3 g(blocks), b(kPairWarps * 32);
   if (wrap) {
-    if (multi) pair_kernel<real, LJ, COUL, true, true, false><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, true, false><<<g, b, 0, st>>>(a);
+    if (multi) pair_kernel<real, LJ, COUL, true, true, false, BUILD><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, true, false, BUILD><<<g, b, 0, st>>>(a);
   } else if (a.smax16 > 0) {
-    if (multi) pair_kernel<real, LJ, COUL, true, false, true><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, false, true><<<g, b, 0, st>>>(a);
+    if (multi) pair_kernel<real, LJ, COUL, true, false, true, BUILD><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, false, true, BUILD><<<g, b, 0, st>>>(a);
   } else {
-    if (multi) pair_kernel<real, LJ, COUL, true, false, false><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, false, false><<<g, b, 0, st>>>(a);
+    if (multi) pair_kernel<real, LJ, COUL, true, false, false, BUILD><<<g, b, 0, st>>>(a);
+    else pair_kernel<real, LJ, COUL, false, false, false, BUILD><<<g, b, 0, st>>>(a);
   }
 }
 
-// Group x-extent (cells) for the half-precision test: every frame coordinate of a group and
-// its candidates stays below 64 scaled units (r_c = 8), i.e. 8 r_c in length; 0 disables
-// the half test (the FP32 test is used).
-int frame_span_cells_half(const Ctx &c, int smax) {
+// Group x-extent (cells) for the half-precision test at cutoff rc with stencil R: every
+// frame coordinate of a group and its candidates stays below 64 scaled units (rc = 8),
+// i.e. 8 rc in length; 0 disables the half test (the FP32 test is used).
+int frame_span_cells_half(const Ctx &c, int smax, double rc, const int *R) {
   if (smax < 1) return 0;
-  const double lim = 8.0 * c.rc * (1.0 - 1e-6);
+  const double lim = 8.0 * rc * (1.0 - 1e-6);
   for (int d = 1; d < 3; ++d)
-    if ((2 * c.grid.R[d] + 2) * (c.box[d] / c.grid.n[d]) >= lim) return 0;
+    if ((2 * R[d] + 2) * (c.box[d] / c.grid.n[d]) >= lim) return 0;
   const double ax = c.box[0] / c.grid.n[0];
-  const int s = (int)std::floor(lim / ax) - 2 * c.grid.R[0] - 1;
+  const int s = (int)std::floor(lim / ax) - 2 * R[0] - 1;
   return s >= 1 ? std::min(s, smax) : 0;
 }
 
-// Largest x-extent (in cells) of a group whose leader frame stays a valid minimum image;
-// 0 when even one cell is too wide (the wrapping variant is used then).
-int frame_span_cells(const Ctx &c) {
+// Largest x-extent (in cells) of a group whose leader frame stays a valid minimum image at
+// cutoff rc; 0 when even one cell is too wide (the wrapping variant is used then).
+int frame_span_cells(const Ctx &c, double rc) {
   for (int d = 1; d < 3; ++d) {
     const double a = c.box[d] / c.grid.n[d];
-    if (!(a + c.rc < 0.5 * c.box[d] * (1.0 - 1e-9))) return 0;
+    if (!(a + rc < 0.5 * c.box[d] * (1.0 - 1e-9))) return 0;
   }
   const double ax = c.box[0] / c.grid.n[0];
-  const int s = (int)std::floor((0.5 * c.box[0] * (1.0 - 1e-9) - c.rc) / ax);
+  const int s = (int)std::floor((0.5 * c.box[0] * (1.0 - 1e-9) - rc) / ax);
   return s >= 1 ? std::min(s, 1 << 20) : 0;
 }
 
@@ -328,10 +350,10 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   a.accumulate = 0;
   a.epart = c.epart + c.off_pair;
   a.nbr = want_counts ? c.nbr : nullptr;
-  a.smax = frame_span_cells(c);
+  a.smax = frame_span_cells(c, c.rc);
   a.comp = c.precision == RBE_FP32_COMP;
   a.scale16 = (float)(8.0 / c.rc);
-  a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax) : 0;
+  a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax, c.rc, c.grid.R) : 0;
   const bool wrap = a.smax == 0;
   for (int d = 0; d < 3; ++d) {
     a.L[d] = (float)c.box[d];
@@ -358,6 +380,44 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
       if (fp64) launch_one<double, false, true>(b2, c.Nq, false, wrap, c.stream);
       else launch_one<float, false, true>(b2, c.Nq, false, wrap, c.stream);
     }
+  }
+  return cudaGetLastError();
+}
+
+// Verlet-list build at r_list = r_c + skin over the full set and, when the Coulomb pass
+// runs separately, over the charged subset. Gated on the device rebuild flag.
+cudaError_t launch_list_build(Ctx &c) {
+  const int b = c.cur;
+  const bool fused = c.Nq * 2 > c.N;
+  PairArgs a{};
+  a.grid = c.grid;
+  for (int d = 0; d < 3; ++d) a.grid.R[d] = c.vl_R[d];
+  a.pc = c.pc;
+  const double rl = c.rc + c.vl_skin, rl2 = rl * rl;
+  a.pc.rc2d = rl2;
+  a.pc.rc2_lo = (float)(rl2 * (1.0 - 1e-5));
+  a.pc.rc2_hi = (float)(rl2 * (1.0 + 1e-5));
+  a.set.sx = c.s[b]; a.set.sy = c.s[b] + c.N; a.set.sz = c.s[b] + 2 * c.N;
+  a.set.qf = c.qf[b]; a.set.qd = c.qd[b]; a.set.type = nullptr;
+  a.set.cell_start = c.cell_start; a.set.map = nullptr; a.set.n = c.N;
+  a.smax = frame_span_cells(c, rl);
+  a.scale16 = (float)(8.0 / rl);
+  a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax, rl, c.vl_R) : 0;
+  const bool wrap = a.smax == 0;
+  for (int d = 0; d < 3; ++d) {
+    a.L[d] = (float)c.box[d];
+    a.invL[d] = (float)(1.0 / c.box[d]);
+  }
+  a.list = c.vl_list; a.len = c.vl_len; a.K = c.vl_K;
+  a.gate = c.vl_flags; a.maxlen = c.vl_flags + 2; a.err = c.err;
+  launch_one<float, false, false, true>(a, c.N, false, wrap, c.stream);
+  if (!fused && c.Nq > 0) {
+    PairArgs q = a;
+    q.set.sx = c.cs; q.set.sy = c.cs + c.Nq; q.set.sz = c.cs + 2 * c.Nq;
+    q.set.qf = c.cqf; q.set.qd = c.cqd; q.set.type = nullptr;
+    q.set.cell_start = c.ccell_start; q.set.map = c.cmap; q.set.n = c.Nq;
+    q.list = c.vl_listq; q.len = c.vl_lenq; q.K = c.vl_Kq; q.maxlen = c.vl_flags + 3;
+    launch_one<float, false, false, true>(q, c.Nq, false, wrap, c.stream);
   }
   return cudaGetLastError();
 }

@@ -19,6 +19,10 @@
 // the staged exact integer displacements (branch-light), and keeps per lane the number of
 // shell members of each 32-candidate chunk. Pass 2 draws, sorts the draws, and re-walks
 // only the chunks that hold them (same classification) to evaluate the drawn pairs.
+// Eager variant, for shells that are mostly no larger than p (dilute systems): pass 1 also
+// evaluates every shell pair, in canonical order, into a second accumulator. A particle
+// with #S_i <= p then keeps it (the same sum pass 2 would form, bit for bit) and skips
+// pass 2; one with #S_i > p discards it and draws as above.
 // The mean-force correction is a fixed-order FP64 reduction followed by a subtraction.
 #include <climits>
 
@@ -71,11 +75,11 @@ __device__ __forceinline__ void rbl_pair_ds(const RblArgs &a, const LJTable *tab
   pair_force_v<real, true, COUL, MULTI>(a.pa, tab, dx, dy, dz, r2, qi, ti, qj, tj, acc);
 }
 
-// Core or drawn-shell pair with a 0/1 activity mask (idle lanes compute a finite dummy).
+// One pair with a 0/1 activity mask (idle lanes compute a finite dummy with q_j = 0).
 template <typename real, bool COUL, bool MULTI>
-__device__ __forceinline__ void rbl_pair_masked(const RblArgs &a, const LJTable *tab, bool act,
-                                                int dsx, int dsy, int dsz, real qi, int ti,
-                                                real qj, int tj, PairAcc<real> &acc) {
+__device__ __forceinline__ PairAcc<real> rbl_pair_eval(const RblArgs &a, const LJTable *tab, bool act,
+                                                       int dsx, int dsy, int dsz, real qi, int ti,
+                                                       real qj, int tj) {
   const PairConst &pc = a.pa.pc;
   real dx, dy, dz;
   if (sizeof(real) == 8) {
@@ -91,18 +95,29 @@ __device__ __forceinline__ void rbl_pair_masked(const RblArgs &a, const LJTable 
   t.nbr = 0;
   pair_force_v<real, true, COUL, MULTI>(a.pa, tab, dx * on, dy * on, dz * on, r2s, qi, ti,
                                         act ? qj : (real)0, tj, t);
-  acc.fx += t.fx; acc.fy += t.fy; acc.fz += t.fz;
+  return t;
+}
+
+// acc += t where `on`, unchanged bit for bit otherwise.
+template <typename real>
+__device__ __forceinline__ void rbl_acc_add(const RblArgs &a, bool on_, const PairAcc<real> &t,
+                                            PairAcc<real> &acc) {
+  const real on = on_ ? (real)1 : (real)0;
+  acc.fx += on * t.fx; acc.fy += on * t.fy; acc.fz += on * t.fz;
   acc.ulj += on * t.ulj; acc.wlj += on * t.wlj;
-  if (a.pa.comp) {  // zero for idle lanes (q_j = 0)
-    kahan_add(acc.uc, acc.cuc, t.uc);
-    kahan_add(acc.wc, acc.cwc, t.wc);
+  if (a.pa.comp) {
+    real s = acc.uc, cs = acc.cuc, w = acc.wc, cw = acc.cwc;
+    kahan_add(s, cs, t.uc);
+    kahan_add(w, cw, t.wc);
+    acc.uc = on_ ? s : acc.uc; acc.cuc = on_ ? cs : acc.cuc;
+    acc.wc = on_ ? w : acc.wc; acc.cwc = on_ ? cw : acc.cwc;
   } else {
-    acc.uc += t.uc;
-    acc.wc += t.wc;
+    acc.uc += on * t.uc;
+    acc.wc += on * t.wc;
   }
 }
 
-template <typename real, bool COUL, bool MULTI, bool WRAP>
+template <typename real, bool COUL, bool MULTI, bool WRAP, bool EAGER>
 __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   __shared__ float4 stage[kRblWarps][kRblWin][32];
   __shared__ int4 stage_d[kRblWarps][kRblWin][32];
@@ -120,11 +135,12 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   const int64_t i = i0 + lane;
   const bool valid = i < n;
   const LJTable *tab = a.pa.table;
-  PairAcc<real> core, shell;
+  PairAcc<real> core, shell, shall;  // shall: every shell pair (eager variant)
   core.fx = core.fy = core.fz = core.ulj = core.wlj = core.uc = core.wc = (real)0;
   core.cuc = core.cwc = (real)0;
+  core.nbr = 0;
   shell = core;
-  core.nbr = shell.nbr = 0;
+  shall = core;
   real fx = 0, fy = 0, fz = 0;
   double en[NQ_PAIR] = {0.0, 0.0, 0.0, 0.0};
   if (i0 < n) {
@@ -136,7 +152,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
     const int ti = (MULTI && valid) ? S.type[i] : 0;
     const uint32_t idi = valid ? (uint32_t)a.id[i] : 0u;
     const int cx = cell_of(sxi, n0), cy = cell_of(syi, n1), cz = cell_of(szi, n2);
-    int ncore = 0, nsh = 0;
+    int ncore = 0, nsh = 0, ksh = 0;
     unsigned remaining = __ballot_sync(FULL, valid);
     while (remaining) {
       const int leader = __ffs(remaining) - 1;
@@ -241,28 +257,44 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           const int chunk = (base >> 5) + w;
           if (chunk < nchunks) ccount[wid][chunk][lane] = (uint8_t)__popc(mshell);
           nsh += __popc(mshell);
-          // core pairs, branch-light (the particle itself, r = 0, is skipped)
-          uint32_t bits = mcore;
+          // core pairs (and, eager, shell pairs), branch-light, in canonical order; the
+          // particle itself (r = 0, always core) is skipped
+          uint32_t bits = EAGER ? (mcore | mshell) : mcore;
           while (__any_sync(FULL, bits != 0u)) {
             const bool act = bits != 0u;
             const int tt = act ? __ffs(bits) - 1 : 0;
             bits &= bits - 1u;
             const int32_t j = stage_j[wid][w][tt];
             const bool use = act && j != (int32_t)i;
+            const bool is_core = ((mcore >> tt) & 1u) != 0u;
             const int4 d = stage_d[wid][w][tt];
             real qj = (real)0;
             if (COUL) qj = sizeof(real) == 8 ? (use ? (real)S.qd[j] : (real)0) : (real)stage_q[wid][w][tt];
-            ncore += use ? 1 : 0;
-            rbl_pair_masked<real, COUL, MULTI>(a, tab, use, (int)((uint32_t)dxi - (uint32_t)d.x),
-                                               (int)((uint32_t)dyi - (uint32_t)d.y),
-                                               (int)((uint32_t)dzi - (uint32_t)d.z), qi, ti, qj,
-                                               d.w, core);
+            ncore += (use && is_core) ? 1 : 0;
+            const PairAcc<real> t = rbl_pair_eval<real, COUL, MULTI>(
+                a, tab, use, (int)((uint32_t)dxi - (uint32_t)d.x), (int)((uint32_t)dyi - (uint32_t)d.y),
+                (int)((uint32_t)dzi - (uint32_t)d.z), qi, ti, qj, d.w);
+            rbl_acc_add(a, use && is_core, t, core);
+            if (EAGER) {
+              rbl_acc_add(a, use && !is_core, t, shall);
+              if (a.partners && use && !is_core) {  // shell rank ksh in canonical order
+                if (ksh < a.p) a.partners[i * a.p + ksh] = a.id[j];
+                ++ksh;
+              }
+            }
           }
         }
         __syncwarp();
       }
-      // ---- pass 2: the drawn shell partners (all of them when #S_i <= p)
-      if (in) {
+      // ---- pass 2: the drawn shell partners (all of them when #S_i <= p; the eager
+      //      variant has that sum, and the partners, already and runs pass 2 only to draw)
+      const bool pass2 = in && (!EAGER || nsh > a.p);
+      if (EAGER && in && !pass2) {
+        shell = shall;
+        if (a.partners)
+          for (int t = nsh; t < a.p; ++t) a.partners[i * a.p + t] = -1;
+      }
+      if (pass2) {
         uint32_t idx[kRblMaxP];
         int ord[kRblMaxP];
         int ndraw;
@@ -320,8 +352,9 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
             while (ptr < ndraw && idx[ord[ptr]] == (uint32_t)k) {
               real qj = (real)0;
               if (COUL) qj = sizeof(real) == 8 ? (real)S.qd[j] : (real)S.qf[j];
-              rbl_pair_masked<real, COUL, MULTI>(a, tab, true, dsx, dsy, dsz, qi, ti, qj,
-                                                 MULTI ? S.type[j] : 0, shell);
+              const PairAcc<real> t = rbl_pair_eval<real, COUL, MULTI>(
+                  a, tab, true, dsx, dsy, dsz, qi, ti, qj, MULTI ? S.type[j] : 0);
+              rbl_acc_add(a, true, t, shell);
               if (a.partners) a.partners[i * a.p + ord[ptr]] = a.id[j];
               ++ptr;
             }
@@ -394,15 +427,27 @@ __global__ void rbl_subtract_kernel(real *__restrict__ F, int64_t N, const doubl
 
 int64_t rbl_blocks(int64_t n) { return (n + 32 * kRblWarps - 1) / (32 * kRblWarps); }
 
-template <typename real, bool COUL>
+template <typename real, bool COUL, bool EAGER>
 static void rbl_launch(const RblArgs &a, int64_t blocks, bool multi, bool wrap, cudaStream_t st) {
   const dim3 g((unsigned)blocks), b(kRblWarps * 32);
   if (wrap) {
-    if (multi) rbl_kernel<real, COUL, true, true><<<g, b, 0, st>>>(a);
-    else rbl_kernel<real, COUL, false, true><<<g, b, 0, st>>>(a);
+    if (multi) rbl_kernel<real, COUL, true, true, EAGER><<<g, b, 0, st>>>(a);
+    else rbl_kernel<real, COUL, false, true, EAGER><<<g, b, 0, st>>>(a);
   } else {
-    if (multi) rbl_kernel<real, COUL, true, false><<<g, b, 0, st>>>(a);
-    else rbl_kernel<real, COUL, false, false><<<g, b, 0, st>>>(a);
+    if (multi) rbl_kernel<real, COUL, true, false, EAGER><<<g, b, 0, st>>>(a);
+    else rbl_kernel<real, COUL, false, false, EAGER><<<g, b, 0, st>>>(a);
+  }
+}
+
+template <typename real>
+static void rbl_launch(const RblArgs &a, int64_t blocks, bool coul, bool eager, bool multi,
+                       bool wrap, cudaStream_t st) {
+  if (coul) {
+    if (eager) rbl_launch<real, true, true>(a, blocks, multi, wrap, st);
+    else rbl_launch<real, true, false>(a, blocks, multi, wrap, st);
+  } else {
+    if (eager) rbl_launch<real, false, true>(a, blocks, multi, wrap, st);
+    else rbl_launch<real, false, false>(a, blocks, multi, wrap, st);
   }
 }
 
@@ -445,13 +490,8 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   }
   pa.smax = 1;
   pa.comp = c.precision == RBE_FP32_COMP;
-  if (c.precision == RBE_FP64) {
-    if (coul) rbl_launch<double, true>(a, blocks, multi, wrap, c.stream);
-    else rbl_launch<double, false>(a, blocks, multi, wrap, c.stream);
-  } else {
-    if (coul) rbl_launch<float, true>(a, blocks, multi, wrap, c.stream);
-    else rbl_launch<float, false>(a, blocks, multi, wrap, c.stream);
-  }
+  if (c.precision == RBE_FP64) rbl_launch<double>(a, blocks, coul, c.rbl_eager, multi, wrap, c.stream);
+  else rbl_launch<float>(a, blocks, coul, c.rbl_eager, multi, wrap, c.stream);
   mark(c, RBE_PH_PAIR2);
   rbl_mean_kernel<<<1, 256, 0, c.stream>>>(c.rbl_part, blocks, c.N, c.rbl_mean);
   const unsigned nb = (unsigned)((c.N + 255) / 256);

@@ -37,6 +37,15 @@ struct PairArgs {
   // neighbour is rejected; the exact decision is taken again when the pair is evaluated.
   float scale16;
   int smax16;
+  // Verlet-list build (the cell kernel's BUILD variant): pc's cutoff fields then hold
+  // r_list = r_c + skin, and every j != i with r_ij^2 <= r_list^2 (1 + 1e-5) in FP32 is
+  // appended to i's list: warp-interleaved, entry t of the particle in slot i at
+  // list[((i / 32) * K + t) * 32 + i % 32].
+  int32_t *list, *len;
+  int K;
+  const int32_t *gate;   // build only when *gate != 0
+  int32_t *maxlen;       // longest list (atomic max)
+  int *err;
 };
 
 // Fold a coordinate difference into [-L/2, L/2) (only the small-box variants use it).

@@ -124,6 +124,8 @@ int free_all(Ctx &c) {
   dfree(c.err); dfree(c.nbr); dfree(c.nshell); dfree(c.partners); dfree(c.rbl_mean);
   dfree(c.rbl_part); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
   dfree(c.thermo);
+  dfree(c.vl_list); dfree(c.vl_len); dfree(c.vl_listq); dfree(c.vl_lenq); dfree(c.vl_ref);
+  dfree(c.s4); dfree(c.cs4); dfree(c.vl_flags); dfree(c.vl_count);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   c.cap_stream = nullptr;
   if (c.scal_host) cudaFreeHost(c.scal_host);
@@ -131,16 +133,24 @@ int free_all(Ctx &c) {
   return RBE_OK;
 }
 
-// bin + sort -> sample -> structure factor -> real space -> k-space gather
+// [list check] -> bin + sort -> sample -> structure factor -> [list build] -> real space
+// -> k-space gather
 int force_pipeline(Ctx &c, bool debug) {
   mark(c, RBE_PH_BIN);
+  if (c.vl_on) RBE_CUDA_TRY(launch_list_check(c));
   RBE_CUDA_TRY(launch_bin_sort(c));
   mark(c, RBE_PH_SAMPLE);
   RBE_CUDA_TRY(launch_sample_k(c));
   mark(c, RBE_PH_SF);
   RBE_CUDA_TRY(launch_structure_factor(c));
+  mark(c, RBE_PH_LIST);
+  if (c.vl_on) {
+    RBE_CUDA_TRY(launch_list_build(c));
+    RBE_CUDA_TRY(launch_list_commit(c));
+  }
   mark(c, RBE_PH_PAIR);
   if (c.rbl) RBE_CUDA_TRY(launch_rbl(c, debug));
+  else if (c.vl_on) RBE_CUDA_TRY(launch_list_pair(c, debug));
   else RBE_CUDA_TRY(launch_pair(c, debug));
   mark(c, RBE_PH_GATHER);
   RBE_CUDA_TRY(launch_kspace_gather(c));
@@ -156,6 +166,8 @@ int64_t kernels_per_step(const Ctx &c) {
   k += c.Nq > 0 ? 2 : 0;                 // structure factor + combine
   if (c.rbl) k += 3;                     // RBL, mean, subtract
   else k += (c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2;  // pair passes
+  if (c.vl_on)                           // check, identity copy, build(s), commit
+    k += 3 + ((c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2);
   k += c.Nq > 0 ? 1 : 0;                 // gather
   k += 2;                                // kick (+kinetic), totals
   if (c.nvt) k += 2;                     // thermostat, end-of-step velocity scaling
@@ -256,7 +268,9 @@ const char *rbe_error_string(int code) {
     case RBE_ERR_SAMPLER: return "mode sampler drew k = 0 in 64 consecutive attempts";
     case RBE_ERR_NONFINITE: return "non-finite or runaway position update";
     case RBE_ERR_STATE: return "call not valid in the current state";
-    case RBE_ERR_CAPACITY: return "an RBL neighbour stencil held more than 6144 candidates";
+    case RBE_ERR_CAPACITY:
+      return "neighbour capacity exceeded (RBL stencil over 6144 candidates, or a Verlet "
+             "list over its capacity: raise it with rbe_set_neighbor_list)";
     default: return "unknown error";
   }
 }
@@ -306,6 +320,12 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   c.stream = (cudaStream_t)cuda_stream;
   c.sum_q2 = q2;
   c.U_self = c.C * std::sqrt(c.alpha / kPi) * q2;
+  if (rbl) {  // eager shell evaluation when the mean shell holds no more than p particles
+    const double vol = box[0] * box[1] * box[2];
+    const double shell_mean = (double)N / vol * (4.0 / 3.0) * kPi *
+                              (c.rc * c.rc * c.rc - c.r_core * c.r_core * c.r_core);
+    c.rbl_eager = shell_mean <= (double)c.p_rbl;
+  }
 
   // cell grid
   if (rbl) {
@@ -541,6 +561,8 @@ int rbe_set_positions(rbe_handle h, const double *pos, int on_device) {
   RBE_CUDA_TRY(cudaMemcpyAsync(c.pos_stage, pos, sizeof(double) * 3 * c.N,
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                c.stream));
+  // (a Verlet list stays valid: new positions are written in the kept order, and the next
+  //  displacement check against the build positions decides whether to rebuild)
   RBE_CUDA_TRY(launch_set_positions(c));
   c.have_forces = false;
   return RBE_OK;
@@ -828,6 +850,9 @@ int rbe_set_tuning(rbe_handle h, int key, int value) {
   if (key == RBE_TUNE_PAIR_TEST16) {
     if (value != 0 && value != 1) return RBE_ERR_INVALID;
     c.pair_test16 = value != 0;
+  } else if (key == RBE_TUNE_RBL_EAGER) {
+    if (value != 0 && value != 1) return RBE_ERR_INVALID;
+    c.rbl_eager = value != 0;
   } else if (key == RBE_TUNE_SF_TILE) {
     if (value < 32 || value > 1024 || value % 32) return RBE_ERR_INVALID;
     // the partial buffer was sized for the initial tile; smaller tiles need more blocks
@@ -845,6 +870,7 @@ int rbe_get_tuning(rbe_handle h, int key, int *value) {
   if (!h || !value) return RBE_ERR_INVALID;
   if (key == RBE_TUNE_PAIR_TEST16) *value = h->pair_test16 ? 1 : 0;
   else if (key == RBE_TUNE_SF_TILE) *value = h->sf_tile;
+  else if (key == RBE_TUNE_RBL_EAGER) *value = h->rbl_eager ? 1 : 0;
   else return RBE_ERR_INVALID;
   return RBE_OK;
 }
@@ -882,6 +908,17 @@ int rbe_autotune(rbe_handle h, int reps, int *chosen) {
     if (v == 0 || ms < best) { best = ms; best16 = v; }
   }
   c.pair_test16 = best16 != 0;
+  int best_eager = c.rbl_eager ? 1 : 0;
+  if (c.rbl) {
+    for (int v = 0; v <= 1; ++v) {
+      c.rbl_eager = v != 0;
+      float ms = 0.f;
+      int rc = time_forces(c, reps, &ms);
+      if (rc != RBE_OK) { c.timing = saved_timing; return rc; }
+      if (v == 0 || ms < best) { best = ms; best_eager = v; }
+    }
+    c.rbl_eager = best_eager != 0;
+  }
   int best_tile = c.sf_tile;
   best = 0.f;
   bool first = true;
@@ -907,7 +944,99 @@ int rbe_autotune(rbe_handle h, int reps, int *chosen) {
   c.timing = saved_timing;
   drop_graphs(c);
   c.have_forces = false;
-  if (chosen) { chosen[0] = best16; chosen[1] = best_tile; }
+  if (chosen) { chosen[0] = best16; chosen[1] = best_tile; chosen[2] = best_eager; }
+  return RBE_OK;
+}
+
+static void free_list(Ctx &c) {
+  dfree(c.vl_list); dfree(c.vl_len); dfree(c.vl_listq); dfree(c.vl_lenq); dfree(c.vl_ref);
+  dfree(c.s4); dfree(c.cs4); dfree(c.vl_flags); dfree(c.vl_count);
+  c.vl_list = c.vl_len = c.vl_listq = c.vl_lenq = nullptr;
+  c.vl_ref = nullptr;
+  c.s4 = c.cs4 = nullptr;
+  c.vl_flags = nullptr;
+  c.vl_count = nullptr;
+  c.bytes -= c.vl_bytes;
+  c.vl_bytes = 0;
+  c.vl_on = false;
+  c.vl_skin = 0.0;
+  c.vl_K = c.vl_Kq = 0;
+}
+
+// Automatic list capacity for a mean of n entries.
+static int list_capacity(double n) {
+  const double k = n + 6.0 * std::sqrt(n) + 32.0;
+  return (int)(std::ceil(k / 8.0) * 8.0);
+}
+
+int rbe_set_neighbor_list(rbe_handle h, double skin, int capacity) {
+  if (!h) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  if (!std::isfinite(skin) || skin < 0.0 || capacity < 0) return RBE_ERR_INVALID;
+  if (c.rbl) return RBE_ERR_STATE;
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  drop_graphs(c);
+  c.have_forces = false;
+  free_list(c);
+  if (skin == 0.0) return RBE_OK;
+  const double rl = c.rc + skin;
+  int R[3];
+  for (int d = 0; d < 3; ++d) {
+    if (!(rl < 0.5 * c.box[d])) return RBE_ERR_CUTOFF;
+    const double a = c.box[d] / c.grid.n[d];
+    R[d] = (int)std::ceil(rl / a);
+    if (R[d] > 3 || c.grid.n[d] < 2 * R[d] + 1) return RBE_ERR_CELLS;
+  }
+  const double vol = c.box[0] * c.box[1] * c.box[2];
+  const double sph = 4.0 / 3.0 * kPi * rl * rl * rl;
+  const int K = capacity > 0 ? capacity : list_capacity((double)c.N / vol * sph);
+  const int Kq = capacity > 0 ? capacity : list_capacity((double)c.Nq / vol * sph);
+  const int64_t Np = (c.N + 31) / 32 * 32, Nqp = (c.Nq + 31) / 32 * 32;
+  const int64_t before = c.bytes;
+  int rc = RBE_OK;
+  rc |= dalloc(c, &c.vl_list, Np * (int64_t)K);
+  rc |= dalloc(c, &c.vl_len, c.N);
+  rc |= dalloc(c, &c.vl_listq, Nqp * (int64_t)Kq);
+  rc |= dalloc(c, &c.vl_lenq, c.Nq);
+  rc |= dalloc(c, &c.vl_ref, 3 * c.N);
+  rc |= dalloc(c, &c.s4, c.N);
+  rc |= dalloc(c, &c.cs4, c.Nq);
+  rc |= dalloc(c, &c.vl_flags, 8);
+  rc |= dalloc(c, &c.vl_count, 2);
+  c.vl_bytes = c.bytes - before;
+  if (rc != RBE_OK) {
+    free_list(c);
+    return RBE_ERR_OOM;
+  }
+  RBE_CUDA_TRY(cudaMemsetAsync(c.vl_flags, 0, sizeof(int32_t) * 8, c.stream));
+  RBE_CUDA_TRY(cudaMemsetAsync(c.vl_flags + 1, 1, sizeof(int32_t), c.stream));  // build first
+  RBE_CUDA_TRY(cudaMemsetAsync(c.vl_count, 0, sizeof(unsigned long long) * 2, c.stream));
+  RBE_CUDA_TRY(cudaMemsetAsync(c.vl_ref, 0, sizeof(uint32_t) * 3 * c.N, c.stream));
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  c.vl_on = true;
+  c.vl_skin = skin;
+  c.vl_K = K;
+  c.vl_Kq = Kq;
+  for (int d = 0; d < 3; ++d) c.vl_R[d] = R[d];
+  return RBE_OK;
+}
+
+int rbe_get_neighbor_list(rbe_handle h, int64_t stats[6]) {
+  if (!h || !stats) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  for (int k = 0; k < 6; ++k) stats[k] = 0;
+  if (!c.vl_on) return RBE_OK;
+  int32_t fl[8];
+  unsigned long long cnt[2];
+  RBE_CUDA_TRY(cudaMemcpyAsync(fl, c.vl_flags, sizeof(fl), cudaMemcpyDeviceToHost, c.stream));
+  RBE_CUDA_TRY(cudaMemcpyAsync(cnt, c.vl_count, sizeof(cnt), cudaMemcpyDeviceToHost, c.stream));
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  stats[0] = (int64_t)cnt[0];
+  stats[1] = (int64_t)cnt[1];
+  stats[2] = fl[4];
+  stats[3] = fl[5];
+  stats[4] = c.vl_K;
+  stats[5] = c.vl_Kq;
   return RBE_OK;
 }
 

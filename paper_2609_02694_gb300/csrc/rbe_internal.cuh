@@ -73,6 +73,7 @@ struct Ctx {
   double alpha = 0, rc = 0, r_core = 0, C = 0, dt = 0, kappa = 0;
   int P = 0, p_rbl = 0, precision = RBE_FP32_COMP, nt = 1, sub = 2;
   bool pair_test16 = true;  // packed half-precision candidate pre-test in the pair kernel
+  bool rbl_eager = false;   // RBL: evaluate every shell pair in the classifying pass
   uint64_t seed = 0;
   uint32_t replica = 0;
   bool rbl = false;
@@ -143,6 +144,18 @@ struct Ctx {
   bool nvt = false, nvt_primed = false;
   double T0 = 0, tau = 0, kB = 0, Qnh = 0, Nf = 0;
   double *thermo = nullptr;
+  // Verlet neighbour list (cell-list real space only): lists warp-interleaved, K entries a
+  // particle; vl_flags / vl_count as described in k_list.cu
+  bool vl_on = false;
+  double vl_skin = 0;
+  int vl_K = 0, vl_Kq = 0;
+  int vl_R[3] = {0, 0, 0};           // stencil of the build at r_c + skin
+  int32_t *vl_list = nullptr, *vl_len = nullptr, *vl_listq = nullptr, *vl_lenq = nullptr;
+  uint32_t *vl_ref = nullptr;        // positions at the last build, 3N, sorted order
+  uint4 *s4 = nullptr, *cs4 = nullptr;  // packed (s_x, s_y, s_z, q bits): full, charged set
+  int32_t *vl_flags = nullptr;       // 8 ints
+  unsigned long long *vl_count = nullptr;  // builds, force evaluations
+  int64_t vl_bytes = 0;
   // graph
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per starting buffer parity
   cudaStream_t cap_stream = nullptr;  // internal non-blocking stream used only for capture
@@ -213,6 +226,10 @@ cudaError_t launch_kspace_gather(Ctx &c);
 cudaError_t launch_pair(Ctx &c, bool want_counts);   // main pass, then mark, then Coulomb pass
 void mark(Ctx &c, int k);  // record the profiling event k (no-op when profiling is off)
 cudaError_t launch_rbl(Ctx &c, bool want_debug);
+cudaError_t launch_list_check(Ctx &c);    // rebuild flag from the displacements
+cudaError_t launch_list_build(Ctx &c);    // gated list build(s) at r_c + skin
+cudaError_t launch_list_commit(Ctx &c);   // gated: reference positions, counters
+cudaError_t launch_list_pair(Ctx &c, bool want_counts);  // pair forces from the lists
 cudaError_t launch_kick_drift(Ctx &c);
 cudaError_t launch_kick(Ctx &c);
 cudaError_t launch_kinetic(Ctx &c);

@@ -234,6 +234,31 @@ def test_rbl_small_shell_takes_all(orc):
     assert rel_l2(F, ex["F"]) < TOL_F32
 
 
+def test_rbl_eager_shell_bit_identical(orc):
+    """Shells of mean size ~p: the eager variant (shell pairs summed while classifying) and
+    the draw pass give bit-identical forces, energies, counts and partners, and match the
+    oracle's draws."""
+    sy = synth.make_system(12000, density=0.1, frac_charged=0.1, seed=8)
+    p, r_core, r_c, seed, step = 30, 4.5, 5.2, 2, 3
+    out = {}
+    for eager in (0, 1):
+        with handle(sy, 64, r_core=r_core, p_rbl=p, r_c=r_c, seed=seed) as h:
+            h.set_tuning("rbl_eager", eager)
+            assert h.get_tuning("rbl_eager") == eager
+            F, E, W = h.forces_f64(step)
+            out[eager] = (F, E, W, *h.neighbor_counts(), h.rbl_partners())
+    F0, E0, W0, nc0, ns0, pa0 = out[0]
+    F1, E1, W1, nc1, ns1, pa1 = out[1]
+    assert np.array_equal(F0, F1)
+    assert E0 == E1 and W0 == W1
+    assert np.array_equal(nc0, nc1) and np.array_equal(ns0, ns1) and np.array_equal(pa0, pa1)
+    assert (ns0 <= p).any() and (ns0 > p).any()  # both branches taken
+    ref = orc.rbl(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, r_c, p, seed, step, 0, C,
+                  sy.eps, sy.sig)
+    assert np.array_equal(ns1, ref["n_shell"])
+    assert np.array_equal(pa1, ref["partners"])
+
+
 # -------------------------------------------------------------------------- Verlet
 
 
