@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--skin", type=float, default=None,
                     help="Verlet-list skin (A); 0 = cell traversal; default: timed trial of "
                          "0, 0.5, 1.0, 1.5 on the workload itself")
+    ap.add_argument("--ljelec-sizes", default="200000,1400000,7000000,28000000",
+                    help="ion counts of --config ljelec")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 form, e2e, error and CPU legs (profiling runs)")
     ap.add_argument("--config", default="main",
@@ -585,7 +587,7 @@ def run_ljelec(args):
     stream = torch.cuda.current_stream()
     peaks = measured_peaks()
     prm = synth.LJ_ELECTROLYTE
-    for N in (200000, 1400000, 7000000, 28000000):
+    for N in [int(x) for x in args.ljelec_sizes.split(",")]:
         sy = synth.lj_electrolyte(N)
         h = binding.from_system(sy, P=prm["P"], alpha=prm["alpha"], r_c=prm["r_c"],
                                 r_core=prm["r_core"], p_rbl=prm["p_rbl"],

@@ -200,8 +200,12 @@ int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kernels_per_step);
  *  RBE_TUNE_RBL_EAGER    random batch list only. 1: the classifying pass evaluates every shell
  *                        pair too, and a particle with #S_i <= p keeps that sum (bit-identical
  *                        to the draw pass); 0: shell pairs only in the draw pass. The default
- *                        is 1 when the mean shell size N/V * 4/3 pi (r_s^3 - r_core^3) <= p. */
-enum { RBE_TUNE_PAIR_TEST16 = 0, RBE_TUNE_SF_TILE = 1, RBE_TUNE_RBL_EAGER = 2, RBE_N_TUNE = 3 };
+ *                        is 1 when the mean shell size N/V * 4/3 pi (r_s^3 - r_core^3) <= p.
+ *  RBE_TUNE_RBL_SPAN     random batch list only: cells in x that one warp's particle group may
+ *                        span (1..14; 0 = automatic, floor(32 / particles per cell), at least 1,
+ *                        at most n_x - 2). Results are bit-identical for every span. */
+enum { RBE_TUNE_PAIR_TEST16 = 0, RBE_TUNE_SF_TILE = 1, RBE_TUNE_RBL_EAGER = 2,
+       RBE_TUNE_RBL_SPAN = 3, RBE_N_TUNE = 4 };
 int rbe_set_tuning(rbe_handle h, int key, int value);
 int rbe_get_tuning(rbe_handle h, int key, int *value);
 

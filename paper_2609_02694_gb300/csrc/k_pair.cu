@@ -158,8 +158,10 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
             const float fy = (float)dyj * a.pc.h[1];
             const float fz = (float)dzj * a.pc.h[2];
             if (T16) {
-              __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane >> 1]);
-              const int o = lane & 1;
+              // entry p packs candidates p (low halves) and p + 16 (high halves), so that
+              // bit b of the test mask is candidate b
+              __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
+              const int o = lane >> 4;
               h[o] = __float2half_rn(fx * a.scale16);
               h[2 + o] = __float2half_rn(fy * a.scale16);
               h[4 + o] = __float2half_rn(fz * a.scale16);
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
           uint32_t mask = 0u;
           if (nj > 0) {
             if (T16) {
-              // bit p: candidate 2p, bit 16 + p: candidate 2p + 1
+              // bit p: candidate p, bit 16 + p: candidate p + 16
 #pragma unroll
               for (int pp = 0; pp < 16; ++pp) {
                 const uint4 v = stage16[wid][w][pp];
@@ -188,11 +190,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
                 const __half2 dy2 = __hsub2(yi2, *reinterpret_cast<const __half2 *>(&v.y));
                 const __half2 dz2 = __hsub2(zi2, *reinterpret_cast<const __half2 *>(&v.z));
                 const __half2 r2 = __hfma2(dx2, dx2, __hfma2(dy2, dy2, __hmul2(dz2, dz2)));
-                mask |= (__hlt2_mask(r2, thr2) & 0x00010001u) << pp;
+                mask |= __hlt2_mask(r2, thr2) & (0x00010001u << pp);  // one LOP3 (pp unrolled)
               }
-              const uint32_t ve = (1u << ((nj + 1) >> 1)) - 1u;
-              const uint32_t vo = nj >= 32 ? 0xFFFF0000u : ((1u << (nj >> 1)) - 1u) << 16;
-              mask &= ve | vo;
+              if (nj < 32) mask &= (1u << nj) - 1u;
             } else {
 #pragma unroll
               for (int tt = 0; tt < 32; ++tt) {
@@ -226,10 +226,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
           const uint64_t rest = bits & (bits - 1ull);
           mA = useA ? rest : mA;
           mB = useA ? mB : rest;
-          const int wb = (useA ? 0 : 64) + b;
-          const int bb = wb & 31;
-          const int tt = T16 ? (((bb & 15) << 1) | (bb >> 4)) : bb;
-          const int slot = (wb & ~31) + tt;
+          const int slot = (useA ? 0 : 64) + b;  // window slot = chunk * 32 + candidate
           const int32_t j = sj[slot];
           const int4 d = sd[slot];
           if (BUILD) {

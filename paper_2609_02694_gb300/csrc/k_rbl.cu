@@ -11,9 +11,13 @@
 // (t mod 4) of Philox4x32-10 with counter (id_i, t / 4, step, 1). When #S_i <= p the whole
 // shell enters with weight 1.
 //
-// Work decomposition: one thread per i. Lanes of a warp that share a cell walk that
-// cell's 27 neighbours together. Candidates are staged in shared memory in FP32
-// coordinates relative to the group leader. Membership is decided exactly: FP32 outside
+// Work decomposition: one thread per i. Lanes of a warp whose cells share a row (c_y, c_z)
+// and lie within `gs` cells in x form a group; gs > 1 only in dilute systems, so that a
+// group fills the warp. The group walks the union of its members' 27-cell stencils: the
+// 9 rows (dz, dy) in canonical order, each a run of gs + 2 cells in x. Every candidate
+// carries its x offset in that run, and a lane keeps only candidates of its own three x
+// cells; in canonical order these form exactly the lane's own S_i order. Candidates are
+// staged in shared memory in FP32 coordinates relative to the group leader. Membership is decided exactly: FP32 outside
 // a +-1e-5 band around r_core^2 and r_s^2, the FP64 oracle expression inside it.
 // Pass 1 classifies every candidate once in canonical order, evaluates the core pairs from
 // the staged exact integer displacements (branch-light), and keeps per lane the number of
@@ -24,7 +28,9 @@
 // with #S_i <= p then keeps it (the same sum pass 2 would form, bit for bit) and skips
 // pass 2; one with #S_i > p discards it and draws as above.
 // The mean-force correction is a fixed-order FP64 reduction followed by a subtraction.
+#include <algorithm>
 #include <climits>
+#include <cmath>
 
 #include "pair_common.cuh"
 
@@ -33,7 +39,8 @@ namespace rbe {
 constexpr int kRblWarps = 4;
 constexpr int kRblMaxP = 32;
 constexpr int kRblWin = 4;          // chunks of 32 candidates per window
-constexpr int kRblMaxChunks = 192;  // candidates per group <= 6144 (27 cells)
+constexpr int kRblMaxChunks = 192;  // candidates per group <= 6144
+constexpr int kRblMaxSpan = 14;     // x cells per group (gs)
 
 struct RblArgs {
   PairArgs pa;
@@ -46,7 +53,16 @@ struct RblArgs {
   double *fsum_part;   // per block: sum of F~ (3 doubles)
   int32_t *ncore, *nshell, *partners;  // sorted order, nullable
   int *err;
+  int gs;  // group extent in x cells (1 .. kRblMaxSpan, gs + 2 <= n_x)
 };
+
+// x offset of cell cxj in the group's run of cells gx - 1 .. gx + gs (mod n_x)
+__device__ __forceinline__ int run_offset(int cxj, int gx, int n0) {
+  int d = cxj - gx + 1;  // in [-(n0 - 2), n0]
+  d += d < 0 ? n0 : 0;
+  d -= d >= n0 ? n0 : 0;
+  return d;
+}
 
 // Coarse FP32 classes with the exact FP64 decision inside the +-1e-5 bands of r_core^2 and
 // r_s^2: 0 outside, 1 core (r <= r_core), 2 shell (r_core < r <= r_s).
@@ -123,8 +139,9 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   __shared__ int4 stage_d[kRblWarps][kRblWin][32];
   __shared__ float stage_q[kRblWarps][kRblWin][32];
   __shared__ int32_t stage_j[kRblWarps][kRblWin][32];
-  __shared__ int32_t seg_beg[kRblWarps][27];
-  __shared__ int32_t seg_pre[kRblWarps][28];
+  __shared__ int32_t seg_beg[kRblWarps][18];
+  __shared__ int32_t seg_pre[kRblWarps][19];
+  __shared__ uint32_t tmask[kRblWarps][kRblWin][kRblMaxSpan + 2];  // candidates per x offset
   __shared__ uint8_t ccount[kRblWarps][kRblMaxChunks][32];  // shell members per chunk, per lane
   __shared__ double wred[kRblWarps][NQ_PAIR + 3];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -135,12 +152,13 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   const int64_t i = i0 + lane;
   const bool valid = i < n;
   const LJTable *tab = a.pa.table;
-  PairAcc<real> core, shell, shall;  // shall: every shell pair (eager variant)
+  // shell: the drawn shell pairs; in the eager variant first every shell pair, reset when
+  // the particle turns out to need draws
+  PairAcc<real> core, shell;
   core.fx = core.fy = core.fz = core.ulj = core.wlj = core.uc = core.wc = (real)0;
   core.cuc = core.cwc = (real)0;
   core.nbr = 0;
   shell = core;
-  shall = core;
   real fx = 0, fy = 0, fz = 0;
   double en[NQ_PAIR] = {0.0, 0.0, 0.0, 0.0};
   if (i0 < n) {
@@ -158,24 +176,33 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
       const int leader = __ffs(remaining) - 1;
       const int gx = __shfl_sync(FULL, cx, leader), gy = __shfl_sync(FULL, cy, leader),
                 gz = __shfl_sync(FULL, cz, leader);
-      const bool in = valid && cx == gx && cy == gy && cz == gz;
+      const bool in = valid && cy == gy && cz == gz && (unsigned)(cx - gx) < (unsigned)a.gs;
       remaining &= ~__ballot_sync(FULL, in);
+      const int lo = cx - gx;  // the lane's x cells are offsets lo .. lo + 2 of the run
       const uint32_t ox = __shfl_sync(FULL, sxi, leader), oy = __shfl_sync(FULL, syi, leader),
                      oz = __shfl_sync(FULL, szi, leader);
       const int dxi = (int)(sxi - ox), dyi = (int)(syi - oy), dzi = (int)(szi - oz);
       const float xi = __fmul_rn((float)dxi, a.pa.pc.h[0]);
       const float yi = __fmul_rn((float)dyi, a.pa.pc.h[1]);
       const float zi = __fmul_rn((float)dzi, a.pa.pc.h[2]);
-      // the 27 neighbour cells in canonical (dz, dy, dx) order, one lane each
+      // the 9 rows (dz, dy) in canonical order, each the x cells gx - 1 .. gx + gs (mod n_x)
+      // as at most two contiguous runs; one lane per run
       {
         int b0 = 0, l0 = 0;
-        if (lane < 27) {
-          const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
-          const int rx = ((gx + dx) % n0 + n0) % n0, ry = ((gy + dy) % n1 + n1) % n1,
-                    rz = ((gz + dz) % n2 + n2) % n2;
-          const int64_t cell = rx + (int64_t)n0 * (ry + (int64_t)n1 * rz);
-          b0 = S.cell_start[cell];
-          l0 = S.cell_start[cell + 1] - b0;
+        if (lane < 18) {
+          const int r = lane >> 1, part = lane & 1;
+          const int dz = r / 3 - 1, dy = r % 3 - 1;
+          const int ry = ((gy + dy) % n1 + n1) % n1, rz = ((gz + dz) % n2 + n2) % n2;
+          const int64_t rowbase = (int64_t)n0 * (ry + (int64_t)n1 * rz);
+          const int xlo = gx - 1, xhi = gx + a.gs;
+          int c0, c1;  // inclusive cell range of this run (empty when c1 < c0)
+          if (xlo < 0) { c0 = part ? 0 : n0 - 1; c1 = part ? xhi : n0 - 1; }
+          else if (xhi >= n0) { c0 = part ? 0 : xlo; c1 = part ? xhi - n0 : n0 - 1; }
+          else { c0 = xlo; c1 = part ? xlo - 1 : xhi; }
+          if (c1 >= c0) {
+            b0 = S.cell_start[rowbase + c0];
+            l0 = S.cell_start[rowbase + c1 + 1] - b0;
+          }
         }
         int incl = l0;
 #pragma unroll
@@ -183,14 +210,14 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           const int v = __shfl_up_sync(FULL, incl, o);
           if (lane >= o) incl += v;
         }
-        if (lane < 27) {
+        if (lane < 18) {
           seg_beg[wid][lane] = b0;
           seg_pre[wid][lane] = incl - l0;
         }
-        if (lane == 26) seg_pre[wid][27] = incl;
+        if (lane == 17) seg_pre[wid][18] = incl;
       }
       __syncwarp();
-      const int T = seg_pre[wid][27];
+      const int T = seg_pre[wid][18];
       const int nchunks = (T + 31) / 32;
       if (nchunks > kRblMaxChunks) {  // capacity of the per-lane chunk counts
         if (lane == 0) atomicOr(a.err, ERRBIT_CAPACITY);
@@ -203,11 +230,13 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
 #pragma unroll
         for (int w = 0; w < kRblWin; ++w) {
           const int c = base + 32 * w + lane;
-          int s = sg;
+          int s = sg, tc = -1;
           if (c < T) {
             while (seg_pre[wid][s + 1] <= c) ++s;
             const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
-            const int dxj = (int)(S.sx[j] - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
+            const uint32_t sxj = S.sx[j];
+            const int dxj = (int)(sxj - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
+            if (a.gs > 1) tc = run_offset(cell_of(sxj, n0), gx, n0);  // x offset in the run
             // products rounded explicitly: pass 2 recomputes them and must classify identically
             stage[wid][w][lane] = make_float4(__fmul_rn((float)dxj, a.pa.pc.h[0]),
                                               __fmul_rn((float)dyj, a.pa.pc.h[1]),
@@ -216,6 +245,11 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
             if (COUL) stage_q[wid][w][lane] = S.qf[j];
             stage_j[wid][w][lane] = (int32_t)j;
           }
+          if (a.gs > 1)  // (one-cell groups keep every candidate)
+            for (int t = 0; t < a.gs + 2; ++t) {
+              const uint32_t mt = __ballot_sync(FULL, tc == t);
+              if (lane == 0) tmask[wid][w][t] = mt;
+            }
           sg = __shfl_sync(FULL, s, 31);
         }
         __syncwarp();
@@ -242,6 +276,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
             }
             uint32_t vmask = nj >= 32 ? 0xFFFFFFFFu : ((1u << nj) - 1u);
             if (!in) vmask = 0u;
+            else if (a.gs > 1) vmask &= tmask[wid][w][lo] | tmask[wid][w][lo + 1] | tmask[wid][w][lo + 2];
             mcore &= vmask; mshell &= vmask; mamb &= vmask;
             while (mamb) {  // rare: exact decision inside the bands
               const int tt = __ffs(mamb) - 1;
@@ -276,7 +311,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
                 (int)((uint32_t)dzi - (uint32_t)d.z), qi, ti, qj, d.w);
             rbl_acc_add(a, use && is_core, t, core);
             if (EAGER) {
-              rbl_acc_add(a, use && !is_core, t, shall);
+              rbl_acc_add(a, use && !is_core, t, shell);
               if (a.partners && use && !is_core) {  // shell rank ksh in canonical order
                 if (ksh < a.p) a.partners[i * a.p + ksh] = a.id[j];
                 ++ksh;
@@ -289,10 +324,11 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
       // ---- pass 2: the drawn shell partners (all of them when #S_i <= p; the eager
       //      variant has that sum, and the partners, already and runs pass 2 only to draw)
       const bool pass2 = in && (!EAGER || nsh > a.p);
-      if (EAGER && in && !pass2) {
-        shell = shall;
-        if (a.partners)
-          for (int t = nsh; t < a.p; ++t) a.partners[i * a.p + t] = -1;
+      if (EAGER && in && !pass2 && a.partners)
+        for (int t = nsh; t < a.p; ++t) a.partners[i * a.p + t] = -1;
+      if (EAGER && pass2) {  // the eager sum is not the estimator here: draw instead
+        shell.fx = shell.fy = shell.fz = shell.ulj = shell.wlj = shell.uc = shell.wc = (real)0;
+        shell.cuc = shell.cwc = (real)0;
       }
       if (pass2) {
         uint32_t idx[kRblMaxP];
@@ -336,7 +372,9 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
             if (c >= T) break;
             while (seg_pre[wid][s + 1] <= c) ++s;
             const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
-            const int dxj = (int)(S.sx[j] - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
+            const uint32_t sxj = S.sx[j];
+            if (a.gs > 1 && (unsigned)(run_offset(cell_of(sxj, n0), gx, n0) - lo) > 2u) continue;  // not i's cell
+            const int dxj = (int)(sxj - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
             float ddx = xi - __fmul_rn((float)dxj, a.pa.pc.h[0]),
                   ddy = yi - __fmul_rn((float)dyj, a.pa.pc.h[1]),
                   ddz = zi - __fmul_rn((float)dzj, a.pa.pc.h[2]);
@@ -481,13 +519,24 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   a.partners = want_debug ? c.partners : nullptr;
   const int64_t blocks = rbl_blocks(c.N);
   const bool multi = c.nt > 1, coul = c.Nq > 0;
-  // groups share one cell: the leader frame is a valid minimum image while a + r_s < L/2
+  // group extent gs in x cells: enough cells to fill a warp (1 unless the system is dilute),
+  // unless set by RBE_TUNE_RBL_SPAN; gs + 2 <= n_x keeps the union's cells distinct
+  int gs = c.rbl_span;
+  if (gs <= 0) {
+    const double per_cell = (double)c.N / (double)c.grid.ncell;
+    gs = per_cell > 0.0 ? (int)std::floor(32.0 / per_cell) : 1;
+  }
+  gs = std::max(1, std::min(std::min(gs, kRblMaxSpan), c.grid.n[0] - 2));
+  // the leader frame is a valid minimum image while (group extent) + r_s < L/2
   bool wrap = false;
   for (int d = 0; d < 3; ++d) {
     pa.L[d] = (float)c.box[d];
     pa.invL[d] = (float)(1.0 / c.box[d]);
     if (!(c.box[d] / c.grid.n[d] + c.rc < 0.5 * c.box[d] * (1.0 - 1e-9))) wrap = true;
   }
+  if (!wrap)
+    while (gs > 1 && !(gs * c.box[0] / c.grid.n[0] + c.rc < 0.5 * c.box[0] * (1.0 - 1e-9))) --gs;
+  a.gs = gs;
   pa.smax = 1;
   pa.comp = c.precision == RBE_FP32_COMP;
   if (c.precision == RBE_FP64) rbl_launch<double>(a, blocks, coul, c.rbl_eager, multi, wrap, c.stream);

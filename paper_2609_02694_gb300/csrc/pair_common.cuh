@@ -97,7 +97,7 @@ __device__ __forceinline__ void pair_force_v(const PairArgs &a, const LJTable *t
     }
     real rinv2;
     if (sizeof(real) == 8) rinv2 = (real)(1.0 / (double)r2);
-    else rinv2 = (real)__frcp_rn((float)r2);
+    else rinv2 = (real)__fdividef(1.0f, (float)r2);  // fast reciprocal (2 ulp)
     const real sr2 = s2 * rinv2;
     const real sr6 = sr2 * sr2 * sr2;
     const real gl = e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);
@@ -198,7 +198,7 @@ __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTabl
     }
     real rinv2;
     if (sizeof(real) == 8) rinv2 = (real)(1.0 / (double)r2s);
-    else rinv2 = (real)__frcp_rn((float)r2s);
+    else rinv2 = (real)__fdividef(1.0f, (float)r2s);  // fast reciprocal (2 ulp)
     const real sr2 = s2 * rinv2;
     const real sr6 = sr2 * sr2 * sr2;
     const real gl = on * e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);

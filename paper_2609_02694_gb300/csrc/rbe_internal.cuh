@@ -74,6 +74,7 @@ struct Ctx {
   int P = 0, p_rbl = 0, precision = RBE_FP32_COMP, nt = 1, sub = 2;
   bool pair_test16 = true;  // packed half-precision candidate pre-test in the pair kernel
   bool rbl_eager = false;   // RBL: evaluate every shell pair in the classifying pass
+  int rbl_span = 0;         // RBL: group extent in x cells (0: automatic)
   uint64_t seed = 0;
   uint32_t replica = 0;
   bool rbl = false;

@@ -259,6 +259,31 @@ def test_rbl_eager_shell_bit_identical(orc):
     assert np.array_equal(pa1, ref["partners"])
 
 
+@pytest.mark.parametrize("density,eager", [(0.1, 0), (0.1, 1), (0.02, 1)])
+def test_rbl_span_bit_identical(orc, density, eager):
+    """Warp groups spanning several cells in x (the dilute-system layout) enumerate every
+    particle's shell in the same canonical order: forces, energies, counts and draws are
+    bit-identical for every span and match the oracle's sets and draws."""
+    sy = synth.make_system(20000, density=density, frac_charged=0.1, seed=9)
+    p, r_core, r_c, seed, step = 12, 4.5, 6.0, 4, 5
+    out = {}
+    for span in (1, 3, 6):
+        with handle(sy, 32, r_core=r_core, p_rbl=p, r_c=r_c, seed=seed) as h:
+            h.set_tuning("rbl_eager", eager)
+            h.set_tuning("rbl_span", span)
+            F, E, W = h.forces_f64(step)
+            out[span] = (F, E, W, *h.neighbor_counts(), h.rbl_partners())
+    F1, E1, W1, nc1, ns1, pa1 = out[1]
+    for span in (3, 6):
+        F, E, W, nc, ns, pa = out[span]
+        assert np.array_equal(F, F1) and E == E1 and W == W1
+        assert np.array_equal(nc, nc1) and np.array_equal(ns, ns1) and np.array_equal(pa, pa1)
+    ref = orc.rbl(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, r_c, p, seed, step, 0, C,
+                  sy.eps, sy.sig)
+    assert np.array_equal(nc1, ref["n_core"]) and np.array_equal(ns1, ref["n_shell"])
+    assert np.array_equal(pa1, ref["partners"])
+
+
 # -------------------------------------------------------------------------- Verlet
 
 
