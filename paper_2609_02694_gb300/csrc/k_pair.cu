@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
         const int4 *sd = &stage_d[wid][0][0];
         const float *sq = &stage_q[wid][0][0];
         const int32_t *sj = &stage_j[wid][0][0];
-        while (__any_sync(FULL, (mA | mB) != 0ull)) {
+        // uniform trip count: the largest number of hits of any lane in this window
+        const int nhit = __reduce_max_sync(FULL, __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]));
+        for (int k = 0; k < nhit; ++k) {
           const bool useA = mA != 0ull;
           const uint64_t bits = useA ? mA : mB;
           const bool act = bits != 0ull;
@@ -227,22 +229,26 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
           mA = useA ? rest : mA;
           mB = useA ? mB : rest;
           const int slot = (useA ? 0 : 64) + b;  // window slot = chunk * 32 + candidate
-          const int32_t j = sj[slot];
           const int4 d = sd[slot];
+          const int dsx = (int)((uint32_t)dxi - (uint32_t)d.x);
+          const int dsy = (int)((uint32_t)dyi - (uint32_t)d.y);
+          const int dsz = (int)((uint32_t)dzi - (uint32_t)d.z);
           if (BUILD) {
-            const float ex = (float)(int)((uint32_t)dxi - (uint32_t)d.x) * a.pc.h[0];
-            const float ey = (float)(int)((uint32_t)dyi - (uint32_t)d.y) * a.pc.h[1];
-            const float ez = (float)(int)((uint32_t)dzi - (uint32_t)d.z) * a.pc.h[2];
+            const int32_t j = sj[slot];
+            const float ex = (float)dsx * a.pc.h[0];
+            const float ey = (float)dsy * a.pc.h[1];
+            const float ez = (float)dsz * a.pc.h[2];
             const bool hit = act && j != (int32_t)i && ex * ex + ey * ey + ez * ez <= a.pc.rc2_hi;
             if (hit && cnt < a.K) lst[(int64_t)cnt * 32] = j;
             cnt += hit ? 1 : 0;
           } else {
             real qj = (real)0;
-            if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[j] : (real)sq[slot];
-            pair_eval_masked<real, LJ, COUL, MULTI>(
-                a, tab, act && j != (int32_t)i, (int)((uint32_t)dxi - (uint32_t)d.x),
-                (int)((uint32_t)dyi - (uint32_t)d.y), (int)((uint32_t)dzi - (uint32_t)d.z), qi,
-                ti, qj, d.w, acc);
+            if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[sj[slot]] : (real)sq[slot];
+            // the particle itself is the one candidate at zero displacement (coincident
+            // particles, which no valid configuration has, would be skipped the same way)
+            const bool self = (dsx | dsy | dsz) == 0;
+            pair_eval_masked<real, LJ, COUL, MULTI>(a, tab, act && !self, dsx, dsy, dsz, qi, ti,
+                                                    qj, d.w, acc);
           }
         }
         __syncwarp();
