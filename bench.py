@@ -33,6 +33,21 @@ METRIC = "RBE force particle-steps/s on 1 GB300, FP32-comp vs FP64 form at state
 UNIT = "particle-steps/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 PAIR_FLOPS = 20.0  # FP32 flops per unique pair (LJ), the per-unit figure of the roofline
+# Algorithmic HBM bytes per particle of the streaming phases (FP32 form): binning = count
+# (read s, q; write key, slot: 24 B) + scatter (8 B read, 4 B write) + permute (read slot and
+# s, v, id, q, 1/m; write them: 76 B) + charged subset (~2 B at 10%); integration =
+# kick-drift (read s, v, F, 1/m; write s, v: 64 B) + kick (read v, F, 1/m; write v: 40 B).
+BIN_BYTES = 114.0
+INTEGRATE_BYTES = 104.0
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 def parse():
@@ -129,6 +144,20 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks after a barrier (the job's time is its slowest rank's);
+    x itself on one rank. `device` is where the process group reduces (cuda for NCCL, cpu
+    for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dist.barrier()
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def time_steps(h, stream, flush_buf, K, profile_phase=None):
@@ -282,15 +311,18 @@ def run_ours(args):
             h.step(1)
         total_ms, phases = time_steps(h, stream, flush, args.steps, profile_phase=True)
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     kps = h.kernels_per_step()
     peaks = measured_peaks()
+    hbm = hbm_peak_gbs()
     nq_pairs = float((sy.q != 0).sum()) * args.P
     E1, _ = h.energies()
+    # force evaluation alone (no integration), forces left on the device
+    F_dev = torch.empty((sy.n, 3), dtype=torch.float32, device=dev)
+    h.set_profiling(False)
+    for k in range(2):
+        h.forces(1000 + k, out=F_dev, energies=False)
+    f_ms = _timed(lambda: h.forces(1002, out=F_dev, energies=False), args.steps, stream) / args.steps
     value = sy.n * args.steps * ws / (total_ms / 1e3)
     pair_ms = phases["pair"] / args.steps
     achieved = pairs * PAIR_FLOPS / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
@@ -306,6 +338,8 @@ def run_ours(args):
                                        else "cell traversal every step"),
                        "traversal_trial_ms_per_step": trial},
             "gpu_launches": kps * args.steps,
+            "force_only": {"value": sy.n / (f_ms / 1e3), "unit": UNIT, "ms_per_eval": f_ms,
+                           "call": "rbe_forces (forces kept on the device, no energies read)"},
             "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
             "roofline": {"bound": "alu",
                          "kernel": ("list_pair_kernel (Verlet-list LJ)" if skin > 0
@@ -325,6 +359,15 @@ def run_ours(args):
                            "peak": peaks["sincos_pairs"],
                            "frac": nq_pairs / (phases["gather"] / args.steps / 1e3) / peaks["sincos_pairs"]},
                 "pair_vs_measured_fp32": achieved * 1e12 / peaks["fp32_flops"] if achieved else None,
+                "bin": {"bound": "hbm", "unit": "GB/s", "bytes_per_particle": BIN_BYTES,
+                        "achieved": sy.n * BIN_BYTES / (phases["bin"] / args.steps / 1e3) / 1e9,
+                        "peak": hbm[0], "peak_source": hbm[1],
+                        "frac": sy.n * BIN_BYTES / (phases["bin"] / args.steps / 1e3) / 1e9 / hbm[0]},
+                "integrate": {"bound": "hbm", "unit": "GB/s", "bytes_per_particle": INTEGRATE_BYTES,
+                              "achieved": sy.n * INTEGRATE_BYTES / ((phases["kick_drift"] + phases["tail"]) / args.steps / 1e3) / 1e9,
+                              "peak": hbm[0], "peak_source": hbm[1],
+                              "frac": sy.n * INTEGRATE_BYTES / ((phases["kick_drift"] + phases["tail"]) / args.steps / 1e3) / 1e9 / hbm[0],
+                              "note": "kick-drift + (kick, kinetic energy and totals)"},
                 "peak_source": "own probes (rbe_measure_peak) at the run's clock"},
             "clocks": clk.summary(),
             "neighbor_list": h.neighbor_list_stats() if skin > 0 else None,
@@ -502,6 +545,8 @@ def run_rbl134m(args):
     h.set_profiling(True)
     F, E, W = h.forces(0)
     net = np.abs(F.astype(np.float64).sum(0)).max() / np.abs(F).sum()
+    n_core, n_shell = h.neighbor_counts()
+    core_mean, shell_mean = float(n_core.mean()), float(n_shell.mean())
     for _ in range(max(1, args.warmup)):
         h.step(1)
     torch.cuda.synchronize()
@@ -516,7 +561,13 @@ def run_rbl134m(args):
                       "ms_per_step": tot / K, "steps": K,
                       "device_bytes_per_particle": h.memory_bytes() / N,
                       "phases_ms_per_step": {k: v / K for k, v in ph_tot.items()},
-                      "net_force_over_sum_abs": float(net), "init_s": init_s}), flush=True)
+                      "net_force_over_sum_abs": float(net), "init_s": init_s,
+                      "per_particle": {"core_pairs": core_mean, "shell_members": shell_mean,
+                                       "drawn_pairs": 10},
+                      "rbl_kernel": {"ms": ph_tot["pair"] / K,
+                                     "pair_evaluations_per_s": N * (core_mean + 10) / (ph_tot["pair"] / K / 1e3),
+                                     "note": "core pairs + p draws per particle; every stencil "
+                                             "candidate is classified once"}}), flush=True)
     h.close()
 
 

@@ -20,9 +20,15 @@
 // staged in shared memory in FP32 coordinates relative to the group leader. Membership is decided exactly: FP32 outside
 // a +-1e-5 band around r_core^2 and r_s^2, the FP64 oracle expression inside it.
 // Pass 1 classifies every candidate once in canonical order, evaluates the core pairs from
-// the staged exact integer displacements (branch-light), and keeps per lane the number of
-// shell members of each 32-candidate chunk. Pass 2 draws, sorts the draws, and re-walks
-// only the chunks that hold them (same classification) to evaluate the drawn pairs.
+// the staged exact integer displacements (branch-light), and keeps per lane the shell
+// members of each 32-candidate chunk: their count in shared memory and their bit mask in a
+// per-warp scratch row in global memory. Pass 2 draws, sorts the draws, finds each draw's
+// chunk from the counts and its candidate from the mask (n-th set bit), and evaluates the
+// drawn pairs: no candidate is classified twice.
+// The scratch is sized by the blocks that can be resident at once, not by N: each block
+// takes a free slot of a pool with one slot per block the GPU can hold (numbered by
+// compare-and-swap probes that always succeed, since at most that many blocks are resident)
+// and frees it when it ends.
 // Eager variant, for shells that are mostly no larger than p (dilute systems): pass 1 also
 // evaluates every shell pair, in canonical order, into a second accumulator. A particle
 // with #S_i <= p then keeps it (the same sum pass 2 would form, bit for bit) and skips
@@ -54,6 +60,9 @@ struct RblArgs {
   int32_t *ncore, *nshell, *partners;  // sorted order, nullable
   int *err;
   int gs;  // group extent in x cells (1 .. kRblMaxSpan, gs + 2 <= n_x)
+  uint32_t *masks;  // per slot and warp: kRblMaxChunks x 32 shell masks
+  int *slots;       // slot pool (0 free, 1 taken)
+  int nslots;
 };
 
 // x offset of cell cxj in the group's run of cells gx - 1 .. gx + gs (mod n_x)
@@ -146,12 +155,26 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   __shared__ double wred[kRblWarps][NQ_PAIR + 3];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
+  __shared__ int slot_s;
   const PairSet &S = a.pa.set;
   const int64_t n = S.n;
+  const LJTable *tab = a.pa.table;
+  if (threadIdx.x == 0) {  // a free scratch slot (at most nslots blocks are resident)
+    int got = -1;
+    for (int k = 0; k < a.nslots && got < 0; ++k) {
+      const int sl = (int)((blockIdx.x + (unsigned)k) % (unsigned)a.nslots);
+      if (atomicCAS(&a.slots[sl], 0, 1) == 0) got = sl;
+    }
+    if (got < 0) atomicOr(a.err, ERRBIT_CAPACITY);
+    slot_s = got;
+  }
+  __syncthreads();
+  const int slot = slot_s;
+  uint32_t *const scr =
+      a.masks + ((int64_t)(slot < 0 ? 0 : slot) * kRblWarps + wid) * (int64_t)kRblMaxChunks * 32;
   const int64_t i0 = ((int64_t)blockIdx.x * kRblWarps + wid) * 32;
   const int64_t i = i0 + lane;
-  const bool valid = i < n;
-  const LJTable *tab = a.pa.table;
+  const bool valid = i < n && slot >= 0;
   // shell: the drawn shell pairs; in the eager variant first every shell pair, reset when
   // the particle turns out to need draws
   PairAcc<real> core, shell;
@@ -258,6 +281,11 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           const int nj = max(0, min(32, T - base - 32 * w));
           uint32_t mcore = 0u, mshell = 0u, mamb = 0u;
           if (nj > 0) {
+            // Four threshold tests per candidate, each the sign bit of a difference shifted
+            // into a mask (one funnel shift; the sign of a rounded difference is exact):
+            // lo1 = r2 < rcore2_lo, up1 = r2 > rcore2_hi, lo2 = r2 < rs2_lo, up2 = r2 > rs2_hi.
+            // Candidate tt lands in bit 31 - tt; the masks are bit-reversed afterwards.
+            uint32_t lo1 = 0u, up1 = 0u, lo2 = 0u, up2 = 0u;
 #pragma unroll
             for (int tt = 0; tt < 32; ++tt) {
               const float4 pj = stage[wid][w][tt];
@@ -268,12 +296,15 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
                 ddz = fold(ddz, a.pa.L[2], a.pa.invL[2]);
               }
               const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-              const uint32_t bit = 1u << tt;
-              mcore |= r2 < a.rcore2_lo ? bit : 0u;
-              mshell |= (r2 > a.rcore2_hi && r2 < a.rs2_lo) ? bit : 0u;
-              mamb |= ((r2 >= a.rcore2_lo && r2 <= a.rcore2_hi) ||
-                       (r2 >= a.rs2_lo && r2 <= a.rs2_hi)) ? bit : 0u;
+              lo1 = __funnelshift_l(__float_as_uint(r2 - a.rcore2_lo), lo1, 1);
+              up1 = __funnelshift_l(__float_as_uint(a.rcore2_hi - r2), up1, 1);
+              lo2 = __funnelshift_l(__float_as_uint(r2 - a.rs2_lo), lo2, 1);
+              up2 = __funnelshift_l(__float_as_uint(a.rs2_hi - r2), up2, 1);
             }
+            lo1 = __brev(lo1); up1 = __brev(up1); lo2 = __brev(lo2); up2 = __brev(up2);
+            mcore = lo1;                                   // r2 < rcore2_lo
+            mshell = up1 & lo2;                            // rcore2_hi < r2 < rs2_lo
+            mamb = (~lo1 & ~up1) | (~lo2 & ~up2);          // inside one of the two bands
             uint32_t vmask = nj >= 32 ? 0xFFFFFFFFu : ((1u << nj) - 1u);
             if (!in) vmask = 0u;
             else if (a.gs > 1) vmask &= tmask[wid][w][lo] | tmask[wid][w][lo + 1] | tmask[wid][w][lo + 2];
@@ -290,7 +321,10 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
             }
           }
           const int chunk = (base >> 5) + w;
-          if (chunk < nchunks) ccount[wid][chunk][lane] = (uint8_t)__popc(mshell);
+          if (chunk < nchunks) {
+            ccount[wid][chunk][lane] = (uint8_t)__popc(mshell);
+            scr[chunk * 32 + lane] = mshell;  // coalesced, read back by pass 2
+          }
           nsh += __popc(mshell);
           // core pairs (and, eager, shell pairs), branch-light, in canonical order; the
           // particle itself (r = 0, always core) is skipped
@@ -356,50 +390,32 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           ndraw = nsh;
           for (int t = 0; t < ndraw; ++t) { idx[t] = (uint32_t)t; ord[t] = t; }
         }
-        int ptr = 0, chunk = 0, before = 0;
-        while (ptr < ndraw) {
-          const uint32_t target = idx[ord[ptr]];
-          while (before + (int)ccount[wid][chunk][lane] <= (int)target) {
+        // draws in canonical order: chunk from the counts, candidate from the chunk's mask
+        int chunk = 0, before = 0, sgd = 0;
+        for (int ptr = 0; ptr < ndraw; ++ptr) {
+          const int target = (int)idx[ord[ptr]];
+          while (before + (int)ccount[wid][chunk][lane] <= target) {
             before += ccount[wid][chunk][lane];
             ++chunk;
           }
-          // walk this chunk's candidates with the classification of pass 1
-          int k = before;
-          int s = 0;
-          while (seg_pre[wid][s + 1] <= chunk * 32) ++s;  // run of the chunk's first candidate
-          for (int tt = 0; tt < 32 && ptr < ndraw; ++tt) {
-            const int c = chunk * 32 + tt;
-            if (c >= T) break;
-            while (seg_pre[wid][s + 1] <= c) ++s;
-            const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
-            const uint32_t sxj = S.sx[j];
-            if (a.gs > 1 && (unsigned)(run_offset(cell_of(sxj, n0), gx, n0) - lo) > 2u) continue;  // not i's cell
-            const int dxj = (int)(sxj - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
-            float ddx = xi - __fmul_rn((float)dxj, a.pa.pc.h[0]),
-                  ddy = yi - __fmul_rn((float)dyj, a.pa.pc.h[1]),
-                  ddz = zi - __fmul_rn((float)dzj, a.pa.pc.h[2]);
-            if (WRAP) {
-              ddx = fold(ddx, a.pa.L[0], a.pa.invL[0]);
-              ddy = fold(ddy, a.pa.L[1], a.pa.invL[1]);
-              ddz = fold(ddz, a.pa.L[2], a.pa.invL[2]);
-            }
-            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-            const int dsx = (int)((uint32_t)dxi - (uint32_t)dxj), dsy = (int)((uint32_t)dyi - (uint32_t)dyj),
-                      dsz = (int)((uint32_t)dzi - (uint32_t)dzj);
-            if (rbl_class(a, r2, dsx, dsy, dsz) != 2) continue;
-            while (ptr < ndraw && idx[ord[ptr]] == (uint32_t)k) {
-              real qj = (real)0;
-              if (COUL) qj = sizeof(real) == 8 ? (real)S.qd[j] : (real)S.qf[j];
-              const PairAcc<real> t = rbl_pair_eval<real, COUL, MULTI>(
-                  a, tab, true, dsx, dsy, dsz, qi, ti, qj, MULTI ? S.type[j] : 0);
-              rbl_acc_add(a, true, t, shell);
-              if (a.partners) a.partners[i * a.p + ord[ptr]] = a.id[j];
-              ++ptr;
-            }
-            ++k;
+          const uint32_t mk = scr[chunk * 32 + lane];
+          const uint32_t pos = __fns(mk, 0u, target - before + 1);
+          if (pos > 31u) {  // counts and masks disagree: cannot happen; never index with it
+            atomicOr(a.err, ERRBIT_CAPACITY);
+            continue;
           }
-          before = k;
-          ++chunk;
+          const int c = chunk * 32 + (int)pos;
+          while (seg_pre[wid][sgd + 1] <= c) ++sgd;  // draws ascend, so runs do too
+          const int64_t j = seg_beg[wid][sgd] + (c - seg_pre[wid][sgd]);
+          const int dsx = (int)((uint32_t)dxi - (S.sx[j] - ox));
+          const int dsy = (int)((uint32_t)dyi - (S.sy[j] - oy));
+          const int dsz = (int)((uint32_t)dzi - (S.sz[j] - oz));
+          real qj = (real)0;
+          if (COUL) qj = sizeof(real) == 8 ? (real)S.qd[j] : (real)S.qf[j];
+          const PairAcc<real> t = rbl_pair_eval<real, COUL, MULTI>(
+              a, tab, true, dsx, dsy, dsz, qi, ti, qj, MULTI ? S.type[j] : 0);
+          rbl_acc_add(a, true, t, shell);
+          if (a.partners) a.partners[i * a.p + ord[ptr]] = a.id[j];
         }
       }
     }
@@ -434,6 +450,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
     if (threadIdx.x < NQ_PAIR) a.pa.epart[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = 0.5 * s;
     else a.fsum_part[(int64_t)blockIdx.x * 3 + threadIdx.x - NQ_PAIR] = s;
   }
+  if (threadIdx.x == 0 && slot >= 0) atomicExch(&a.slots[slot], 0);  // after the block's last use
 }
 
 // Mean of F~ over all particles (fixed-order FP64), then F -= mean (Eq. F_corr).
@@ -489,6 +506,39 @@ static void rbl_launch(const RblArgs &a, int64_t blocks, bool coul, bool eager, 
   }
 }
 
+// Group extent gs in x cells (enough cells to fill a warp: 1 unless the system is dilute,
+// unless set by RBE_TUNE_RBL_SPAN; gs + 2 <= n_x keeps the union's cells distinct) and
+// whether the leader frame needs the wrapping variant.
+static void rbl_shape(const Ctx &c, int *gs_out, bool *wrap_out) {
+  int gs = c.rbl_span;
+  if (gs <= 0) {
+    const double per_cell = (double)c.N / (double)c.grid.ncell;
+    gs = per_cell > 0.0 ? (int)std::floor(32.0 / per_cell) : 1;
+  }
+  gs = std::max(1, std::min(std::min(gs, kRblMaxSpan), c.grid.n[0] - 2));
+  // the leader frame is a valid minimum image while (group extent) + r_s < L/2
+  bool wrap = false;
+  for (int d = 0; d < 3; ++d)
+    if (!(c.box[d] / c.grid.n[d] + c.rc < 0.5 * c.box[d] * (1.0 - 1e-9))) wrap = true;
+  if (!wrap)
+    while (gs > 1 && !(gs * c.box[0] / c.grid.n[0] + c.rc < 0.5 * c.box[0] * (1.0 - 1e-9))) --gs;
+  *gs_out = gs;
+  *wrap_out = wrap;
+}
+
+// Slots of the scratch pool: the most 128-thread blocks the GPU can hold at once (thread
+// limit per SM), never more than the grid has blocks.
+int64_t rbl_slot_count(int64_t n) {
+  int dev = 0, sms = 152, thr = 2048;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  const int64_t per_sm = std::max(1, thr / (kRblWarps * 32));
+  return std::max<int64_t>(1, std::min<int64_t>(rbl_blocks(n), (int64_t)sms * per_sm));
+}
+
+int64_t rbl_mask_words(int64_t slots) { return slots * kRblWarps * (int64_t)kRblMaxChunks * 32; }
+
 cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   const int b = c.cur;
   RblArgs a;
@@ -519,24 +569,17 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   a.partners = want_debug ? c.partners : nullptr;
   const int64_t blocks = rbl_blocks(c.N);
   const bool multi = c.nt > 1, coul = c.Nq > 0;
-  // group extent gs in x cells: enough cells to fill a warp (1 unless the system is dilute),
-  // unless set by RBE_TUNE_RBL_SPAN; gs + 2 <= n_x keeps the union's cells distinct
-  int gs = c.rbl_span;
-  if (gs <= 0) {
-    const double per_cell = (double)c.N / (double)c.grid.ncell;
-    gs = per_cell > 0.0 ? (int)std::floor(32.0 / per_cell) : 1;
-  }
-  gs = std::max(1, std::min(std::min(gs, kRblMaxSpan), c.grid.n[0] - 2));
-  // the leader frame is a valid minimum image while (group extent) + r_s < L/2
-  bool wrap = false;
+  int gs;
+  bool wrap;
+  rbl_shape(c, &gs, &wrap);
   for (int d = 0; d < 3; ++d) {
     pa.L[d] = (float)c.box[d];
     pa.invL[d] = (float)(1.0 / c.box[d]);
-    if (!(c.box[d] / c.grid.n[d] + c.rc < 0.5 * c.box[d] * (1.0 - 1e-9))) wrap = true;
   }
-  if (!wrap)
-    while (gs > 1 && !(gs * c.box[0] / c.grid.n[0] + c.rc < 0.5 * c.box[0] * (1.0 - 1e-9))) --gs;
   a.gs = gs;
+  a.masks = c.rbl_masks;
+  a.slots = c.rbl_slots;
+  a.nslots = (int)c.rbl_nslots;
   pa.smax = 1;
   pa.comp = c.precision == RBE_FP32_COMP;
   if (c.precision == RBE_FP64) rbl_launch<double>(a, blocks, coul, c.rbl_eager, multi, wrap, c.stream);

@@ -19,6 +19,8 @@ using namespace rbe;
 namespace rbe {
 int64_t pair_blocks(int64_t n);
 int64_t rbl_blocks(int64_t n);
+int64_t rbl_slot_count(int64_t n);
+int64_t rbl_mask_words(int64_t slots);
 }  // namespace rbe
 
 struct rbe_ctx : public rbe::Ctx {};
@@ -122,7 +124,7 @@ int free_all(Ctx &c) {
   dfree(c.m); dfree(c.kcf); dfree(c.kcd); dfree(c.sf_part); dfree(c.rho); dfree(c.abf);
   dfree(c.abd); dfree(c.emode); dfree(c.epart); dfree(c.scal); dfree(c.step_dev);
   dfree(c.err); dfree(c.nbr); dfree(c.nshell); dfree(c.partners); dfree(c.rbl_mean);
-  dfree(c.rbl_part); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
+  dfree(c.rbl_part); dfree(c.rbl_masks); dfree(c.rbl_slots); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
   dfree(c.thermo);
   dfree(c.vl_list); dfree(c.vl_len); dfree(c.vl_listq); dfree(c.vl_lenq); dfree(c.vl_ref);
   dfree(c.s4); dfree(c.cs4); dfree(c.vl_flags); dfree(c.vl_count);
@@ -406,6 +408,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   c.n_pair_blk = rbl ? 0 : pair_blocks(N);
   c.n_coul_blk = rbl ? 0 : pair_blocks(Nq);
   c.n_rbl_blk = rbl ? rbl_blocks(N) : 0;
+  c.rbl_nslots = rbl ? rbl_slot_count(N) : 0;
   c.n_ke_blk = (N + 255) / 256;
   c.off_pair = 0;
   c.off_coul = c.off_pair + c.n_pair_blk * NQ_PAIR;
@@ -457,6 +460,8 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
     rc |= dalloc(c, &c.nshell, N);
     rc |= dalloc(c, &c.partners, N * c.p_rbl);
     rc |= dalloc(c, &c.rbl_part, c.n_rbl_blk * 3);
+    rc |= dalloc(c, &c.rbl_masks, rbl_mask_words(c.rbl_nslots));
+    rc |= dalloc(c, &c.rbl_slots, c.rbl_nslots);
   }
   rc |= dalloc(c, &c.rbl_mean, 3);
   rc |= dalloc(c, &c.outf, 3 * N);
@@ -516,6 +521,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
     e |= cudaMemset(c.epart, 0, sizeof(double) * c.epart_slots);
     e |= cudaMemset(c.emode, 0, sizeof(double) * 2 * c.P);
     e |= cudaMemset(c.err, 0, sizeof(int));
+    if (c.rbl_slots) e |= cudaMemset(c.rbl_slots, 0, sizeof(int) * c.rbl_nslots);
     e |= cudaMemset(c.step_dev, 0, sizeof(uint64_t));
     e |= cudaMemset(c.scal, 0, sizeof(double) * S_COUNT);
     if (e != 0) {

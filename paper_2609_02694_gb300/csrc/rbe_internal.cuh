@@ -136,6 +136,9 @@ struct Ctx {
   int32_t *partners = nullptr; // sorted order, N x p (ids)
   double *rbl_mean = nullptr;  // 3 doubles: mean short-range force
   double *rbl_part = nullptr;  // RBL blocks x 3
+  uint32_t *rbl_masks = nullptr;  // RBL: per slot, warp, chunk and lane: shell masks
+  int *rbl_slots = nullptr;         // RBL: slot pool flags
+  int64_t rbl_nslots = 0;
   float *outf = nullptr;       // 3N id-order staging
   double *outd = nullptr;      // 3N id-order staging (FP64 outputs, positions)
   float *out_host = nullptr;   // pinned
