@@ -39,6 +39,9 @@ PAIR_FLOPS = 20.0  # FP32 flops per unique pair (LJ), the per-unit figure of the
 # kick-drift (read s, v, F, 1/m; write s, v: 64 B) + kick (read v, F, 1/m; write v: 40 B).
 BIN_BYTES = 114.0
 INTEGRATE_BYTES = 104.0
+# DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
+# capture of the kernel as it stands (profiles/pair_kernel_lj_n1m.md, list_pair_kernel_n1m.md)
+TRAFFIC_BYTES = {"cells": 12.94e6, "list_skin_1.0": 2.4174e9}
 
 
 def hbm_peak_gbs():
@@ -346,7 +349,10 @@ def run_ours(args):
                                     else "pair_kernel (cell-list LJ)"),
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS if achieved else None,
-                         "traffic": None, "pair_ms_per_launch": pair_ms,
+                         "traffic": (TRAFFIC_BYTES["cells"] if skin == 0 else
+                                     TRAFFIC_BYTES["list_skin_1.0"] if skin == 1.0 else None),
+                         "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch",
+                         "pair_ms_per_launch": pair_ms,
                          "units": f"{pairs:.0f} unique pairs x {PAIR_FLOPS:.0f} flops",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"},
             "rooflines_other": {

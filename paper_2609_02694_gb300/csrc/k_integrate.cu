@@ -10,6 +10,8 @@
 
 namespace rbe {
 
+int64_t rbl_compact_count(int64_t nblk);
+
 template <typename V, typename FT>
 __global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
                                   const float *__restrict__ invm, uint32_t *__restrict__ s,
@@ -271,7 +273,9 @@ cudaError_t launch_totals(Ctx &c) {
   TotalsArgs a;
   a.pair = c.epart + c.off_pair; a.n_pair = c.n_pair_blk;
   a.coul = c.epart + c.off_coul; a.n_coul = c.n_coul_blk;
-  a.rbl = c.epart + c.off_rbl; a.n_rbl = c.n_rbl_blk;
+  // RBL partials: the compacted ones (rbl_compact_kernel runs after the RBL kernel)
+  a.rbl = c.rbl ? c.rbl_cpart : c.epart + c.off_rbl;
+  a.n_rbl = c.rbl ? rbl_compact_count(c.n_rbl_blk) : 0;
   a.ke = c.epart + c.off_ke; a.n_ke = c.n_ke_blk;
   a.emode = c.emode; a.P = c.P;
   a.U_self = c.U_self;

@@ -42,7 +42,7 @@
 
 namespace rbe {
 
-constexpr int kRblWarps = 4;
+constexpr int kRblWarps = 1;  // one warp a block: no warp waits for a slower one
 constexpr int kRblMaxP = 32;
 constexpr int kRblWin = 4;          // chunks of 32 candidates per window
 constexpr int kRblMaxChunks = 192;  // candidates per group <= 6144
@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
       //      keep the number of shell members of each 32-candidate chunk
       int sg = 0;
       for (int base = 0; base < T; base += 32 * kRblWin) {
-#pragma unroll
+        // (window loops stay rolled: the unrolled kernel outgrew the instruction cache)
+#pragma unroll 1
         for (int w = 0; w < kRblWin; ++w) {
           const int c = base + 32 * w + lane;
           int s = sg, tc = -1;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           sg = __shfl_sync(FULL, s, 31);
         }
         __syncwarp();
-#pragma unroll
+#pragma unroll 1
         for (int w = 0; w < kRblWin; ++w) {
           const int nj = max(0, min(32, T - base - 32 * w));
           uint32_t mcore = 0u, mshell = 0u, mamb = 0u;
@@ -453,6 +454,40 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   if (threadIdx.x == 0 && slot >= 0) atomicExch(&a.slots[slot], 0);  // after the block's last use
 }
 
+// The RBL kernel leaves one partial per block (energies, virials: NQ_PAIR doubles; sum of
+// F~: 3 doubles). This pass sums fixed contiguous ranges of them into `ncomp` partials, in a
+// fixed order, so the totals and the mean below read few slots whatever N is.
+__global__ void __launch_bounds__(256) rbl_compact_kernel(const double *__restrict__ epart,
+                                                          const double *__restrict__ fpart,
+                                                          int64_t nblk, int64_t per,
+                                                          double *__restrict__ eout,
+                                                          double *__restrict__ fout) {
+  constexpr int NV = NQ_PAIR + 3;
+  __shared__ double sh[NV][256];
+  const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(nblk, b0 + per);
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NQ_PAIR; ++k) acc[k] += epart[b * NQ_PAIR + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[NQ_PAIR + k] += fpart[b * 3 + k];
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < NQ_PAIR) eout[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = sh[threadIdx.x][0];
+  else if (threadIdx.x < NV) fout[(int64_t)blockIdx.x * 3 + threadIdx.x - NQ_PAIR] = sh[threadIdx.x][0];
+}
+
+int64_t rbl_compact_count(int64_t nblk) { return std::max<int64_t>(1, std::min<int64_t>(nblk, 1024)); }
+
 // Mean of F~ over all particles (fixed-order FP64), then F -= mean (Eq. F_corr).
 __global__ void __launch_bounds__(256) rbl_mean_kernel(const double *__restrict__ part, int64_t nblk,
                                                        int64_t N, double *__restrict__ mean) {
@@ -585,7 +620,11 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   if (c.precision == RBE_FP64) rbl_launch<double>(a, blocks, coul, c.rbl_eager, multi, wrap, c.stream);
   else rbl_launch<float>(a, blocks, coul, c.rbl_eager, multi, wrap, c.stream);
   mark(c, RBE_PH_PAIR2);
-  rbl_mean_kernel<<<1, 256, 0, c.stream>>>(c.rbl_part, blocks, c.N, c.rbl_mean);
+  const int64_t ncomp = rbl_compact_count(blocks);
+  rbl_compact_kernel<<<(unsigned)ncomp, 256, 0, c.stream>>>(c.epart + c.off_rbl, c.rbl_part, blocks,
+                                                             (blocks + ncomp - 1) / ncomp,
+                                                             c.rbl_cpart, c.rbl_cpart + ncomp * NQ_PAIR);
+  rbl_mean_kernel<<<1, 256, 0, c.stream>>>(c.rbl_cpart + ncomp * NQ_PAIR, ncomp, c.N, c.rbl_mean);
   const unsigned nb = (unsigned)((c.N + 255) / 256);
   if (c.precision == RBE_FP64) rbl_subtract_kernel<double><<<nb, 256, 0, c.stream>>>(c.Fd, c.N, c.rbl_mean);
   else rbl_subtract_kernel<float><<<nb, 256, 0, c.stream>>>(c.F, c.N, c.rbl_mean);

@@ -20,6 +20,7 @@ namespace rbe {
 int64_t pair_blocks(int64_t n);
 int64_t rbl_blocks(int64_t n);
 int64_t rbl_slot_count(int64_t n);
+int64_t rbl_compact_count(int64_t nblk);
 int64_t rbl_mask_words(int64_t slots);
 }  // namespace rbe
 
@@ -124,7 +125,7 @@ int free_all(Ctx &c) {
   dfree(c.m); dfree(c.kcf); dfree(c.kcd); dfree(c.sf_part); dfree(c.rho); dfree(c.abf);
   dfree(c.abd); dfree(c.emode); dfree(c.epart); dfree(c.scal); dfree(c.step_dev);
   dfree(c.err); dfree(c.nbr); dfree(c.nshell); dfree(c.partners); dfree(c.rbl_mean);
-  dfree(c.rbl_part); dfree(c.rbl_masks); dfree(c.rbl_slots); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
+  dfree(c.rbl_part); dfree(c.rbl_masks); dfree(c.rbl_slots); dfree(c.rbl_cpart); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
   dfree(c.thermo);
   dfree(c.vl_list); dfree(c.vl_len); dfree(c.vl_listq); dfree(c.vl_lenq); dfree(c.vl_ref);
   dfree(c.s4); dfree(c.cs4); dfree(c.vl_flags); dfree(c.vl_count);
@@ -166,7 +167,7 @@ int64_t kernels_per_step(const Ctx &c) {
   k += 6;                                // count, 3 scan passes, scatter, rank+permute
   k += 1;                                // sampler
   k += c.Nq > 0 ? 2 : 0;                 // structure factor + combine
-  if (c.rbl) k += 3;                     // RBL, mean, subtract
+  if (c.rbl) k += 4;                     // RBL, compact partials, mean, subtract
   else k += (c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2;  // pair passes
   if (c.vl_on)                           // check, identity copy, build(s), commit
     k += 3 + ((c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2);
@@ -462,6 +463,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
     rc |= dalloc(c, &c.rbl_part, c.n_rbl_blk * 3);
     rc |= dalloc(c, &c.rbl_masks, rbl_mask_words(c.rbl_nslots));
     rc |= dalloc(c, &c.rbl_slots, c.rbl_nslots);
+    rc |= dalloc(c, &c.rbl_cpart, rbl_compact_count(c.n_rbl_blk) * (NQ_PAIR + 3));
   }
   rc |= dalloc(c, &c.rbl_mean, 3);
   rc |= dalloc(c, &c.outf, 3 * N);

@@ -137,6 +137,7 @@ struct Ctx {
   double *rbl_mean = nullptr;  // 3 doubles: mean short-range force
   double *rbl_part = nullptr;  // RBL blocks x 3
   uint32_t *rbl_masks = nullptr;  // RBL: per slot, warp, chunk and lane: shell masks
+  double *rbl_cpart = nullptr;     // RBL: compacted partials (energies NQ_PAIR, then F~ sums 3)
   int *rbl_slots = nullptr;         // RBL: slot pool flags
   int64_t rbl_nslots = 0;
   float *outf = nullptr;       // 3N id-order staging
