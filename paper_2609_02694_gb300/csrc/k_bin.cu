@@ -171,56 +171,91 @@ struct PermuteArgs {
   const int32_t *gate;    // nullable: always run
 };
 
-// One warp per cell: rank members by id (and charged members among themselves), then move
-// every field of the particle to its final slot.
-__global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (c >= a.ncell || gated_off(a.gate)) return;
-  const int32_t beg = a.cell_start[c];
-  const int32_t cnt = a.cell_start[c + 1] - beg;
-  const int32_t cbeg = a.ccell_start[c];
+// Move every field of the particle in provisional slot o to its final slot p (and, when
+// charged, to charged slot pc of the charged subset).
+__device__ __forceinline__ void move_particle(const PermuteArgs &a, int32_t o, int64_t p,
+                                              int32_t myid, bool mych, int64_t pc) {
   const int64_t N = a.N, Nq = a.Nq;
-  for (int kb = 0; kb < cnt; kb += 32) {
-    const int k = kb + lane;
+  const uint32_t sx = a.s0[o], sy = a.s0[N + o], sz = a.s0[2 * N + o];
+  a.s1[p] = sx; a.s1[N + p] = sy; a.s1[2 * N + p] = sz;
+  if (a.vf0) { a.vf1[p] = a.vf0[o]; a.vf1[N + p] = a.vf0[N + o]; a.vf1[2 * N + p] = a.vf0[2 * N + o]; }
+  if (a.vd0) { a.vd1[p] = a.vd0[o]; a.vd1[N + p] = a.vd0[N + o]; a.vd1[2 * N + p] = a.vd0[2 * N + o]; }
+  a.id1[p] = myid;
+  const float qv = a.qf0[o];
+  a.qf1[p] = qv;
+  if (a.qd0) a.qd1[p] = a.qd0[o];
+  if (a.ty0) a.ty1[p] = a.ty0[o];
+  a.im1[p] = a.im0[o];
+  if (a.s4) a.s4[p] = make_uint4(sx, sy, sz, __float_as_uint(qv));
+  if (mych) {
+    a.cs[pc] = sx; a.cs[Nq + pc] = sy; a.cs[2 * Nq + pc] = sz;
+    a.cqf[pc] = qv;
+    if (a.cqd) a.cqd[pc] = a.qd0[o];
+    a.cmap[pc] = (int32_t)p;
+    if (a.cs4) a.cs4[pc] = make_uint4(sx, sy, sz, __float_as_uint(qv));
+  }
+}
+
+constexpr int kCellsPerWarp = 4;
+
+// One warp per kCellsPerWarp consecutive cells: rank members by id (and charged members
+// among themselves), then move every field to the final slot. When no cell of the four
+// holds more than 8 particles (dilute systems), each cell gets 8 lanes; otherwise the warp
+// takes the cells one after another, 32 members at a time.
+__global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t c0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kCellsPerWarp;
+  if (c0 >= a.ncell || gated_off(a.gate)) return;
+  int cnt4 = 0;
+  if (lane < kCellsPerWarp && c0 + lane < a.ncell)
+    cnt4 = a.cell_start[c0 + lane + 1] - a.cell_start[c0 + lane];
+  if (__all_sync(FULL, cnt4 <= 8)) {
+    const int64_t c = c0 + (lane >> 3);
+    const int k = lane & 7;
+    const bool cell_ok = c < a.ncell;
+    const int32_t beg = cell_ok ? a.cell_start[c] : 0;
+    const int32_t cnt = cell_ok ? a.cell_start[c + 1] - beg : 0;
     const bool valid = k < cnt;
     const int32_t o = valid ? a.tmp[beg + k] : 0;
     const int32_t myid = valid ? a.id0[o] : INT_MAX;
-    const bool mych = valid && a.qf0[o] != 0.0f;
+    const int mych = (valid && a.qf0[o] != 0.0f) ? 1 : 0;
     int rank = 0, crank = 0;
-    for (int mb = 0; mb < cnt; mb += 32) {
-      const int mm = mb + lane;
-      const int32_t ov = mm < cnt ? a.tmp[beg + mm] : 0;
-      const int32_t oid = mm < cnt ? a.id0[ov] : INT_MAX;
-      const int och = (mm < cnt && a.qf0[ov] != 0.0f) ? 1 : 0;
-      const int lim = min(32, cnt - mb);
-      for (int t = 0; t < lim; ++t) {
-        const int32_t x = __shfl_sync(0xffffffffu, oid, t);
-        const int xc = __shfl_sync(0xffffffffu, och, t);
-        if (x < myid) { ++rank; crank += xc; }
-      }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {  // 8-lane segments: lanes past the count hold INT_MAX
+      const int32_t x = __shfl_sync(FULL, myid, t, 8);
+      const int xc = __shfl_sync(FULL, mych, t, 8);
+      if (x < myid) { ++rank; crank += xc; }
     }
-    if (valid) {
-      const int64_t p = beg + rank;
-      const uint32_t sx = a.s0[o], sy = a.s0[N + o], sz = a.s0[2 * N + o];
-      a.s1[p] = sx; a.s1[N + p] = sy; a.s1[2 * N + p] = sz;
-      if (a.vf0) { a.vf1[p] = a.vf0[o]; a.vf1[N + p] = a.vf0[N + o]; a.vf1[2 * N + p] = a.vf0[2 * N + o]; }
-      if (a.vd0) { a.vd1[p] = a.vd0[o]; a.vd1[N + p] = a.vd0[N + o]; a.vd1[2 * N + p] = a.vd0[2 * N + o]; }
-      a.id1[p] = myid;
-      const float qv = a.qf0[o];
-      a.qf1[p] = qv;
-      if (a.qd0) a.qd1[p] = a.qd0[o];
-      if (a.ty0) a.ty1[p] = a.ty0[o];
-      a.im1[p] = a.im0[o];
-      if (a.s4) a.s4[p] = make_uint4(sx, sy, sz, __float_as_uint(qv));
-      if (mych) {
-        const int64_t pc = cbeg + crank;
-        a.cs[pc] = sx; a.cs[Nq + pc] = sy; a.cs[2 * Nq + pc] = sz;
-        a.cqf[pc] = qv;
-        if (a.cqd) a.cqd[pc] = a.qd0[o];
-        a.cmap[pc] = (int32_t)p;
-        if (a.cs4) a.cs4[pc] = make_uint4(sx, sy, sz, __float_as_uint(qv));
+    if (valid) move_particle(a, o, beg + rank, myid, mych != 0, a.ccell_start[c] + crank);
+    return;
+  }
+  for (int q = 0; q < kCellsPerWarp; ++q) {
+    const int64_t c = c0 + q;
+    if (c >= a.ncell) break;
+    const int32_t beg = a.cell_start[c];
+    const int32_t cnt = a.cell_start[c + 1] - beg;
+    const int32_t cbeg = a.ccell_start[c];
+    for (int kb = 0; kb < cnt; kb += 32) {
+      const int k = kb + lane;
+      const bool valid = k < cnt;
+      const int32_t o = valid ? a.tmp[beg + k] : 0;
+      const int32_t myid = valid ? a.id0[o] : INT_MAX;
+      const bool mych = valid && a.qf0[o] != 0.0f;
+      int rank = 0, crank = 0;
+      for (int mb = 0; mb < cnt; mb += 32) {
+        const int mm = mb + lane;
+        const int32_t ov = mm < cnt ? a.tmp[beg + mm] : 0;
+        const int32_t oid = mm < cnt ? a.id0[ov] : INT_MAX;
+        const int och = (mm < cnt && a.qf0[ov] != 0.0f) ? 1 : 0;
+        const int lim = min(32, cnt - mb);
+        for (int t = 0; t < lim; ++t) {
+          const int32_t x = __shfl_sync(FULL, oid, t);
+          const int xc = __shfl_sync(FULL, och, t);
+          if (x < myid) { ++rank; crank += xc; }
+        }
       }
+      if (valid) move_particle(a, o, beg + rank, myid, mych, cbeg + crank);
     }
   }
 }
@@ -288,7 +323,7 @@ cudaError_t launch_bin_sort(Ctx &c) {
     a.s4 = c.vl_on ? c.s4 : nullptr;
     a.cs4 = c.vl_on ? c.cs4 : nullptr;
     a.gate = gate;
-    const int64_t threads = nc * 32;
+    const int64_t threads = (nc + kCellsPerWarp - 1) / kCellsPerWarp * 32;
     bin_rank_permute_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(a);
     if (gate)
       bin_identity_kernel<<<(unsigned)((N + c.Nq + 255) / 256), 256, 0, c.stream>>>(a);

@@ -12,15 +12,15 @@ namespace rbe {
 
 int64_t rbl_compact_count(int64_t nblk);
 
+// g_d = dt 2^32 / L_d (FP64, from the host): the fixed-point increment is rint(v g_d).
 template <typename V, typename FT>
 __global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
                                   const float *__restrict__ invm, uint32_t *__restrict__ s,
-                                  int64_t N, double hdk, double dt, double Lx, double Ly,
-                                  double Lz, int *__restrict__ err,
-                                  const double *__restrict__ scale) {
+                                  int64_t N, double hdk, double gx, double gy, double gz,
+                                  int *__restrict__ err, const double *__restrict__ scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const double L[3] = {Lx, Ly, Lz};
+  const double g[3] = {gx, gy, gz};
   const V im = (V)invm[i];
   const V sc = scale ? (V)*scale : (V)1;  // Nose-Hoover start-of-step scaling
   bool bad = false;
@@ -28,7 +28,7 @@ __global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
   for (int d = 0; d < 3; ++d) {
     V vv = v[d * N + i] * sc + (V)F[d * N + i] * im * (V)hdk;
     v[d * N + i] = vv;
-    const double inc = __ddiv_rn(__dmul_rn(__dmul_rn((double)vv, dt), kTwo32), L[d]);
+    const double inc = (double)vv * g[d];
     bad |= !isfinite(inc) || fabs(inc) > 2.0e9;
     const long long st = bad ? 0ll : __double2ll_rn(inc);
     s[d * N + i] += (uint32_t)st;
@@ -56,7 +56,9 @@ __global__ void __launch_bounds__(256)
       }
       v2 += (double)vv * (double)vv;
     }
-    ke = 0.5 * v2 / (double)invm[i] * inv_kappa;
+    // m = 1 / (1/m): FP64 division in the FP64 form, FP32 reciprocal otherwise
+    if (sizeof(V) == 8) ke = 0.5 * v2 / (double)invm[i] * inv_kappa;
+    else ke = 0.5 * v2 * (double)__frcp_rn(invm[i]) * inv_kappa;
   }
   sh[threadIdx.x] = ke;
   __syncthreads();
@@ -229,14 +231,14 @@ cudaError_t launch_kick_drift(Ctx &c) {
   const double hdk = 0.5 * c.dt * c.kappa;
   if (c.N == 0) return cudaSuccess;
   const double *scale = c.nvt ? c.thermo + 2 : nullptr;
+  const double gx = c.dt * kTwo32 / c.box[0], gy = c.dt * kTwo32 / c.box[1],
+               gz = c.dt * kTwo32 / c.box[2];
   if (c.precision == RBE_FP64)
     kick_drift_kernel<double, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vd[b], c.Fd, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err,
-        scale);
+        c.vd[b], c.Fd, c.invm[b], c.s[b], c.N, hdk, gx, gy, gz, c.err, scale);
   else
     kick_drift_kernel<float, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vf[b], c.F, c.invm[b], c.s[b], c.N, hdk, c.dt, c.box[0], c.box[1], c.box[2], c.err,
-        scale);
+        c.vf[b], c.F, c.invm[b], c.s[b], c.N, hdk, gx, gy, gz, c.err, scale);
   return cudaGetLastError();
 }
 
