@@ -505,6 +505,9 @@ def run_sweep16m(args):
                            synth.COULOMB_C, small.eps, small.sig)
     ke = 0.5 * (small.mass[:, None] * small.v ** 2).sum() / synth.ACCEL_KAPPA
     V = float(np.prod(small.box))
+    peaks = measured_peaks()
+    hbm = hbm_peak_gbs()
+    nq_big = int((big.q != 0).sum())
     for P in (100, 500, 2000):
         m, S = oracle.sample_k(1, 0, 0, small.box, synth.ALPHA, P)
         Fk, Uk, Wk = oracle.rbe_kspace(small.s, small.q, small.box, synth.ALPHA, synth.COULOMB_C,
@@ -526,11 +529,32 @@ def run_sweep16m(args):
             torch.cuda.synchronize()
             K = 2 if form == "fp64" else 3
             ms = _timed(lambda: h.step(1), K, stream)
+            h.set_profiling(True)
+            h.step(1)
+            ph, _ = h.profile()
             h.close()
-            print(json.dumps({"config": "sweep16m", "form": form, "P": P,
-                              "value": big.n * K / (ms / 1e3), "unit": UNIT,
-                              "ms_per_step": ms / K, "errors_65536_box": errs,
-                              "pressure_A3": (2 * ke + Wo) / (3 * V)}), flush=True)
+            pairs = nq_big * P
+            line = {"config": "sweep16m", "form": form, "P": P,
+                    "value": big.n * K / (ms / 1e3), "unit": UNIT,
+                    "ms_per_step": ms / K, "errors_65536_box": errs,
+                    "pressure_A3": (2 * ke + Wo) / (3 * V),
+                    "phases_ms_one_step": ph}
+            if form != "fp64":
+                line["rooflines"] = {
+                    "structure_factor": {"bound": "sfu", "unit": "sincos pairs/s",
+                                         "achieved": pairs / (ph["sf"] / 1e3),
+                                         "frac": pairs / (ph["sf"] / 1e3) / peaks["sincos_pairs"]},
+                    "gather": {"bound": "sfu", "unit": "sincos pairs/s",
+                               "achieved": pairs / (ph["gather"] / 1e3),
+                               "frac": pairs / (ph["gather"] / 1e3) / peaks["sincos_pairs"]},
+                    "bin": {"bound": "hbm", "unit": "GB/s",
+                            "achieved": big.n * BIN_BYTES / (ph["bin"] / 1e3) / 1e9,
+                            "frac": big.n * BIN_BYTES / (ph["bin"] / 1e3) / 1e9 / hbm[0]},
+                    "integrate": {"bound": "hbm", "unit": "GB/s",
+                                  "achieved": big.n * INTEGRATE_BYTES / ((ph["kick_drift"] + ph["tail"]) / 1e3) / 1e9,
+                                  "frac": big.n * INTEGRATE_BYTES / ((ph["kick_drift"] + ph["tail"]) / 1e3) / 1e9 / hbm[0]},
+                    "peaks": {"sincos_pairs": peaks["sincos_pairs"], "hbm_gbs": hbm[0]}}
+            print(json.dumps(line), flush=True)
 
 
 def run_rbl134m(args):

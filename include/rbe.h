@@ -97,7 +97,8 @@ typedef struct {
  *  mass  N masses (host), or NULL when rbe_step is not used (mass 1)
  *  vel   N x 3 velocities (host), or NULL for zero
  *  cuda_stream  a cudaStream_t the library launches on (NULL = legacy default stream)
- * Allocates all device memory for the system; no allocation happens after this call. */
+ * Allocates all device memory for the system; later calls allocate nothing, except
+ * rbe_set_neighbor_list (the list buffers) and rbe_measure_peak (64 bytes of scratch). */
 int rbe_init(rbe_handle *h, const rbe_params *p, int64_t N, const double box[3],
              const double *pos, const double *q, const int32_t *type, const double *mass,
              const double *vel, void *cuda_stream);
@@ -113,8 +114,8 @@ int rbe_sample_k(rbe_handle h, uint64_t step, int32_t *m_out, double *S_out);
 int rbe_set_positions(rbe_handle h, const double *pos, int on_device);
 
 /* One nonbonded force evaluation for step `step`:
- * bin + sort -> sample P modes -> structure factor -> k-space gather -> real space
- * (cell list, or RBL with the mean-force correction when r_core > 0) -> totals.
+ * bin + sort -> sample P modes -> structure factor -> real space (cell list or Verlet list,
+ * or RBL with the mean-force correction when r_core > 0) -> k-space gather -> totals.
  *  F_out     N x 3 float forces in id order (nullable), in host (F_on_device = 0) or
  *            device memory
  *  energies  RBE_N_ENERGY doubles (nullable, host)
@@ -196,7 +197,8 @@ int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kernels_per_step);
 /* Tunables of the launch shapes (none changes results beyond FP32 rounding order):
  *  RBE_TUNE_PAIR_TEST16  1: packed half-precision candidate pre-test in the cell-list pair
  *                        kernel (exact decision still at evaluation), 0: FP32 pre-test
- *  RBE_TUNE_SF_TILE      particles per block tile of the structure factor (32..1024, x32)
+ *  RBE_TUNE_SF_TILE      particles per block tile of the structure factor (32..1024, x32;
+ *                        at most as many tiles as the tile chosen at rbe_init allows)
  *  RBE_TUNE_RBL_EAGER    random batch list only. 1: the classifying pass evaluates every shell
  *                        pair too, and a particle with #S_i <= p keeps that sum (bit-identical
  *                        to the draw pass); 0: shell pairs only in the draw pass. The default
@@ -246,7 +248,8 @@ int rbe_measure_peak(int kind, double *ops_per_s, double *ms);
 /* Bytes of device memory held by the handle. */
 int rbe_get_memory(rbe_handle h, int64_t *bytes);
 
-/* Read and clear the device error flags (RBE_ERR_SAMPLER / RBE_ERR_NONFINITE bits). */
+/* Read and clear the device error flags; returns the first of RBE_ERR_SAMPLER,
+ * RBE_ERR_NONFINITE, RBE_ERR_CAPACITY that is set, else RBE_OK. Synchronises. */
 int rbe_check_device(rbe_handle h);
 
 /* Free every device buffer and the handle. NULL is accepted. */

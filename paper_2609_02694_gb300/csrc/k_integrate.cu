@@ -12,7 +12,10 @@ namespace rbe {
 
 int64_t rbl_compact_count(int64_t nblk);
 
-// g_d = dt 2^32 / L_d (FP64, from the host): the fixed-point increment is rint(v g_d).
+// g_d = dt 2^32 / L_d (FP64, from the host): the fixed-point increment is rint(v g_d), in
+// FP64 in the FP64 form. The FP32 forms round the FP32 product (off by at most one grid unit
+// of L / 2^32 where the FP64 rounding would differ); FP64 runs at 1/64 of the FP32 rate on
+// this GPU, and this pass would otherwise be bound by it instead of by memory.
 template <typename V, typename FT>
 __global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
                                   const float *__restrict__ invm, uint32_t *__restrict__ s,
@@ -28,9 +31,16 @@ __global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
   for (int d = 0; d < 3; ++d) {
     V vv = v[d * N + i] * sc + (V)F[d * N + i] * im * (V)hdk;
     v[d * N + i] = vv;
-    const double inc = (double)vv * g[d];
-    bad |= !isfinite(inc) || fabs(inc) > 2.0e9;
-    const long long st = bad ? 0ll : __double2ll_rn(inc);
+    int st;
+    if (sizeof(V) == 8) {
+      const double inc = (double)vv * g[d];
+      bad |= !isfinite(inc) || fabs(inc) > 2.0e9;
+      st = bad ? 0 : __double2int_rn(inc);
+    } else {
+      const float inc = (float)vv * (float)g[d];
+      bad |= !isfinite(inc) || fabsf(inc) > 2.0e9f;
+      st = bad ? 0 : __float2int_rn(inc);
+    }
     s[d * N + i] += (uint32_t)st;
   }
   if (bad) atomicOr(err, ERRBIT_NONFINITE);
@@ -46,7 +56,7 @@ __global__ void __launch_bounds__(256)
   double ke = 0.0;
   if (i < N) {
     const V im = (V)invm[i];
-    double v2 = 0.0;
+    V v2 = (V)0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       V vv = v[d * N + i];
@@ -54,11 +64,12 @@ __global__ void __launch_bounds__(256)
         vv += (V)F[d * N + i] * im * (V)hdk;
         v[d * N + i] = vv;
       }
-      v2 += (double)vv * (double)vv;
+      v2 += vv * vv;
     }
-    // m = 1 / (1/m): FP64 division in the FP64 form, FP32 reciprocal otherwise
-    if (sizeof(V) == 8) ke = 0.5 * v2 / (double)invm[i] * inv_kappa;
-    else ke = 0.5 * v2 * (double)__frcp_rn(invm[i]) * inv_kappa;
+    // 1/2 m v^2 / kappa, m = 1 / (1/m): FP64 in the FP64 form; the FP32 forms form each
+    // particle's term in FP32 and sum the terms in FP64
+    if (sizeof(V) == 8) ke = 0.5 * (double)v2 / (double)invm[i] * inv_kappa;
+    else ke = (double)(0.5f * (float)v2 * __frcp_rn(invm[i]) * (float)inv_kappa);
   }
   sh[threadIdx.x] = ke;
   __syncthreads();

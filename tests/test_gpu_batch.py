@@ -62,3 +62,38 @@ def test_replica_key_gives_independent_modes():
     import oracle
     mo, _ = oracle.sample_k(1, 0, 1, reps[0][1].box, synth.ALPHA, 64)
     assert np.array_equal(m1, mo)
+
+
+def test_batch_mixed_traversals_equal_individual_steps():
+    """A batch mixing a random-batch-list replica, a Verlet-list replica and a cell-list
+    replica replays exactly what each replica's own steps give (list rebuilds, RBL draws
+    and the RBL scratch pool included)."""
+    import torch
+    reps = _replicas([6000, 7000, 2500])
+
+    def make(r, sy):
+        if r == 0:
+            return binding.from_system(sy, P=64, alpha=synth.ALPHA, r_c=synth.R_CUT,
+                                       coulomb_C=synth.COULOMB_C, dt=1.0,
+                                       kappa=synth.ACCEL_KAPPA, replica=r, r_core=5.0,
+                                       p_rbl=10)
+        h = _handle(r, sy)
+        if r == 1:
+            h.set_neighbor_list(0.5)
+        return h
+
+    hb = [make(r, sy) for r, sy in reps]
+    hi = [make(r, sy) for r, sy in reps]
+    with binding.Batch(hb) as b:
+        b.step(4)
+        torch.cuda.synchronize()
+        for h in hi:
+            h.step(4)
+        for a, c in zip(hb, hi):
+            _, va, sa = a.state()
+            _, vc, sc = c.state()
+            assert np.array_equal(sa, sc) and np.array_equal(va, vc)
+            assert a.energies()[0]["total"] == c.energies()[0]["total"]
+    assert hb[1].neighbor_list_stats()["builds"] == hi[1].neighbor_list_stats()["builds"] >= 1
+    for h in hb + hi:
+        h.close()
