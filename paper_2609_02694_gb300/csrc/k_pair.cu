@@ -378,6 +378,9 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
       b2.set.qf = c.cqf; b2.set.qd = c.cqd; b2.set.type = nullptr;
       b2.set.cell_start = c.ccell_start; b2.set.map = c.cmap; b2.set.n = c.Nq;
       b2.accumulate = 1;
+      // FP32 pre-test: the dilute charged subset's groups then span more cells (the half-
+      // precision test bounds a group's extent), so fewer groups walk their stencils
+      b2.smax16 = 0;
       b2.epart = c.epart + c.off_coul;
       b2.nbr = nullptr;
       if (fp64) launch_one<double, false, true>(b2, c.Nq, false, wrap, c.stream);

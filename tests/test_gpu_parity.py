@@ -284,6 +284,17 @@ def test_rbl_span_bit_identical(orc, density, eager):
     assert np.array_equal(pa1, ref["partners"])
 
 
+def test_rbl_capacity_is_reported_not_faulted():
+    """A 27-cell stencil with more candidates than the per-chunk counters hold (6,144) is
+    skipped and reported as RBE_ERR_CAPACITY at the next synchronising call."""
+    sy = synth.make_system(30000, density=1.5, frac_charged=0.0, seed=10)
+    with handle(sy, 8, r_core=3.0, p_rbl=10, r_c=6.0) as h:
+        with pytest.raises(binding.RBEError) as e:
+            h.forces_f64(0)
+        assert e.value.code == -10
+        h.check_device()  # the flag was read and cleared: no error now
+
+
 # -------------------------------------------------------------------------- Verlet
 
 
