@@ -15,6 +15,8 @@
 // 128-byte line per warp and entry). Candidates are gathered as packed (s_x, s_y, s_z, q)
 // and go through the same exact cutoff decision as the cell kernel, so neighbour counts
 // are bit-exact against the oracle; pairs between r_c and r_list contribute nothing.
+#include <algorithm>
+
 #include "pair_common.cuh"
 
 namespace rbe {

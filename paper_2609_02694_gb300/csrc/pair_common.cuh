@@ -8,7 +8,6 @@
 namespace rbe {
 
 constexpr int kPairWarps = 4;
-constexpr int kListK = 64;
 
 struct PairArgs {
   PairSet set;
@@ -115,8 +114,8 @@ __device__ __forceinline__ void pair_force_v(const PairArgs &a, const LJTable *t
         erfcv = (real)erfc(pc.sqrt_alpha_d * (double)r);
         expv = (real)exp(-pc.alpha_d * (double)r2);
       } else {
-        r = (real)sqrtf((float)r2);
-        rinv = (real)__frcp_rn((float)r);
+        rinv = (real)rsqrtf((float)r2);  // 1/r and r from one reciprocal square root
+        r = r2 * rinv;
         erfcv = (real)erfcf(pc.sqrt_alpha * (float)r);
         expv = (real)expf(-pc.alpha * (float)r2);
       }
@@ -216,8 +215,8 @@ __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTabl
         erfcv = (real)erfc(pc.sqrt_alpha_d * (double)r);
         expv = (real)exp(-pc.alpha_d * (double)r2);
       } else {
-        r = (real)sqrtf((float)r2);
-        rinv = (real)__frcp_rn((float)r);
+        rinv = (real)rsqrtf((float)r2);  // 1/r and r from one reciprocal square root
+        r = r2 * rinv;
         erfcv = (real)erfcf(pc.sqrt_alpha * (float)r);
         expv = (real)expf(-pc.alpha * (float)r2);
       }
