@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--skin", type=float, default=None,
                     help="Verlet-list skin (A); 0 = cell traversal; default: timed trial of "
                          "0, 0.5, 1.0, 1.5 on the workload itself")
+    ap.add_argument("--tuning", default="auto",
+                    help="'auto' (rbe_autotune) or fixed values, e.g. pair_test16=1,sf_tile=256 "
+                         "(profiling runs: the autotuner's timings are distorted under ncu)")
     ap.add_argument("--ljelec-sizes", default="200000,1400000,7000000,28000000",
                     help="ion counts of --config ljelec")
     ap.add_argument("--no-extras", action="store_true",
@@ -290,7 +293,14 @@ def run_ours(args):
     skin, trial = pick_traversal(binding, sy, mk, args, stream)
     h = binding.from_system(sy, precision=args.precision, **mk)
     h.set_neighbor_list(skin)
-    tuned = h.autotune(3)
+    if args.tuning == "auto":
+        tuned = h.autotune(3)
+    else:
+        tuned = {}
+        for kv in args.tuning.split(","):
+            k, v = kv.split("=")
+            h.set_tuning(k, int(v))
+            tuned[k] = int(v)
     h.set_profiling(True)
     # exact unique-pair count of step 0 (the roofline's units) and the force sample
     F0, E0, _ = h.forces_f64(0)

@@ -11,9 +11,11 @@
 // of its members' stencils: for every (dy, dz) row, one contiguous run of cells in x.
 //  1. Stage: the warp loads 32 candidates j at a time. Each lane converts one of them to
 //     FP32 coordinates relative to the group leader and writes it to shared memory.
-//  2. Test: every lane tests its own i against the 32 staged j (broadcast reads) with a
-//     cutoff widened by 1e-5, and appends the hits to a per-lane list in shared memory.
-//     The append is branch-free.
+//  2. Test: every lane tests its own i against the staged j (broadcast reads) with a
+//     cutoff widened by 1e-5 and appends the window slot of each candidate to its own
+//     byte list in shared memory, advancing the list end only on a hit (branch-free: one
+//     store and one add a candidate). Slots past the run and lanes outside the group get
+//     test coordinates that can never hit.
 //  3. Evaluate: when a list may overflow, and at the end, each lane walks its own list.
 //     It recomputes the displacement exactly from the integer coordinates and applies
 //     the exact cutoff decision: FP32 outside a +-1e-5 band, FP64 inside it, which
@@ -44,6 +46,9 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
   __shared__ int32_t seg_beg[kPairWarps][kMaxSeg];
   __shared__ int32_t seg_pre[kPairWarps][kMaxSeg + 1];
   __shared__ double wred[kPairWarps][NQ_PAIR];
+  // per-lane hit lists (window slots), rows of 132 bytes so that lanes hit distinct banks
+  constexpr bool HL = !BUILD && !WRAP;
+  __shared__ uint8_t hits[kPairWarps][HL ? 32 : 1][HL ? 132 : 4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t n = a.set.n;
@@ -87,12 +92,14 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
       const uint32_t oz = __shfl_sync(FULL, szi, leader);
       // integer frame coordinates relative to the leader (exact); float / half test copies
       const int dxi = (int)(sxi - ox), dyi = (int)(syi - oy), dzi = (int)(szi - oz);
-      const float xi = (float)dxi * a.pc.h[0];
-      const float yi = (float)dyi * a.pc.h[1];
-      const float zi = (float)dzi * a.pc.h[2];
-      const __half2 xi2 = __float2half2_rn(xi * a.scale16);
-      const __half2 yi2 = __float2half2_rn(yi * a.scale16);
-      const __half2 zi2 = __float2half2_rn(zi * a.scale16);
+      // test coordinates; lanes outside the group get a point that no candidate can reach
+      const float far_i = T16 ? -30000.f : -1e30f;
+      const float xi = (HL && !in) ? far_i : (float)dxi * a.pc.h[0];
+      const float yi = (HL && !in) ? far_i : (float)dyi * a.pc.h[1];
+      const float zi = (HL && !in) ? far_i : (float)dzi * a.pc.h[2];
+      const __half2 xi2 = __float2half2_rn((HL && !in) ? far_i : xi * a.scale16);
+      const __half2 yi2 = __float2half2_rn((HL && !in) ? far_i : yi * a.scale16);
+      const __half2 zi2 = __float2half2_rn((HL && !in) ? far_i : zi * a.scale16);
       const __half2 thr2 = __float2half2_rn(66.5f);
       const int span = cxhi - cxlo + 2 * R0 + 1;
       // 1. Runs of candidates: one lane per stencil row (dz, dy) loads the row's cell
@@ -171,10 +178,71 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
             stage_d[wid][w][lane] = make_int4(dxj, dyj, dzj, MULTI ? a.set.type[j] : 0);
             if (COUL) stage_q[wid][w][lane] = a.set.qf[j];
             stage_j[wid][w][lane] = (int32_t)j;
+          } else if (HL) {  // past the run: a point that no lane can reach
+            if (T16) {
+              __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
+              const int o = lane >> 4;
+              h[o] = h[2 + o] = h[4 + o] = __float2half_rn(30000.f);
+            } else {
+              stage[wid][w][lane] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            }
           }
           sg = __shfl_sync(FULL, s, 31);
         }
         __syncwarp();
+        if (HL) {
+          // test and append (half-precision pairs or FP32), then evaluate the lane's hits
+          uint8_t *myl = &hits[wid][HL ? lane : 0][0];
+          int hc = 0;
+#pragma unroll
+          for (int w = 0; w < kWin; ++w) {
+            if (T16) {
+#pragma unroll
+              for (int pp = 0; pp < 16; ++pp) {
+                const uint4 v = stage16[wid][w][pp];
+                const __half2 dx2 = __hsub2(xi2, *reinterpret_cast<const __half2 *>(&v.x));
+                const __half2 dy2 = __hsub2(yi2, *reinterpret_cast<const __half2 *>(&v.y));
+                const __half2 dz2 = __hsub2(zi2, *reinterpret_cast<const __half2 *>(&v.z));
+                const __half2 r2 = __hfma2(dx2, dx2, __hfma2(dy2, dy2, __hmul2(dz2, dz2)));
+                const uint32_t hm = __hlt2_mask(r2, thr2);
+                myl[hc] = (uint8_t)(w * 32 + pp);
+                hc += (int)(hm & 1u);
+                myl[hc] = (uint8_t)(w * 32 + pp + 16);
+                hc += (int)((hm >> 16) & 1u);
+              }
+            } else {
+#pragma unroll
+              for (int tt = 0; tt < 32; ++tt) {
+                const float4 p = stage[wid][w][tt];
+                const float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
+                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                myl[hc] = (uint8_t)(w * 32 + tt);
+                hc += r2 < rc2_hi ? 1 : 0;
+              }
+            }
+          }
+          const int4 *sd = &stage_d[wid][0][0];
+          const float *sq = &stage_q[wid][0][0];
+          const int32_t *sj = &stage_j[wid][0][0];
+          // uniform trip count: the longest hit list of the warp in this window
+          const int nh = __reduce_max_sync(FULL, hc);
+          for (int k = 0; k < nh; ++k) {
+            const bool act = k < hc;
+            const int slot = myl[act ? k : 0];  // entry 0 is always written
+            const int4 d = sd[slot];
+            const int dsx = (int)((uint32_t)dxi - (uint32_t)d.x);
+            const int dsy = (int)((uint32_t)dyi - (uint32_t)d.y);
+            const int dsz = (int)((uint32_t)dzi - (uint32_t)d.z);
+            real qj = (real)0;
+            if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[sj[slot]] : (real)sq[slot];
+            // the particle itself is the one candidate at zero displacement
+            const bool self = (dsx | dsy | dsz) == 0;
+            pair_eval_masked<real, LJ, COUL, MULTI>(a, tab, act && !self, dsx, dsy, dsz, qi, ti,
+                                                    qj, d.w, acc);
+          }
+          __syncwarp();
+          continue;
+        }
         uint32_t m[kWin];
 #pragma unroll
         for (int w = 0; w < kWin; ++w) {

@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           // core pairs (and, eager, shell pairs), branch-light, in canonical order; the
           // particle itself (r = 0, always core) is skipped
           uint32_t bits = EAGER ? (mcore | mshell) : mcore;
-          while (__any_sync(FULL, bits != 0u)) {
+          const int nbits = __reduce_max_sync(FULL, __popc(bits));  // uniform trip count
+          for (int kb = 0; kb < nbits; ++kb) {
             const bool act = bits != 0u;
             const int tt = act ? __ffs(bits) - 1 : 0;
             bits &= bits - 1u;
