@@ -178,14 +178,24 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
             stage_d[wid][w][lane] = make_int4(dxj, dyj, dzj, MULTI ? a.set.type[j] : 0);
             if (COUL) stage_q[wid][w][lane] = a.set.qf[j];
             stage_j[wid][w][lane] = (int32_t)j;
-          } else if (HL) {  // past the run: a point that no lane can reach
-            if (T16) {
-              __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
-              const int o = lane >> 4;
-              h[o] = h[2 + o] = h[4 + o] = __float2half_rn(30000.f);
-            } else {
-              stage[wid][w][lane] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+          } else {
+            // Past the run: a valid dummy (set index 0, type 0, no charge). Idle lanes of
+            // the evaluation loops read some slot (slot 0 or 64, or the last one a hit list
+            // wrote) and gather its charge or LJ-table entry by index before the result is
+            // masked, so no slot may keep an index left by an earlier window or kernel. The
+            // hit lists also need test coordinates that no lane can reach.
+            if (HL) {
+              if (T16) {
+                __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
+                const int o = lane >> 4;
+                h[o] = h[2 + o] = h[4 + o] = __float2half_rn(30000.f);
+              } else {
+                stage[wid][w][lane] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+              }
             }
+            stage_d[wid][w][lane] = make_int4(0, 0, 0, 0);
+            if (COUL) stage_q[wid][w][lane] = 0.f;
+            stage_j[wid][w][lane] = 0;
           }
           sg = __shfl_sync(FULL, s, 31);
         }
