@@ -9,17 +9,20 @@
 // Work decomposition (one thread per particle i, 32 consecutive cell-sorted particles per
 // warp). Lanes sharing a cell row (c_y, c_z) form a group, and the group walks the union
 // of its members' stencils: for every (dy, dz) row, one contiguous run of cells in x.
-//  1. Stage: the warp loads 32 candidates j at a time. Each lane converts one of them to
-//     FP32 coordinates relative to the group leader and writes it to shared memory.
+//  1. Stage: the warp loads 32 candidates j at a time (a chunk) into a ring of four
+//     chunk positions in shared memory. Each lane converts one of them to coordinates
+//     relative to the group leader: half-precision test copies, exact integers.
 //  2. Test: every lane tests its own i against the staged j (broadcast reads) with a
-//     cutoff widened by 1e-5 and appends the window slot of each candidate to its own
-//     byte list in shared memory, advancing the list end only on a hit (branch-free: one
+//     cutoff widened beyond the worst rounding and appends the ring slot of each candidate
+//     to its own FIFO in shared memory, advancing the tail only on a hit (branch-free: one
 //     store and one add a candidate). Slots past the run and lanes outside the group get
 //     test coordinates that can never hit.
-//  3. Evaluate: when a list may overflow, and at the end, each lane walks its own list.
-//     It recomputes the displacement exactly from the integer coordinates and applies
-//     the exact cutoff decision: FP32 outside a +-1e-5 band, FP64 inside it, which
-//     matches the oracle's decision bit for bit. Then it evaluates the pair force.
+//  3. Evaluate: before a chunk overwrites a ring position, the warp runs just enough
+//     iterations that every lane has consumed its hits staged there; every lane with hits
+//     pending evaluates in each iteration, so lanes light on old chunks work ahead. Each
+//     lane recomputes the displacement exactly from the integer coordinates and applies
+//     the exact cutoff decision: FP32 outside a +-1e-5 band, FP64 inside it, which matches
+//     the oracle's decision bit for bit. Then it evaluates the pair force.
 // Forces are summed per i in a fixed j order with no atomics, so results are run-to-run
 // reproducible. The hot loop is FP32 ALU / SFU bound.
 // The BUILD variant walks the same windows with the list radius r_c + skin and, instead of
@@ -35,6 +38,8 @@ namespace rbe {
 constexpr int kMaxRows = 49;            // (2R+1)^2 stencil rows for R <= 3
 constexpr int kMaxSeg = 2 * kMaxRows;   // a row wraps into at most two runs of cells
 constexpr int kWin = 4;                 // chunks of 32 candidates staged per window
+constexpr int kHitQ = 160;              // hit FIFO capacity: 4 chunks pending + one being tested
+constexpr int kHitRow = kHitQ + 4;
 
 template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
 __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a) {
@@ -42,13 +47,16 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
   __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
   __shared__ int4 stage_d[kPairWarps][kWin][32];               // exact integer frame coords, type
   __shared__ float stage_q[kPairWarps][kWin][32];
-  __shared__ int32_t stage_j[kPairWarps][kWin][32];
+  // candidate indices: read by the FP64 charge gather and by the list build only
+  constexpr bool NEEDJ = BUILD || (COUL && sizeof(real) == 8);
+  __shared__ int32_t stage_j[kPairWarps][kWin][NEEDJ ? 32 : 1];
   __shared__ int32_t seg_beg[kPairWarps][kMaxSeg];
   __shared__ int32_t seg_pre[kPairWarps][kMaxSeg + 1];
   __shared__ double wred[kPairWarps][NQ_PAIR];
-  // per-lane hit lists (window slots), rows of 132 bytes so that lanes hit distinct banks
+  // per-lane FIFOs of pending hits (ring slots); rows of 164 bytes (41 words) so that the
+  // 32 lanes' rows start on distinct banks
   constexpr bool HL = !BUILD && !WRAP;
-  __shared__ uint8_t hits[kPairWarps][HL ? 32 : 1][HL ? 132 : 4];
+  __shared__ uint8_t hits[kPairWarps][HL ? 32 : 1][HL ? kHitRow : 4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t n = a.set.n;
@@ -147,112 +155,175 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
       if (lane == 0) seg_pre[wid][2 * nrows] = carry;
       __syncwarp();
       const int T = carry;
-      // 2. Windows of kWin chunks of 32 candidates: stage (one candidate per lane and
-      //    chunk), test every staged candidate against the lane's own i (bit masks), then
-      //    evaluate the hits directly from the staged exact coordinates.
+      // Stage candidate c of the run (one per lane) at chunk position w of the ring, in two
+      // parts so that the global loads of the next chunk can be in flight while this one is
+      // tested: load (run search, coordinates, type, charge, index) and store (test
+      // coordinates, exact integer frame coordinates and type, charge, index). Past the
+      // run: a valid dummy (set index 0, type 0, no charge) with test coordinates that no
+      // lane can reach. Idle lanes of the evaluation loops read some staged slot and gather
+      // its charge or LJ-table entry by index before the result is masked, so no slot may
+      // keep an index left by an earlier chunk or kernel.
+      struct Cand { uint32_t x, y, z; int t; float q; int32_t j; bool v; };
+      auto load_one = [&](int c, int &s, Cand &r) {
+        r.v = c < T;
+        r.x = r.y = r.z = 0u; r.t = 0; r.q = 0.f; r.j = 0;
+        if (r.v) {
+          while (seg_pre[wid][s + 1] <= c) ++s;
+          const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
+          r.x = a.set.sx[j]; r.y = a.set.sy[j]; r.z = a.set.sz[j];
+          if (MULTI) r.t = a.set.type[j];
+          if (COUL) r.q = a.set.qf[j];
+          r.j = (int32_t)j;
+        }
+      };
+      auto store_one = [&](int w, const Cand &r) {
+        if (r.v) {
+          const int dxj = (int)(r.x - ox), dyj = (int)(r.y - oy), dzj = (int)(r.z - oz);
+          const float fx = (float)dxj * a.pc.h[0];
+          const float fy = (float)dyj * a.pc.h[1];
+          const float fz = (float)dzj * a.pc.h[2];
+          if (T16) {
+            // entry p packs candidates p (low halves) and p + 16 (high halves), so that
+            // bit b of the test mask is candidate b
+            __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
+            const int o = lane >> 4;
+            h[o] = __float2half_rn(fx * a.scale16);
+            h[2 + o] = __float2half_rn(fy * a.scale16);
+            h[4 + o] = __float2half_rn(fz * a.scale16);
+          } else {
+            stage[wid][w][lane] = make_float4(fx, fy, fz, 0.f);
+          }
+          stage_d[wid][w][lane] = make_int4(dxj, dyj, dzj, r.t);
+        } else {
+          if (T16) {
+            __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
+            const int o = lane >> 4;
+            h[o] = h[2 + o] = h[4 + o] = __float2half_rn(30000.f);
+          } else {
+            stage[wid][w][lane] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+          }
+          stage_d[wid][w][lane] = make_int4(0, 0, 0, 0);
+        }
+        if (COUL) stage_q[wid][w][lane] = r.q;
+        if (NEEDJ) stage_j[wid][w][lane] = r.j;
+      };
+      const int4 *sd = &stage_d[wid][0][0];
+      const float *sq = &stage_q[wid][0][0];
+      const int32_t *sj = &stage_j[wid][0][0];
+      if (HL) {
+        // 2. Chunks of 32 candidates through a ring of kWin staged chunks. Each lane tests
+        //    every staged candidate and appends its hits (ring slots) to its FIFO; before a
+        //    chunk overwrites a ring position, the warp evaluates just enough iterations
+        //    that every lane has consumed its hits staged there. Every lane with anything
+        //    pending evaluates in each iteration, so a lane that is light on the oldest
+        //    chunk works ahead on newer ones: the warp's trip count follows its heaviest
+        //    lane over four chunks instead of one window. Each lane still evaluates its hits
+        //    in candidate order.
+        uint8_t *myq = &hits[wid][HL ? lane : 0][0];
+        // FIFO read and write index, read wrap point, pending count (explicit: a full FIFO
+        // can have hd == tl)
+        int hd = 0, tl = 0, wrap = kHitQ, cnt = 0;
+        uint32_t q4 = 0u;                  // hits appended per ring position (8-bit fields)
+        const int nch = (T + 31) >> 5;
+        int sg = 0;
+        Cand nx;  // the next chunk's candidate of this lane, loaded ahead
+        {
+          int s = sg;
+          load_one(lane, s, nx);
+          sg = __shfl_sync(FULL, s, 31);
+        }
+        for (int ch = 0; ch <= nch; ++ch) {
+          const int p = ch & (kWin - 1);
+          if (ch >= kWin || ch == nch) {
+            // The pending hits of ring position p (chunk ch - kWin) are the oldest ones:
+            // all pending minus those of the newer chunks. After the last chunk: all.
+            int need = cnt;
+            if (ch < nch) {
+              const int newer = (int)((q4 * 0x01010101u) >> 24) - (int)((q4 >> (8 * p)) & 0xffu);
+              need = max(0, cnt - newer);
+            }
+            const int nit = __reduce_max_sync(FULL, need);
+            const int dummy = ((ch - 1) & (kWin - 1)) * 32;  // a slot of the latest chunk
+            for (int k = 0; k < nit; ++k) {
+              const bool act = k < cnt;
+              const int slot = act ? (int)myq[hd] : dummy;
+              const int4 d = sd[slot];
+              const int dsx = (int)((uint32_t)dxi - (uint32_t)d.x);
+              const int dsy = (int)((uint32_t)dyi - (uint32_t)d.y);
+              const int dsz = (int)((uint32_t)dzi - (uint32_t)d.z);
+              real qj = (real)0;
+              if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[sj[slot]] : (real)sq[slot];
+              // (the particle itself, at zero displacement, is excluded by the evaluation)
+              pair_eval_masked<real, LJ, COUL, MULTI>(a, tab, act, dsx, dsy, dsz, qi, ti, qj,
+                                                      d.w, acc);
+              hd += act ? 1 : 0;
+              hd = hd == wrap ? 0 : hd;
+            }
+            cnt = max(0, cnt - nit);
+            __syncwarp();  // position p is free for every lane
+          }
+          if (ch == nch) break;
+          store_one(p, nx);
+          if (ch + 1 < nch) {
+            int s = sg;
+            load_one(32 * (ch + 1) + lane, s, nx);
+            sg = __shfl_sync(FULL, s, 31);
+          }
+          __syncwarp();
+          // The writer wraps only here, so that the appends below stay linear: at most
+          // 3 x 32 hits are pending now, so from tl >= kHitQ - 32 the reader is in the same
+          // segment; otherwise a reader that has wrapped clears the old wrap point.
+          if (tl >= kHitQ - 32) {
+            wrap = cnt == 0 ? kHitQ : tl;
+            hd = cnt == 0 ? 0 : hd;
+            tl = 0;
+          } else if (hd <= tl) {
+            wrap = kHitQ;
+          }
+          const int t0 = tl;
+          if (T16) {
+#pragma unroll
+            for (int pp = 0; pp < 16; ++pp) {
+              const uint4 v = stage16[wid][p][pp];
+              const __half2 dx2 = __hsub2(xi2, *reinterpret_cast<const __half2 *>(&v.x));
+              const __half2 dy2 = __hsub2(yi2, *reinterpret_cast<const __half2 *>(&v.y));
+              const __half2 dz2 = __hsub2(zi2, *reinterpret_cast<const __half2 *>(&v.z));
+              const __half2 r2 = __hfma2(dx2, dx2, __hfma2(dy2, dy2, __hmul2(dz2, dz2)));
+              const uint32_t hm = __hlt2_mask(r2, thr2);
+              myq[tl] = (uint8_t)(p * 32 + pp);
+              tl += (int)(hm & 1u);
+              myq[tl] = (uint8_t)(p * 32 + pp + 16);
+              tl += (int)((hm >> 16) & 1u);
+            }
+          } else {
+#pragma unroll
+            for (int tt = 0; tt < 32; ++tt) {
+              const float4 q = stage[wid][p][tt];
+              const float ddx = xi - q.x, ddy = yi - q.y, ddz = zi - q.z;
+              const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+              myq[tl] = (uint8_t)(p * 32 + tt);
+              tl += r2 < rc2_hi ? 1 : 0;
+            }
+          }
+          cnt += tl - t0;
+          q4 = (q4 & ~(0xffu << (8 * p))) | ((uint32_t)(tl - t0) << (8 * p));
+        }
+        continue;
+      }
+      // 2. (Lists and small boxes.) Windows of kWin chunks of 32 candidates: stage, test
+      //    every staged candidate against the lane's own i (bit masks), then evaluate (or
+      //    list) the hits directly from the staged exact coordinates.
       int sg = 0;
       for (int base = 0; base < T; base += 32 * kWin) {
 #pragma unroll
         for (int w = 0; w < kWin; ++w) {
-          const int c = base + 32 * w + lane;
           int s = sg;
-          if (c < T) {
-            while (seg_pre[wid][s + 1] <= c) ++s;
-            const int64_t j = seg_beg[wid][s] + (c - seg_pre[wid][s]);
-            const int dxj = (int)(a.set.sx[j] - ox), dyj = (int)(a.set.sy[j] - oy),
-                      dzj = (int)(a.set.sz[j] - oz);
-            const float fx = (float)dxj * a.pc.h[0];
-            const float fy = (float)dyj * a.pc.h[1];
-            const float fz = (float)dzj * a.pc.h[2];
-            if (T16) {
-              // entry p packs candidates p (low halves) and p + 16 (high halves), so that
-              // bit b of the test mask is candidate b
-              __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
-              const int o = lane >> 4;
-              h[o] = __float2half_rn(fx * a.scale16);
-              h[2 + o] = __float2half_rn(fy * a.scale16);
-              h[4 + o] = __float2half_rn(fz * a.scale16);
-            } else {
-              stage[wid][w][lane] = make_float4(fx, fy, fz, 0.f);
-            }
-            stage_d[wid][w][lane] = make_int4(dxj, dyj, dzj, MULTI ? a.set.type[j] : 0);
-            if (COUL) stage_q[wid][w][lane] = a.set.qf[j];
-            stage_j[wid][w][lane] = (int32_t)j;
-          } else {
-            // Past the run: a valid dummy (set index 0, type 0, no charge). Idle lanes of
-            // the evaluation loops read some slot (slot 0 or 64, or the last one a hit list
-            // wrote) and gather its charge or LJ-table entry by index before the result is
-            // masked, so no slot may keep an index left by an earlier window or kernel. The
-            // hit lists also need test coordinates that no lane can reach.
-            if (HL) {
-              if (T16) {
-                __half *h = reinterpret_cast<__half *>(&stage16[wid][w][lane & 15]);
-                const int o = lane >> 4;
-                h[o] = h[2 + o] = h[4 + o] = __float2half_rn(30000.f);
-              } else {
-                stage[wid][w][lane] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
-              }
-            }
-            stage_d[wid][w][lane] = make_int4(0, 0, 0, 0);
-            if (COUL) stage_q[wid][w][lane] = 0.f;
-            stage_j[wid][w][lane] = 0;
-          }
+          Cand r;
+          load_one(base + 32 * w + lane, s, r);
           sg = __shfl_sync(FULL, s, 31);
+          store_one(w, r);
         }
         __syncwarp();
-        if (HL) {
-          // test and append (half-precision pairs or FP32), then evaluate the lane's hits
-          uint8_t *myl = &hits[wid][HL ? lane : 0][0];
-          int hc = 0;
-#pragma unroll
-          for (int w = 0; w < kWin; ++w) {
-            if (T16) {
-#pragma unroll
-              for (int pp = 0; pp < 16; ++pp) {
-                const uint4 v = stage16[wid][w][pp];
-                const __half2 dx2 = __hsub2(xi2, *reinterpret_cast<const __half2 *>(&v.x));
-                const __half2 dy2 = __hsub2(yi2, *reinterpret_cast<const __half2 *>(&v.y));
-                const __half2 dz2 = __hsub2(zi2, *reinterpret_cast<const __half2 *>(&v.z));
-                const __half2 r2 = __hfma2(dx2, dx2, __hfma2(dy2, dy2, __hmul2(dz2, dz2)));
-                const uint32_t hm = __hlt2_mask(r2, thr2);
-                myl[hc] = (uint8_t)(w * 32 + pp);
-                hc += (int)(hm & 1u);
-                myl[hc] = (uint8_t)(w * 32 + pp + 16);
-                hc += (int)((hm >> 16) & 1u);
-              }
-            } else {
-#pragma unroll
-              for (int tt = 0; tt < 32; ++tt) {
-                const float4 p = stage[wid][w][tt];
-                const float ddx = xi - p.x, ddy = yi - p.y, ddz = zi - p.z;
-                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                myl[hc] = (uint8_t)(w * 32 + tt);
-                hc += r2 < rc2_hi ? 1 : 0;
-              }
-            }
-          }
-          const int4 *sd = &stage_d[wid][0][0];
-          const float *sq = &stage_q[wid][0][0];
-          const int32_t *sj = &stage_j[wid][0][0];
-          // uniform trip count: the longest hit list of the warp in this window
-          const int nh = __reduce_max_sync(FULL, hc);
-          for (int k = 0; k < nh; ++k) {
-            const bool act = k < hc;
-            const int slot = myl[act ? k : 0];  // entry 0 is always written
-            const int4 d = sd[slot];
-            const int dsx = (int)((uint32_t)dxi - (uint32_t)d.x);
-            const int dsy = (int)((uint32_t)dyi - (uint32_t)d.y);
-            const int dsz = (int)((uint32_t)dzi - (uint32_t)d.z);
-            real qj = (real)0;
-            if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[sj[slot]] : (real)sq[slot];
-            // the particle itself is the one candidate at zero displacement
-            const bool self = (dsx | dsy | dsz) == 0;
-            pair_eval_masked<real, LJ, COUL, MULTI>(a, tab, act && !self, dsx, dsy, dsz, qi, ti,
-                                                    qj, d.w, acc);
-          }
-          __syncwarp();
-          continue;
-        }
         uint32_t m[kWin];
 #pragma unroll
         for (int w = 0; w < kWin; ++w) {
@@ -293,9 +364,6 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
         // lanes run a masked dummy so the loop body has no divergent branch
         uint64_t mA = (uint64_t)m[0] | ((uint64_t)m[1] << 32);
         uint64_t mB = (uint64_t)m[2] | ((uint64_t)m[3] << 32);
-        const int4 *sd = &stage_d[wid][0][0];
-        const float *sq = &stage_q[wid][0][0];
-        const int32_t *sj = &stage_j[wid][0][0];
         // uniform trip count: the largest number of hits of any lane in this window
         const int nhit = __reduce_max_sync(FULL, __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]));
         for (int k = 0; k < nhit; ++k) {
@@ -322,11 +390,10 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
           } else {
             real qj = (real)0;
             if (COUL) qj = sizeof(real) == 8 ? (real)a.set.qd[sj[slot]] : (real)sq[slot];
-            // the particle itself is the one candidate at zero displacement (coincident
-            // particles, which no valid configuration has, would be skipped the same way)
-            const bool self = (dsx | dsy | dsz) == 0;
-            pair_eval_masked<real, LJ, COUL, MULTI>(a, tab, act && !self, dsx, dsy, dsz, qi, ti,
-                                                    qj, d.w, acc);
+            // the particle itself, at zero displacement, is excluded by the evaluation
+            // (coincident particles, which no valid configuration has, would be too)
+            pair_eval_masked<real, LJ, COUL, MULTI>(a, tab, act, dsx, dsy, dsz, qi, ti, qj, d.w,
+                                                    acc);
           }
         }
         __syncwarp();

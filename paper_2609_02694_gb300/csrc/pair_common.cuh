@@ -154,8 +154,10 @@ __device__ __forceinline__ void pair_force(const PairArgs &a, const LJTable *tab
 // Branch-light evaluation for the cell-list kernel: `act` says whether this lane holds a
 // candidate pair at all (idle lanes compute a masked dummy). The cutoff decision is exact:
 // FP32 outside the +-1e-5 band around r_c^2, the oracle's FP64 expression inside it (a
-// rare, divergent branch); in the FP64 form always the FP64 expression. Every
-// contribution is multiplied by the 0/1 decision, so no early return diverges the warp.
+// rare, divergent branch); in the FP64 form always the FP64 expression. A zero
+// displacement (the particle itself; r^2 = 0 exactly when the integer displacement is 0)
+// is never a pair. Rejected and idle lanes evaluate with 1/r^2 = 0, which makes every LJ
+// term an exact zero, so no early return diverges the warp.
 template <typename real, bool LJ, bool COUL, bool MULTI>
 __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTable *tab,
                                                  bool act, int dsx, int dsy, int dsz, real qi,
@@ -171,19 +173,21 @@ __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTabl
     r2 = (real)__dadd_rn(__dadd_rn(__dmul_rn((double)dx, (double)dx),
                                    __dmul_rn((double)dy, (double)dy)),
                          __dmul_rn((double)dz, (double)dz));
-    inside = act && (double)r2 <= pc.rc2d;
+    inside = act && (double)r2 <= pc.rc2d && (double)r2 > 0.0;
   } else {
     dx = (real)((float)dsx * pc.h[0]);
     dy = (real)((float)dsy * pc.h[1]);
     dz = (real)((float)dsz * pc.h[2]);
     r2 = dx * dx + dy * dy + dz * dz;
-    inside = act && (float)r2 < pc.rc2_lo;
+    inside = act && (float)r2 < pc.rc2_lo && (float)r2 > 0.f;
     const bool band = act && (float)r2 >= pc.rc2_lo && (float)r2 <= pc.rc2_hi;
     if (band) inside = exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d;
   }
   acc.nbr += inside ? 1 : 0;
-  const real on = inside ? (real)1 : (real)0;
-  const real r2s = inside ? r2 : (real)1;  // keeps idle and rejected lanes finite
+  // off the pair: 1/r^2 = 0 exactly (FP64: 1/inf; FP32: the fast quotient is documented
+  // to return 0 for divisors between 2^126 and 2^128)
+  const real r2s = inside ? r2 : (sizeof(real) == 8 ? (real)__longlong_as_double(0x7ff0000000000000ll)
+                                                    : (real)1e38f);
   real g = (real)0;
   if (LJ) {
     real e24, e4, s2;
@@ -200,10 +204,10 @@ __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTabl
     else rinv2 = (real)__fdividef(1.0f, (float)r2s);  // fast reciprocal (2 ulp)
     const real sr2 = s2 * rinv2;
     const real sr6 = sr2 * sr2 * sr2;
-    const real gl = on * e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);
+    const real gl = e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);
     g += gl;
-    acc.ulj += on * e4 * sr6 * (sr6 - (real)1);
-    acc.wlj += gl * r2s;
+    acc.ulj += e4 * sr6 * (sr6 - (real)1);
+    acc.wlj += gl * r2;  // (r2 is finite for every lane; gl is 0 off the pair)
   }
   if (COUL) {
     const real qq = qi * qj;
