@@ -176,8 +176,8 @@ cudaError_t launch_list_pair(Ctx &c, bool want_counts) {
   PairArgs &a = la.pa;
   a.grid = c.grid;
   a.pc = c.pc;
-  a.eps24 = c.lj.eps24[0]; a.eps4 = c.lj.eps4[0]; a.sig2 = c.lj.sig2[0];
-  a.eps24d = c.lj.eps24d[0]; a.eps4d = c.lj.eps4d[0]; a.sig2d = c.lj.sig2d[0];
+  a.ljA = c.lj.A[0]; a.ljB = c.lj.B[0]; a.ljA12 = c.lj.A12[0]; a.ljB6 = c.lj.B6[0];
+  a.ljAd = c.lj.Ad[0]; a.ljBd = c.lj.Bd[0]; a.ljA12d = c.lj.A12d[0]; a.ljB6d = c.lj.B6d[0];
   a.table = reinterpret_cast<const LJTable *>(c.lj_dev);
   a.F = c.F; a.Fd = c.Fd; a.Fstride = c.N;
   a.set.sx = c.s[b]; a.set.sy = c.s[b] + c.N; a.set.sz = c.s[b] + 2 * c.N;

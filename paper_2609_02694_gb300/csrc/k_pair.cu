@@ -12,11 +12,11 @@
 //  1. Stage: the warp loads 32 candidates j at a time (a chunk) into a ring of four
 //     chunk positions in shared memory. Each lane converts one of them to coordinates
 //     relative to the group leader: half-precision test copies, exact integers.
-//  2. Test: every lane tests its own i against the staged j (broadcast reads) with a
-//     cutoff widened beyond the worst rounding and appends the ring slot of each candidate
-//     to its own FIFO in shared memory, advancing the tail only on a hit (branch-free: one
-//     store and one add a candidate). Slots past the run and lanes outside the group get
-//     test coordinates that can never hit.
+//  2. Test: every lane tests its own i against the staged j (broadcast reads, two
+//     candidates per half-precision instruction) with a cutoff widened beyond the worst
+//     rounding, collects a 32-bit hit mask and appends the ring slots of its hits to its
+//     own FIFO in shared memory. Slots past the run and lanes outside the group get test
+//     coordinates that can never hit.
 //  3. Evaluate: before a chunk overwrites a ring position, the warp runs just enough
 //     iterations that every lane has consumed its hits staged there; every lane with hits
 //     pending evaluates in each iteration, so lanes light on old chunks work ahead. Each
@@ -281,6 +281,8 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
             wrap = kHitQ;
           }
           const int t0 = tl;
+          // test: bit b of mk is candidate b of the chunk
+          uint32_t mk = 0u;
           if (T16) {
 #pragma unroll
             for (int pp = 0; pp < 16; ++pp) {
@@ -289,11 +291,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
               const __half2 dy2 = __hsub2(yi2, *reinterpret_cast<const __half2 *>(&v.y));
               const __half2 dz2 = __hsub2(zi2, *reinterpret_cast<const __half2 *>(&v.z));
               const __half2 r2 = __hfma2(dx2, dx2, __hfma2(dy2, dy2, __hmul2(dz2, dz2)));
-              const uint32_t hm = __hlt2_mask(r2, thr2);
-              myq[tl] = (uint8_t)(p * 32 + pp);
-              tl += (int)(hm & 1u);
-              myq[tl] = (uint8_t)(p * 32 + pp + 16);
-              tl += (int)((hm >> 16) & 1u);
+              mk |= __hlt2_mask(r2, thr2) & (0x00010001u << pp);  // one LOP3 (pp unrolled)
             }
           } else {
 #pragma unroll
@@ -301,9 +299,15 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
               const float4 q = stage[wid][p][tt];
               const float ddx = xi - q.x, ddy = yi - q.y, ddz = zi - q.z;
               const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-              myq[tl] = (uint8_t)(p * 32 + tt);
-              tl += r2 < rc2_hi ? 1 : 0;
+              mk |= r2 < rc2_hi ? (1u << tt) : 0u;
             }
+          }
+          // append the hits in candidate order (uniform trip count: the most hits of a lane)
+          const int nb = __reduce_max_sync(FULL, __popc(mk));
+          for (int kb = 0; kb < nb; ++kb) {
+            myq[tl] = (uint8_t)(p * 32 + __ffs(mk) - 1);
+            tl += mk != 0u ? 1 : 0;
+            mk &= mk - 1u;
           }
           cnt += tl - t0;
           q4 = (q4 & ~(0xffu << (8 * p))) | ((uint32_t)(tl - t0) << (8 * p));
@@ -487,8 +491,8 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   PairArgs a;
   a.grid = c.grid;
   a.pc = c.pc;
-  a.eps24 = c.lj.eps24[0]; a.eps4 = c.lj.eps4[0]; a.sig2 = c.lj.sig2[0];
-  a.eps24d = c.lj.eps24d[0]; a.eps4d = c.lj.eps4d[0]; a.sig2d = c.lj.sig2d[0];
+  a.ljA = c.lj.A[0]; a.ljB = c.lj.B[0]; a.ljA12 = c.lj.A12[0]; a.ljB6 = c.lj.B6[0];
+  a.ljAd = c.lj.Ad[0]; a.ljBd = c.lj.Bd[0]; a.ljA12d = c.lj.A12d[0]; a.ljB6d = c.lj.B6d[0];
   a.table = reinterpret_cast<const LJTable *>(c.lj_dev);
   a.F = c.F; a.Fd = c.Fd; a.Fstride = c.N;
   // full set

@@ -581,8 +581,8 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   PairArgs &pa = a.pa;
   pa.grid = c.grid;
   pa.pc = c.pc;
-  pa.eps24 = c.lj.eps24[0]; pa.eps4 = c.lj.eps4[0]; pa.sig2 = c.lj.sig2[0];
-  pa.eps24d = c.lj.eps24d[0]; pa.eps4d = c.lj.eps4d[0]; pa.sig2d = c.lj.sig2d[0];
+  pa.ljA = c.lj.A[0]; pa.ljB = c.lj.B[0]; pa.ljA12 = c.lj.A12[0]; pa.ljB6 = c.lj.B6[0];
+  pa.ljAd = c.lj.Ad[0]; pa.ljBd = c.lj.Bd[0]; pa.ljA12d = c.lj.A12d[0]; pa.ljB6d = c.lj.B6d[0];
   pa.table = reinterpret_cast<const LJTable *>(c.lj_dev);
   pa.F = c.F; pa.Fd = c.Fd; pa.Fstride = c.N; pa.accumulate = 0;
   pa.set.sx = c.s[b]; pa.set.sy = c.s[b] + c.N; pa.set.sz = c.s[b] + 2 * c.N;

@@ -13,9 +13,9 @@ struct PairArgs {
   PairSet set;
   Grid grid;
   PairConst pc;
-  // single-type LJ parameters
-  float eps24, eps4, sig2;
-  double eps24d, eps4d, sig2d;
+  // single-type LJ coefficients (as in LJTable)
+  float ljA, ljB, ljA12, ljB6;
+  double ljAd, ljBd, ljA12d, ljB6d;
   const LJTable *table;  // device copy, multi-type only
   float *F;
   double *Fd;
@@ -76,6 +76,27 @@ __device__ __forceinline__ double exact_r2(const PairConst &pc, int dsx, int dsy
   return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
 }
 
+// LJ terms of one pair from 1/r^2 (types ti, tj): force factor gl (F_i = gl (r_i - r_j)),
+// energy u = A r^-12 - B r^-6 and virial w = gl r^2 = r^-6 (12 A r^-6 - 6 B). With
+// 1/r^2 = 0 all three are exact zeros.
+template <typename real, bool MULTI>
+__device__ __forceinline__ void lj_terms(const PairArgs &a, const LJTable *tab, int ti, int tj,
+                                         real ir2, real &gl, real &u, real &w) {
+  real A, B, A12, B6;
+  if (MULTI) {
+    const int pt = ti * tab->nt + tj;
+    if (sizeof(real) == 8) { A = (real)tab->Ad[pt]; B = (real)tab->Bd[pt]; A12 = (real)tab->A12d[pt]; B6 = (real)tab->B6d[pt]; }
+    else { A = (real)tab->A[pt]; B = (real)tab->B[pt]; A12 = (real)tab->A12[pt]; B6 = (real)tab->B6[pt]; }
+  } else {
+    if (sizeof(real) == 8) { A = (real)a.ljAd; B = (real)a.ljBd; A12 = (real)a.ljA12d; B6 = (real)a.ljB6d; }
+    else { A = (real)a.ljA; B = (real)a.ljB; A12 = (real)a.ljA12; B6 = (real)a.ljB6; }
+  }
+  const real ir6 = ir2 * ir2 * ir2;
+  w = ir6 * (A12 * ir6 - B6);
+  gl = w * ir2;
+  u = ir6 * (A * ir6 - B);
+}
+
 // Pair force, energies and virial of one pair that is inside the cutoff (Eqs. F_i,
 // G_short, LJ), added to acc.
 template <typename real, bool LJ, bool COUL, bool MULTI>
@@ -85,24 +106,14 @@ __device__ __forceinline__ void pair_force_v(const PairArgs &a, const LJTable *t
   const PairConst &pc = a.pc;
   real g = (real)0;
   if (LJ) {
-    real e24, e4, s2;
-    if (MULTI) {
-      const int pt = ti * tab->nt + tj;
-      if (sizeof(real) == 8) { e24 = (real)tab->eps24d[pt]; e4 = (real)tab->eps4d[pt]; s2 = (real)tab->sig2d[pt]; }
-      else { e24 = (real)tab->eps24[pt]; e4 = (real)tab->eps4[pt]; s2 = (real)tab->sig2[pt]; }
-    } else {
-      if (sizeof(real) == 8) { e24 = (real)a.eps24d; e4 = (real)a.eps4d; s2 = (real)a.sig2d; }
-      else { e24 = (real)a.eps24; e4 = (real)a.eps4; s2 = (real)a.sig2; }
-    }
-    real rinv2;
-    if (sizeof(real) == 8) rinv2 = (real)(1.0 / (double)r2);
-    else rinv2 = (real)__fdividef(1.0f, (float)r2);  // fast reciprocal (2 ulp)
-    const real sr2 = s2 * rinv2;
-    const real sr6 = sr2 * sr2 * sr2;
-    const real gl = e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);
+    real ir2;
+    if (sizeof(real) == 8) ir2 = (real)(1.0 / (double)r2);
+    else ir2 = (real)__fdividef(1.0f, (float)r2);  // fast reciprocal (2 ulp)
+    real gl, u, w;
+    lj_terms<real, MULTI>(a, tab, ti, tj, ir2, gl, u, w);
     g += gl;
-    acc.ulj += e4 * sr6 * (sr6 - (real)1);
-    acc.wlj += gl * r2;
+    acc.ulj += u;
+    acc.wlj += w;
   }
   if (COUL) {
     const real qq = qi * qj;
@@ -190,24 +201,14 @@ __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTabl
                                                     : (real)1e38f);
   real g = (real)0;
   if (LJ) {
-    real e24, e4, s2;
-    if (MULTI) {
-      const int pt = ti * tab->nt + tj;
-      if (sizeof(real) == 8) { e24 = (real)tab->eps24d[pt]; e4 = (real)tab->eps4d[pt]; s2 = (real)tab->sig2d[pt]; }
-      else { e24 = (real)tab->eps24[pt]; e4 = (real)tab->eps4[pt]; s2 = (real)tab->sig2[pt]; }
-    } else {
-      if (sizeof(real) == 8) { e24 = (real)a.eps24d; e4 = (real)a.eps4d; s2 = (real)a.sig2d; }
-      else { e24 = (real)a.eps24; e4 = (real)a.eps4; s2 = (real)a.sig2; }
-    }
-    real rinv2;
-    if (sizeof(real) == 8) rinv2 = (real)(1.0 / (double)r2s);
-    else rinv2 = (real)__fdividef(1.0f, (float)r2s);  // fast reciprocal (2 ulp)
-    const real sr2 = s2 * rinv2;
-    const real sr6 = sr2 * sr2 * sr2;
-    const real gl = e24 * rinv2 * sr6 * (sr6 + sr6 - (real)1);
+    real ir2;
+    if (sizeof(real) == 8) ir2 = (real)(1.0 / (double)r2s);
+    else ir2 = (real)__fdividef(1.0f, (float)r2s);  // fast reciprocal (2 ulp)
+    real gl, u, w;
+    lj_terms<real, MULTI>(a, tab, ti, tj, ir2, gl, u, w);
     g += gl;
-    acc.ulj += e4 * sr6 * (sr6 - (real)1);
-    acc.wlj += gl * r2;  // (r2 is finite for every lane; gl is 0 off the pair)
+    acc.ulj += u;
+    acc.wlj += w;
   }
   if (COUL) {
     const real qq = qi * qj;

@@ -380,8 +380,11 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
         delete h;
         return RBE_ERR_INVALID;
       }
-      c.lj.eps24d[k] = 24.0 * e; c.lj.eps4d[k] = 4.0 * e; c.lj.sig2d[k] = s * s;
-      c.lj.eps24[k] = (float)(24.0 * e); c.lj.eps4[k] = (float)(4.0 * e); c.lj.sig2[k] = (float)(s * s);
+      const double s6 = (s * s) * (s * s) * (s * s), s12 = s6 * s6;
+      c.lj.Ad[k] = 4.0 * e * s12; c.lj.Bd[k] = 4.0 * e * s6;
+      c.lj.A12d[k] = 48.0 * e * s12; c.lj.B6d[k] = 24.0 * e * s6;
+      c.lj.A[k] = (float)c.lj.Ad[k]; c.lj.B[k] = (float)c.lj.Bd[k];
+      c.lj.A12[k] = (float)c.lj.A12d[k]; c.lj.B6[k] = (float)c.lj.B6d[k];
     }
 
   // sampling tables

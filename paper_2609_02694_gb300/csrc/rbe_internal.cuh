@@ -45,13 +45,14 @@ struct PairSet {        // one cell-sorted particle set seen by the pair kernels
   int64_t n;
 };
 
+// LJ pair coefficients: U = A r^-12 - B r^-6 with A = 4 eps sigma^12, B = 4 eps sigma^6;
+// the force factor g (F_i = g (r_i - r_j)) is r^-8 (12 A r^-6 - 6 B), i.e. coefficients
+// A12 = 12 A and B6 = 6 B.
 struct LJTable {
-  float eps24[kMaxTypes * kMaxTypes];   // 24 eps_ij
-  float eps4[kMaxTypes * kMaxTypes];    // 4 eps_ij
-  float sig2[kMaxTypes * kMaxTypes];    // sigma_ij^2
-  double eps24d[kMaxTypes * kMaxTypes];
-  double eps4d[kMaxTypes * kMaxTypes];
-  double sig2d[kMaxTypes * kMaxTypes];
+  float A[kMaxTypes * kMaxTypes], B[kMaxTypes * kMaxTypes];
+  float A12[kMaxTypes * kMaxTypes], B6[kMaxTypes * kMaxTypes];
+  double Ad[kMaxTypes * kMaxTypes], Bd[kMaxTypes * kMaxTypes];
+  double A12d[kMaxTypes * kMaxTypes], B6d[kMaxTypes * kMaxTypes];
   int nt;
 };
 
