@@ -182,8 +182,11 @@ def real_space(s, q, types, box, alpha, rc, C, eps, sig, i_list=None):
                 W_lj=vals[3].value, nbr=nbr)
 
 
-def cells(s, n):
-    """Linked cells: cell of each particle, cell_start (ncell+1), ids in (cell, id) order."""
+def cells(s, n, within="id"):
+    """Linked cells (Sec. 2.2, linked-cell reassignment and cell-wise reordering): cell of
+    each particle, cell_start (ncell+1), and the ids in cell order. The paper does not fix
+    the order inside a cell; within="id" orders a cell's members by id, within="x" by
+    (s_x, id), the order the library uses unless the random batch list is on."""
     s = _s(s)
     n = np.ascontiguousarray(n, np.int32)
     ncell = int(np.prod(n.astype(np.int64)))
@@ -191,6 +194,14 @@ def cells(s, n):
     cell_start = np.zeros(ncell + 1, np.int64)
     sorted_ids = np.zeros(len(s), np.int64)
     _check(lib().orc_cells(len(s), s, n, cell_of, cell_start, sorted_ids), "cells")
+    if within == "x":
+        for c in range(ncell):
+            a, b = int(cell_start[c]), int(cell_start[c + 1])
+            if b - a > 1:
+                ids = sorted_ids[a:b]
+                sorted_ids[a:b] = ids[np.lexsort((ids, s[ids, 0].astype(np.int64)))]
+    elif within != "id":
+        raise ValueError(within)
     return cell_of, cell_start, sorted_ids
 
 

@@ -2,11 +2,13 @@
 // reassignment and cell-wise reordering").
 //
 // Cell of a particle: c_d = floor(s_d n_d / 2^32) (exact on the fixed-point grid),
-// c = c_x + n_x (c_y + n_y c_z). Particles are reordered by (cell, id), which is unique, so
-// the order (and every sum taken in it) is independent of the previous order and of
-// atomic timing. The charged subset is reordered the same way into its own arrays.
+// c = c_x + n_x (c_y + n_y c_z). Particles are reordered by (cell, s_x, id), or by
+// (cell, id) when the random batch list is on (its shell order is the (cell, id) order).
+// Either key is unique, so the order (and every sum taken in it) is independent of the
+// previous order and of atomic timing; with s_x in the key every row of cells is sorted by
+// x. The charged subset is reordered the same way into its own arrays.
 // Pipeline: count (atomics give a provisional slot) -> exclusive scan of the counts ->
-// provisional scatter -> per-cell rank by id + permute of every field (one warp per cell).
+// provisional scatter -> per-cell rank by key + permute of every field (warps per cells).
 // Integer work, HBM-bound.
 // With a Verlet neighbour list the order must stay fixed between list builds: every kernel
 // of the pipeline then reads a device gate (1 = rebuild this step) and returns at once when
@@ -169,7 +171,14 @@ struct PermuteArgs {
   uint32_t *cs; float *cqf; double *cqd; int32_t *cmap;
   uint4 *s4, *cs4;        // packed (s_x, s_y, s_z, q bits) copies, nullable
   const int32_t *gate;    // nullable: always run
+  bool xkey;              // order a cell's members by (s_x, id) instead of by id
 };
+
+// Within-cell order key: the id, or (s_x, id) so that every row of cells is sorted by x
+// (the pair kernel then trims each row's run to the x-range its group can reach).
+__device__ __forceinline__ uint64_t member_key(const PermuteArgs &a, int32_t o, int32_t id) {
+  return a.xkey ? (((uint64_t)a.s0[o] << 32) | (uint32_t)id) : (uint64_t)(uint32_t)id;
+}
 
 // Move every field of the particle in provisional slot o to its final slot p (and, when
 // charged, to charged slot pc of the charged subset).
@@ -198,8 +207,8 @@ __device__ __forceinline__ void move_particle(const PermuteArgs &a, int32_t o, i
 
 constexpr int kCellsPerWarp = 4;
 
-// One warp per kCellsPerWarp consecutive cells: rank members by id (and charged members
-// among themselves), then move every field to the final slot. When no cell of the four
+// One warp per kCellsPerWarp consecutive cells: rank members by their key (and charged
+// members among themselves), then move every field to the final slot. When no cell of the four
 // holds more than 8 particles (dilute systems), each cell gets 8 lanes; otherwise the warp
 // takes the cells one after another, 32 members at a time.
 __global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
@@ -219,13 +228,14 @@ __global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
     const bool valid = k < cnt;
     const int32_t o = valid ? a.tmp[beg + k] : 0;
     const int32_t myid = valid ? a.id0[o] : INT_MAX;
+    const uint64_t mykey = valid ? member_key(a, o, myid) : ~0ull;
     const int mych = (valid && a.qf0[o] != 0.0f) ? 1 : 0;
     int rank = 0, crank = 0;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {  // 8-lane segments: lanes past the count hold INT_MAX
-      const int32_t x = __shfl_sync(FULL, myid, t, 8);
+    for (int t = 0; t < 8; ++t) {  // 8-lane segments: lanes past the count hold the maximum
+      const uint64_t x = __shfl_sync(FULL, mykey, t, 8);
       const int xc = __shfl_sync(FULL, mych, t, 8);
-      if (x < myid) { ++rank; crank += xc; }
+      if (x < mykey) { ++rank; crank += xc; }
     }
     if (valid) move_particle(a, o, beg + rank, myid, mych != 0, a.ccell_start[c] + crank);
     return;
@@ -241,18 +251,19 @@ __global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
       const bool valid = k < cnt;
       const int32_t o = valid ? a.tmp[beg + k] : 0;
       const int32_t myid = valid ? a.id0[o] : INT_MAX;
+      const uint64_t mykey = valid ? member_key(a, o, myid) : ~0ull;
       const bool mych = valid && a.qf0[o] != 0.0f;
       int rank = 0, crank = 0;
       for (int mb = 0; mb < cnt; mb += 32) {
         const int mm = mb + lane;
         const int32_t ov = mm < cnt ? a.tmp[beg + mm] : 0;
-        const int32_t oid = mm < cnt ? a.id0[ov] : INT_MAX;
+        const uint64_t okey = mm < cnt ? member_key(a, ov, a.id0[ov]) : ~0ull;
         const int och = (mm < cnt && a.qf0[ov] != 0.0f) ? 1 : 0;
         const int lim = min(32, cnt - mb);
         for (int t = 0; t < lim; ++t) {
-          const int32_t x = __shfl_sync(FULL, oid, t);
+          const uint64_t x = __shfl_sync(FULL, okey, t);
           const int xc = __shfl_sync(FULL, och, t);
-          if (x < myid) { ++rank; crank += xc; }
+          if (x < mykey) { ++rank; crank += xc; }
         }
       }
       if (valid) move_particle(a, o, beg + rank, myid, mych, cbeg + crank);
@@ -323,6 +334,7 @@ cudaError_t launch_bin_sort(Ctx &c) {
     a.s4 = c.vl_on ? c.s4 : nullptr;
     a.cs4 = c.vl_on ? c.cs4 : nullptr;
     a.gate = gate;
+    a.xkey = !c.rbl;  // the random batch list enumerates candidates in (cell, id) order
     const int64_t threads = (nc + kCellsPerWarp - 1) / kCellsPerWarp * 32;
     bin_rank_permute_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(a);
     if (gate)

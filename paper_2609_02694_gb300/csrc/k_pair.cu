@@ -42,7 +42,9 @@ constexpr int kHitQ = 160;              // hit FIFO capacity: 4 chunks pending +
 constexpr int kHitRow = kHitQ + 4;
 
 template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
-__global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a) {
+// Six blocks of four warps fit an SM's shared memory; the register bound lets six fit
+// the register file too (occupancy is worth more than registers to this issue-bound loop).
+__global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs a) {
   __shared__ float4 stage[kPairWarps][kWin][T16 ? 1 : 32];     // FP32 test coordinates
   __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
   __shared__ int4 stage_d[kPairWarps][kWin][32];               // exact integer frame coords, type
@@ -110,6 +112,18 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
       const __half2 zi2 = __float2half2_rn((HL && !in) ? far_i : zi * a.scale16);
       const __half2 thr2 = __float2half2_rn(66.5f);
       const int span = cxhi - cxlo + 2 * R0 + 1;
+      // Trimming: when every row of cells is sorted by x, a row's run is cut to the x-range
+      // that some member of the group can reach: members span [gxlo, gxhi] in x (frame
+      // units), and a row whose cells lie at y/z distance d from the group's box reaches
+      // only sqrt(r^2 - d^2) in x. (Not for the wrapping variant or a run that is a whole
+      // row, whose frame coordinates are not monotone along the run.)
+      const bool trim = !WRAP && a.xsorted && span < n0;
+      const int gxlo = __reduce_min_sync(FULL, in ? dxi : INT_MAX);
+      const int gxhi = __reduce_max_sync(FULL, in ? dxi : INT_MIN);
+      const int gylo = __reduce_min_sync(FULL, in ? dyi : INT_MAX);
+      const int gyhi = __reduce_max_sync(FULL, in ? dyi : INT_MIN);
+      const int gzlo = __reduce_min_sync(FULL, in ? dzi : INT_MAX);
+      const int gzhi = __reduce_max_sync(FULL, in ? dzi : INT_MIN);
       // 1. Runs of candidates: one lane per stencil row (dz, dy) loads the row's cell
       //    range(s) in parallel; a warp scan turns the run lengths into offsets.
       int carry = 0;
@@ -122,11 +136,12 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
           const int ry = ((gy + dy) % n1 + n1) % n1;
           const int64_t rowbase = (int64_t)n0 * (ry + (int64_t)n1 * rz);
           int sa0, sb0, sa1 = 0, sb1 = -1;
+          int64_t sh0 = 0, sh1 = 0;  // unwrapping shift of each segment (x past 0 or L)
           if (span >= n0) { sa0 = 0; sb0 = n0 - 1; }
           else {
             const int lo = cxlo - R0, hi = cxhi + R0;
-            if (lo < 0) { sa0 = lo + n0; sb0 = n0 - 1; sa1 = 0; sb1 = hi; }
-            else if (hi >= n0) { sa0 = lo; sb0 = n0 - 1; sa1 = 0; sb1 = hi - n0; }
+            if (lo < 0) { sa0 = lo + n0; sb0 = n0 - 1; sa1 = 0; sb1 = hi; sh0 = -((int64_t)1 << 32); }
+            else if (hi >= n0) { sa0 = lo; sb0 = n0 - 1; sa1 = 0; sb1 = hi - n0; sh1 = (int64_t)1 << 32; }
             else { sa0 = lo; sb0 = hi; }
           }
           b0 = a.set.cell_start[rowbase + sa0];
@@ -134,6 +149,41 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_kernel(const PairArgs a)
           if (sb1 >= sa1) {
             b1 = a.set.cell_start[rowbase + sa1];
             l1 = a.set.cell_start[rowbase + sb1 + 1] - b1;
+          }
+          if (trim) {
+            // the row's y and z extent in frame units (cells gy + dy, gz + dz unwrapped;
+            // edges rounded outward by 2 units), its distance from the group's box, and
+            // the x-reach left (radius widened by 1e-9, reach rounded up, +2 units)
+            const double wy = 4294967296.0 / n1, wz = 4294967296.0 / n2;
+            const double ylo = (gy + dy) * wy - (double)oy - 2.0, yhi = (gy + dy + 1) * wy - (double)oy + 2.0;
+            const double zlo = (gz + dz) * wz - (double)oz - 2.0, zhi = (gz + dz + 1) * wz - (double)oz + 2.0;
+            const double ddy = fmax(0.0, fmax(ylo - gyhi, gylo - yhi)) * a.pc.hd[1];
+            const double ddz = fmax(0.0, fmax(zlo - gzhi, gzlo - zhi)) * a.pc.hd[2];
+            const double rx2 = a.pc.rc2d * (1.0 + 1e-9) - ddy * ddy - ddz * ddz;
+            if (rx2 <= 0.0) {
+              l0 = l1 = 0;
+            } else {
+              const double rx = ceil(sqrt(rx2) / a.pc.hd[0]) + 2.0;
+              const int64_t xlo = (int64_t)gxlo - (int64_t)rx, xhi = (int64_t)gxhi + (int64_t)rx;
+              // first member of [b, b + l) at unwrapped x (s_x + shift - o_x, exact) >= key.
+              // Runs are sorted by s_x; the minimum-image frame coordinate is not monotone
+              // along a run (candidates beyond L/2 of the leader wrap), the unwrapped one is.
+              auto first_ge = [&](int b, int l, int64_t key, int64_t sh) {
+                int lo = 0, hi = l;
+                while (lo < hi) {
+                  const int mid = (lo + hi) >> 1;
+                  if ((int64_t)a.set.sx[b + mid] + sh - (int64_t)ox < key) lo = mid + 1;
+                  else hi = mid;
+                }
+                return lo;
+              };
+              int u0 = first_ge(b0, l0, xlo, sh0), v0 = first_ge(b0, l0, xhi + 1, sh0);
+              b0 += u0; l0 = v0 - u0;
+              if (l1 > 0) {
+                const int u1 = first_ge(b1, l1, xlo, sh1), v1 = first_ge(b1, l1, xhi + 1, sh1);
+                b1 += u1; l1 = v1 - u1;
+              }
+            }
           }
         }
         const int tot = l0 + l1;
@@ -506,6 +556,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   a.comp = c.precision == RBE_FP32_COMP;
   a.scale16 = (float)(8.0 / c.rc);
   a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax, c.rc, c.grid.R) : 0;
+  a.xsorted = !c.rbl;  // cell members ordered by x (see the binning)
   const bool wrap = a.smax == 0;
   for (int d = 0; d < 3; ++d) {
     a.L[d] = (float)c.box[d];
@@ -530,6 +581,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
       // FP32 pre-test: the dilute charged subset's groups then span more cells (the half-
       // precision test bounds a group's extent), so fewer groups walk their stencils
       b2.smax16 = 0;
+      b2.xsorted = 0;  // rows of the dilute subset are short: trimming costs more than it saves
       b2.epart = c.epart + c.off_coul;
       b2.nbr = nullptr;
       if (fp64) launch_one<double, false, true>(b2, c.Nq, false, wrap, c.stream);
@@ -558,6 +610,7 @@ cudaError_t launch_list_build(Ctx &c) {
   a.smax = frame_span_cells(c, rl);
   a.scale16 = (float)(8.0 / rl);
   a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax, rl, c.vl_R) : 0;
+  a.xsorted = !c.rbl;
   const bool wrap = a.smax == 0;
   for (int d = 0; d < 3; ++d) {
     a.L[d] = (float)c.box[d];

@@ -64,8 +64,20 @@ def test_kset_bit_exact(orc, box, P, seed, step):
 @pytest.mark.parametrize("N,L,sub", [(3000, 32.0, 0), (20000, 58.48, 2), (20000, 58.48, 1),
                                      (5000, 40.0, 3)])
 def test_cells_bit_exact(orc, N, L, sub):
+    """Cell traversal: members ordered by (cell, s_x, id)."""
     sy = synth.make_system(N, L=L, frac_charged=0.1, seed=11)
     with handle(sy, 50, cell_sub=sub) as h:
+        h.forces(0)
+        n, cs, ids = h.cells()
+    _, cso, idso = orc.cells(sy.s, n, within="x")
+    assert np.array_equal(cs, cso)
+    assert np.array_equal(ids, idso)
+
+
+def test_cells_bit_exact_rbl_order(orc):
+    """Random batch list: members ordered by (cell, id), the order its shells enumerate."""
+    sy = synth.make_system(12000, density=0.1, frac_charged=0.1, seed=11)
+    with handle(sy, 50, r_core=4.0, p_rbl=8) as h:
         h.forces(0)
         n, cs, ids = h.cells()
     _, cso, idso = orc.cells(sy.s, n)

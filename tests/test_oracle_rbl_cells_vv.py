@@ -17,6 +17,21 @@ from paper_2609_02694_gb300 import synth
 TWO32 = 2.0 ** 32
 
 
+def test_cells_x_order_is_a_within_cell_sort(orc):
+    """within="x": the same cells and cell_start, each cell's members ordered by (s_x, id),
+    checked against one global sort by (cell, s_x, id)."""
+    sy = synth.make_system(3000, density=0.1, seed=9)
+    n = np.array([6, 5, 7], np.int32)
+    c1, cs1, ids1 = orc.cells(sy.s, n)
+    c2, cs2, ids2 = orc.cells(sy.s, n, within="x")
+    assert np.array_equal(c1, c2) and np.array_equal(cs1, cs2)
+    ref = np.lexsort((np.arange(3000), sy.s[:, 0].astype(np.int64), c1.astype(np.int64)))
+    assert np.array_equal(ids2, ref)
+    for c in range(int(np.prod(n))):  # a permutation inside every cell
+        a, b = cs1[c], cs1[c + 1]
+        assert np.array_equal(np.sort(ids1[a:b]), np.sort(ids2[a:b]))
+
+
 def test_cells_contain_their_particles(orc):
     sy = synth.make_system(2000, density=0.1, seed=7)
     n = np.array([5, 6, 4], np.int32)
