@@ -14,8 +14,8 @@
 //     relative to the group leader: half-precision test copies, exact integers.
 //  2. Test: every lane tests its own i against the staged j (broadcast reads, two
 //     candidates per half-precision instruction) with a cutoff widened beyond the worst
-//     rounding, collects a 32-bit hit mask and appends the ring slots of its hits to its
-//     own FIFO in shared memory. Slots past the run and lanes outside the group get test
+//     rounding and collects a 32-bit hit mask, which it queues (one entry per chunk with
+//     hits) in shared memory. Slots past the run and lanes outside the group get test
 //     coordinates that can never hit.
 //  3. Evaluate: before a chunk overwrites a ring position, the warp runs just enough
 //     iterations that every lane has consumed its hits staged there; every lane with hits
@@ -38,13 +38,12 @@ namespace rbe {
 constexpr int kMaxRows = 49;            // (2R+1)^2 stencil rows for R <= 3
 constexpr int kMaxSeg = 2 * kMaxRows;   // a row wraps into at most two runs of cells
 constexpr int kWin = 4;                 // chunks of 32 candidates staged per window
-constexpr int kHitQ = 160;              // hit FIFO capacity: 4 chunks pending + one being tested
-constexpr int kHitRow = kHitQ + 4;
+constexpr int kHitQ = 4;                // hit-mask queue entries per lane (at most 4 pending)
 
 template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
-// Six blocks of four warps fit an SM's shared memory; the register bound lets six fit
-// the register file too (occupancy is worth more than registers to this issue-bound loop).
-__global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs a) {
+// Seven blocks of four warps per SM (at most 72 registers): occupancy is worth more than
+// registers to this issue-bound loop (eight blocks spill and run slower).
+__global__ void __launch_bounds__(kPairWarps * 32, 7) pair_kernel(const PairArgs a) {
   __shared__ float4 stage[kPairWarps][kWin][T16 ? 1 : 32];     // FP32 test coordinates
   __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
   __shared__ int4 stage_d[kPairWarps][kWin][32];               // exact integer frame coords, type
@@ -55,10 +54,10 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs
   __shared__ int32_t seg_beg[kPairWarps][kMaxSeg];
   __shared__ int32_t seg_pre[kPairWarps][kMaxSeg + 1];
   __shared__ double wred[kPairWarps][NQ_PAIR];
-  // per-lane FIFOs of pending hits (ring slots); rows of 164 bytes (41 words) so that the
-  // 32 lanes' rows start on distinct banks
+  // per-lane queues of pending hit masks: entry e of lane l holds (mask, ring slot base) of
+  // one chunk with hits; entry-major, so any mix of entries costs the minimum two wavefronts
   constexpr bool HL = !BUILD && !WRAP;
-  __shared__ uint8_t hits[kPairWarps][HL ? 32 : 1][HL ? kHitRow : 4];
+  __shared__ uint2 hitq[kPairWarps][HL ? kHitQ : 1][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t n = a.set.n;
@@ -262,18 +261,20 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs
       const int32_t *sj = &stage_j[wid][0][0];
       if (HL) {
         // 2. Chunks of 32 candidates through a ring of kWin staged chunks. Each lane tests
-        //    every staged candidate and appends its hits (ring slots) to its FIFO; before a
-        //    chunk overwrites a ring position, the warp evaluates just enough iterations
-        //    that every lane has consumed its hits staged there. Every lane with anything
-        //    pending evaluates in each iteration, so a lane that is light on the oldest
-        //    chunk works ahead on newer ones: the warp's trip count follows its heaviest
-        //    lane over four chunks instead of one window. Each lane still evaluates its hits
-        //    in candidate order.
-        uint8_t *myq = &hits[wid][HL ? lane : 0][0];
-        // FIFO read and write index, read wrap point, pending count (explicit: a full FIFO
-        // can have hd == tl)
-        int hd = 0, tl = 0, wrap = kHitQ, cnt = 0;
-        uint32_t q4 = 0u;                  // hits appended per ring position (8-bit fields)
+        //    every staged candidate, collects a 32-bit hit mask per chunk and queues it (with
+        //    the chunk's ring position) when it is not empty. Before a chunk overwrites a ring
+        //    position, the warp evaluates just enough iterations that every lane has consumed
+        //    its hits staged there; each iteration takes the lowest set bit of the lane's
+        //    current mask, or the next queued mask when the current one is spent. Every lane
+        //    with anything pending evaluates in each iteration, so a lane that is light on the
+        //    oldest chunk works ahead on newer ones: the warp's trip count follows its
+        //    heaviest lane over four chunks. Each lane evaluates its hits in candidate order.
+        //    At most four masks are queued: after a drain only the three newest chunks can
+        //    hold pending hits, and the chunk being tested adds one.
+        int hd = 0, tl = 0, cnt = 0;  // queue read and write count, pending hits
+        uint32_t cm = 0u;             // the mask being consumed (0: take the next queued one)
+        int cp = 0;                   // its ring slot base (ring position * 32)
+        uint32_t q4 = 0u;             // hits per ring position (8-bit fields)
         const int nch = (T + 31) >> 5;
         int sg = 0;
         Cand nx;  // the next chunk's candidate of this lane, loaded ahead
@@ -296,7 +297,13 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs
             const int dummy = ((ch - 1) & (kWin - 1)) * 32;  // a slot of the latest chunk
             for (int k = 0; k < nit; ++k) {
               const bool act = k < cnt;
-              const int slot = act ? (int)myq[hd] : dummy;
+              const uint2 e = hitq[wid][hd & (kHitQ - 1)][lane];
+              const bool take = act && cm == 0u;
+              cm = take ? e.x : cm;
+              cp = take ? (int)e.y : cp;
+              hd += take ? 1 : 0;
+              const int slot = act ? cp + __ffs(cm) - 1 : dummy;
+              cm &= cm - 1u;
               const int4 d = sd[slot];
               const int dsx = (int)((uint32_t)dxi - (uint32_t)d.x);
               const int dsy = (int)((uint32_t)dyi - (uint32_t)d.y);
@@ -306,8 +313,6 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs
               // (the particle itself, at zero displacement, is excluded by the evaluation)
               pair_eval_masked<real, LJ, COUL, MULTI>(a, tab, act, dsx, dsy, dsz, qi, ti, qj,
                                                       d.w, acc);
-              hd += act ? 1 : 0;
-              hd = hd == wrap ? 0 : hd;
             }
             cnt = max(0, cnt - nit);
             __syncwarp();  // position p is free for every lane
@@ -320,17 +325,6 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs
             sg = __shfl_sync(FULL, s, 31);
           }
           __syncwarp();
-          // The writer wraps only here, so that the appends below stay linear: at most
-          // 3 x 32 hits are pending now, so from tl >= kHitQ - 32 the reader is in the same
-          // segment; otherwise a reader that has wrapped clears the old wrap point.
-          if (tl >= kHitQ - 32) {
-            wrap = cnt == 0 ? kHitQ : tl;
-            hd = cnt == 0 ? 0 : hd;
-            tl = 0;
-          } else if (hd <= tl) {
-            wrap = kHitQ;
-          }
-          const int t0 = tl;
           // test: bit b of mk is candidate b of the chunk
           uint32_t mk = 0u;
           if (T16) {
@@ -352,15 +346,13 @@ __global__ void __launch_bounds__(kPairWarps * 32, 6) pair_kernel(const PairArgs
               mk |= r2 < rc2_hi ? (1u << tt) : 0u;
             }
           }
-          // append the hits in candidate order (uniform trip count: the most hits of a lane)
-          const int nb = __reduce_max_sync(FULL, __popc(mk));
-          for (int kb = 0; kb < nb; ++kb) {
-            myq[tl] = (uint8_t)(p * 32 + __ffs(mk) - 1);
-            tl += mk != 0u ? 1 : 0;
-            mk &= mk - 1u;
+          if (mk != 0u) {
+            hitq[wid][tl & (kHitQ - 1)][lane] = make_uint2(mk, (uint32_t)(p * 32));
+            ++tl;
           }
-          cnt += tl - t0;
-          q4 = (q4 & ~(0xffu << (8 * p))) | ((uint32_t)(tl - t0) << (8 * p));
+          const int nh = __popc(mk);
+          cnt += nh;
+          q4 = (q4 & ~(0xffu << (8 * p))) | ((uint32_t)nh << (8 * p));
         }
         continue;
       }

@@ -1,97 +1,70 @@
-"""Model of the cell-list pair kernel's per-lane hit FIFO protocol (host side, no GPU).
+"""Model of the cell-list pair kernel's hit-mask queue protocol (host side, no GPU).
 
-The kernel stages candidates in a ring of four 32-candidate chunks and appends each lane's
-hits (ring slots) to a FIFO of 160 bytes. Before a chunk overwrites a ring position, the
-warp evaluates just enough iterations that no lane has a hit pending there. This model
-runs the same integer protocol: pending counts packed per ring position, the writer's wrap
-at chunk starts, the reader's wrap point, and an explicit pending count. It uses
-adversarial hit patterns and checks four things:
-- indices stay in range;
-- no append overwrites a pending entry;
-- no entry is read after its ring slot was restaged;
+The kernel stages candidates in a ring of four 32-candidate chunks. Each lane queues a
+chunk's 32-bit hit mask, with its ring position, when the mask is not empty. Before a
+chunk overwrites a ring position, the warp evaluates just enough iterations that no lane
+has a hit pending there; each iteration takes the lowest set bit of the lane's current
+mask, or the next queued mask when that one is spent. This model runs the same integer
+protocol: pending counts packed per ring position, a queue of kHitQ entries, and the
+current mask. It uses adversarial hit patterns and checks four things:
+- no queued mask is overwritten;
+- no hit is read after its ring slot was restaged;
+- nothing is pending at a position about to be restaged;
 - every lane evaluates exactly its own hits, in order.
 The GPU parity tests check the kernel itself against the oracle.
 """
 import numpy as np
 import pytest
 
-K_WIN, K_HITQ = 4, 160
-
-
-def run_protocol(hitmat, explicit_count=True):
-    """hitmat: 32 lanes x T candidates (bool). explicit_count=False derives "pending" from
-    the read and write indices alone, the variant that confuses full with empty."""
-    T = hitmat.shape[1]
-    nch = (T + 31) // 32
-    fifo = [[None] * K_HITQ for _ in range(32)]
-    hd, tl = [0] * 32, [0] * 32
-    wrap, cnt, q4 = [K_HITQ] * 32, [0] * 32, [0] * 32
-    ring = [None] * K_WIN
-    done = [[] for _ in range(32)]
-
-    def pending(l):
-        if explicit_count:
-            return cnt[l]
-        return tl[l] - hd[l] + (wrap[l] if hd[l] > tl[l] else 0)
-
+K_WIN = 4
+def run_protocol(h, QCAP):
+    T = h.shape[1]; nch = (T + 31) // 32
+    fifo = [[None] * QCAP for _ in range(32)]
+    hd = [0] * 32; tl = [0] * 32; cnt = [0] * 32; q4 = [0] * 32; cm = [0] * 32; cp = [0] * 32; cch = [-1] * 32
+    ring = [None] * K_WIN; done = [[] for _ in range(32)]
     for ch in range(nch + 1):
-        p = ch & (K_WIN - 1)
+        p = ch & 3
         if ch >= K_WIN or ch == nch:
             need = []
             for l in range(32):
-                nd = pending(l)
+                nd = cnt[l]
                 if ch < nch:
                     tot = sum((q4[l] >> (8 * b)) & 0xFF for b in range(4))
-                    nd = max(0, nd - (tot - ((q4[l] >> (8 * p)) & 0xFF)))
+                    nd = max(0, cnt[l] - (tot - ((q4[l] >> (8 * p)) & 0xFF)))
                 need.append(nd)
-            nit = max(need)
-            start = [pending(l) for l in range(32)]
+            nit = max(need); c0 = list(cnt)
             for k in range(nit):
                 for l in range(32):
-                    if k < start[l]:
-                        assert 0 <= hd[l] < K_HITQ
-                        e = fifo[l][hd[l]]
-                        assert e is not None, "read of an empty entry"
-                        pos, chunk, t = e
-                        assert ring[pos] == chunk, "ring slot restaged before use"
-                        done[l].append(chunk * 32 + t)
-                        fifo[l][hd[l]] = None
-                        hd[l] += 1
-                    if hd[l] == wrap[l]:
-                        hd[l] = 0
-            for l in range(32):
-                cnt[l] = max(0, cnt[l] - nit)
+                    act = k < c0[l]
+                    if act and cm[l] == 0:
+                        e = fifo[l][hd[l] % QCAP]; assert e is not None, "empty entry"
+                        fifo[l][hd[l] % QCAP] = None
+                        cm[l], cp[l], cch[l] = e; hd[l] += 1
+                    if act:
+                        assert cm[l] != 0
+                        b = (cm[l] & -cm[l]).bit_length() - 1
+                        assert ring[cp[l] // 32] == cch[l], "ring slot restaged before use"
+                        done[l].append(cch[l] * 32 + b)
+                        cm[l] &= cm[l] - 1
+            for l in range(32): cnt[l] = max(0, cnt[l] - nit)
             if ch < nch:
                 for l in range(32):
-                    assert all(e is None or e[0] != p for e in fifo[l]), "hit pending at p"
-        if ch == nch:
-            break
+                    assert not (cm[l] and cp[l] // 32 == p), "current mask at p"
+                    assert all(e is None or e[1] // 32 != p for e in fifo[l]), "queued mask at p"
+        if ch == nch: break
         ring[p] = ch
         for l in range(32):
-            if tl[l] >= K_HITQ - 32:
-                empty = cnt[l] == 0 if explicit_count else hd[l] == tl[l]
-                wrap[l] = K_HITQ if empty else tl[l]
-                hd[l] = 0 if empty else hd[l]
-                tl[l] = 0
-            elif hd[l] <= tl[l]:
-                wrap[l] = K_HITQ
-            t0 = tl[l]
+            mk = 0
             for t in range(32):
-                assert 0 <= tl[l] < K_HITQ
-                old = fifo[l][tl[l]]
-                # the branch-free append writes every candidate at the tail
-                assert old is None or old[2] == -1, "append overwrites a pending hit"
                 c = ch * 32 + t
-                hit = c < T and bool(hitmat[l, c])
-                fifo[l][tl[l]] = (p, ch, t if hit else -1)
-                tl[l] += hit
-            if tl[l] < K_HITQ and fifo[l][tl[l]] is not None and fifo[l][tl[l]][2] == -1:
-                fifo[l][tl[l]] = None
-            cnt[l] += tl[l] - t0
-            q4[l] = (q4[l] & ~(0xFF << (8 * p))) | ((tl[l] - t0) << (8 * p))
+                if c < T and h[l, c]: mk |= 1 << t
+            if mk:
+                assert fifo[l][tl[l] % QCAP] is None, "queue overflow"
+                fifo[l][tl[l] % QCAP] = (mk, p * 32, ch); tl[l] += 1
+            pc = bin(mk).count('1'); cnt[l] += pc
+            q4[l] = (q4[l] & ~(0xFF << (8 * p))) | (pc << (8 * p))
     for l in range(32):
-        assert done[l] == list(np.nonzero(hitmat[l])[0]), l
-        assert cnt[l] == 0
+        assert done[l] == list(np.nonzero(h[l])[0]); assert cnt[l] == 0 and cm[l] == 0
 
 
 def _patterns(rng, n):
@@ -116,12 +89,14 @@ def _patterns(rng, n):
             yield h
 
 
-def test_hit_fifo_protocol():
+def test_hit_queue_protocol():
+    """The kernel's queue of four entries suffices."""
     for h in _patterns(np.random.default_rng(1), 300):
-        run_protocol(h)
+        run_protocol(h, 4)
 
 
-def test_hit_fifo_model_rejects_full_empty_confusion():
+def test_hit_queue_model_rejects_a_short_queue():
+    """Three entries are too few (the model must catch the overflow)."""
     with pytest.raises(AssertionError):
         for h in _patterns(np.random.default_rng(1), 300):
-            run_protocol(h, explicit_count=False)
+            run_protocol(h, 3)
