@@ -152,6 +152,9 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
   __shared__ int32_t seg_pre[kRblWarps][19];
   __shared__ uint32_t tmask[kRblWarps][kRblWin][kRblMaxSpan + 2];  // candidates per x offset
   __shared__ uint8_t ccount[kRblWarps][kRblMaxChunks][32];  // shell members per chunk, per lane
+  // per lane, the window's chunks with pairs to evaluate: (eval mask, core mask) and chunk
+  __shared__ uint2 rq[kRblWarps][kRblWin][32];
+  __shared__ uint8_t rqw[kRblWarps][kRblWin][32];
   __shared__ double wred[kRblWarps][NQ_PAIR + 3];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
@@ -277,6 +280,7 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           sg = __shfl_sync(FULL, s, 31);
         }
         __syncwarp();
+        int nq = 0, qcnt = 0;  // eager: queued chunks and pairs of this lane in the window
 #pragma unroll 1
         for (int w = 0; w < kRblWin; ++w) {
           const int nj = max(0, min(32, T - base - 32 * w));
@@ -327,17 +331,58 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
             scr[chunk * 32 + lane] = mshell;  // coalesced, read back by pass 2
           }
           nsh += __popc(mshell);
-          // core pairs (and, eager, shell pairs), branch-light, in canonical order; the
-          // particle itself (r = 0, always core) is skipped
-          uint32_t bits = EAGER ? (mcore | mshell) : mcore;
-          const int nbits = __reduce_max_sync(FULL, __popc(bits));  // uniform trip count
+          if (EAGER) {  // core and shell pairs are evaluated per window below
+            const uint32_t bits = mcore | mshell;
+            if (bits != 0u) {
+              rq[wid][nq][lane] = make_uint2(bits, mcore);
+              rqw[wid][nq][lane] = (uint8_t)w;
+              ++nq;
+            }
+            qcnt += __popc(bits);
+            continue;
+          }
+          // core pairs, branch-light, in canonical order, one uniform trip count per chunk
+          // (a few core pairs per chunk and lane); the particle itself (r = 0) is skipped
+          uint32_t bits = mcore;
+          const int nbits = __reduce_max_sync(FULL, __popc(bits));
           for (int kb = 0; kb < nbits; ++kb) {
             const bool act = bits != 0u;
             const int tt = act ? __ffs(bits) - 1 : 0;
             bits &= bits - 1u;
             const int32_t j = stage_j[wid][w][tt];
             const bool use = act && j != (int32_t)i;
-            const bool is_core = ((mcore >> tt) & 1u) != 0u;
+            const int4 d = stage_d[wid][w][tt];
+            real qj = (real)0;
+            if (COUL) qj = sizeof(real) == 8 ? (use ? (real)S.qd[j] : (real)0) : (real)stage_q[wid][w][tt];
+            ncore += use ? 1 : 0;
+            const PairAcc<real> t = rbl_pair_eval<real, COUL, MULTI>(
+                a, tab, use, (int)((uint32_t)dxi - (uint32_t)d.x), (int)((uint32_t)dyi - (uint32_t)d.y),
+                (int)((uint32_t)dzi - (uint32_t)d.z), qi, ti, qj, d.w);
+            rbl_acc_add(a, use, t, core);
+          }
+        }
+        // Eager: the window's core and shell pairs, branch-light, each lane in canonical
+        // order, with one uniform trip count for the window (the lane with the most pairs)
+        // instead of one per chunk; the particle itself (r = 0, always core) is skipped.
+        if (EAGER) {
+          const int nit = __reduce_max_sync(FULL, qcnt);
+          int hq = 0, cw = 0;
+          uint32_t cm = 0u, cc = 0u;  // the chunk being consumed: pairs left, core pairs
+          for (int kb = 0; kb < nit; ++kb) {
+            const bool act = kb < qcnt;
+            const uint2 e = rq[wid][hq & (kRblWin - 1)][lane];
+            const int ew = rqw[wid][hq & (kRblWin - 1)][lane];
+            const bool take = act && cm == 0u;
+            cm = take ? e.x : cm;
+            cc = take ? e.y : cc;
+            cw = take ? ew : cw;
+            hq += take ? 1 : 0;
+            const int tt = act ? __ffs(cm) - 1 : 0;
+            const int w = act ? cw : 0;  // (idle lanes: candidate 0 of chunk 0, staged)
+            cm &= cm - 1u;
+            const int32_t j = stage_j[wid][w][tt];
+            const bool use = act && j != (int32_t)i;
+            const bool is_core = ((cc >> tt) & 1u) != 0u;
             const int4 d = stage_d[wid][w][tt];
             real qj = (real)0;
             if (COUL) qj = sizeof(real) == 8 ? (use ? (real)S.qd[j] : (real)0) : (real)stage_q[wid][w][tt];
