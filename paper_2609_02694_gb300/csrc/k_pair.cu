@@ -264,11 +264,12 @@ __global__ void __launch_bounds__(kPairWarps * 32, 7) pair_kernel(const PairArgs
         //    every staged candidate, collects a 32-bit hit mask per chunk and queues it (with
         //    the chunk's ring position) when it is not empty. Before a chunk overwrites a ring
         //    position, the warp evaluates just enough iterations that every lane has consumed
-        //    its hits staged there; each iteration takes the lowest set bit of the lane's
+        //    its hits staged there; each iteration takes the highest set bit of the lane's
         //    current mask, or the next queued mask when the current one is spent. Every lane
         //    with anything pending evaluates in each iteration, so a lane that is light on the
         //    oldest chunk works ahead on newer ones: the warp's trip count follows its
-        //    heaviest lane over four chunks. Each lane evaluates its hits in candidate order.
+        //    heaviest lane over four chunks. Each lane evaluates its hits in a fixed order
+        //    (chunks in order, within a chunk the highest candidate first).
         //    At most four masks are queued: after a drain only the three newest chunks can
         //    hold pending hits, and the chunk being tested adds one.
         int hd = 0, tl = 0, cnt = 0;  // queue read and write count, pending hits
@@ -302,8 +303,9 @@ __global__ void __launch_bounds__(kPairWarps * 32, 7) pair_kernel(const PairArgs
               cm = take ? e.x : cm;
               cp = take ? (int)e.y : cp;
               hd += take ? 1 : 0;
-              const int slot = act ? cp + __ffs(cm) - 1 : dummy;
-              cm &= cm - 1u;
+              const int hb = 31 - __clz(cm);  // highest pending candidate first (one FLO)
+              const int slot = act ? cp + hb : dummy;
+              cm &= ~(1u << (hb & 31));
               const int4 d = sd[slot];
               const int dsx = (int)((uint32_t)dxi - (uint32_t)d.x);
               const int dsy = (int)((uint32_t)dyi - (uint32_t)d.y);

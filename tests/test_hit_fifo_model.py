@@ -3,14 +3,14 @@
 The kernel stages candidates in a ring of four 32-candidate chunks. Each lane queues a
 chunk's 32-bit hit mask, with its ring position, when the mask is not empty. Before a
 chunk overwrites a ring position, the warp evaluates just enough iterations that no lane
-has a hit pending there; each iteration takes the lowest set bit of the lane's current
+has a hit pending there; each iteration takes the highest set bit of the lane's current
 mask, or the next queued mask when that one is spent. This model runs the same integer
 protocol: pending counts packed per ring position, a queue of kHitQ entries, and the
 current mask. It uses adversarial hit patterns and checks four things:
 - no queued mask is overwritten;
 - no hit is read after its ring slot was restaged;
 - nothing is pending at a position about to be restaged;
-- every lane evaluates exactly its own hits, in order.
+- every lane evaluates exactly its own hits, chunk by chunk, the highest candidate first.
 The GPU parity tests check the kernel itself against the oracle.
 """
 import numpy as np
@@ -42,10 +42,10 @@ def run_protocol(h, QCAP):
                         cm[l], cp[l], cch[l] = e; hd[l] += 1
                     if act:
                         assert cm[l] != 0
-                        b = (cm[l] & -cm[l]).bit_length() - 1
+                        b = cm[l].bit_length() - 1
                         assert ring[cp[l] // 32] == cch[l], "ring slot restaged before use"
                         done[l].append(cch[l] * 32 + b)
-                        cm[l] &= cm[l] - 1
+                        cm[l] &= ~(1 << b)
             for l in range(32): cnt[l] = max(0, cnt[l] - nit)
             if ch < nch:
                 for l in range(32):
@@ -64,7 +64,8 @@ def run_protocol(h, QCAP):
             pc = bin(mk).count('1'); cnt[l] += pc
             q4[l] = (q4[l] & ~(0xFF << (8 * p))) | (pc << (8 * p))
     for l in range(32):
-        assert done[l] == list(np.nonzero(h[l])[0]); assert cnt[l] == 0 and cm[l] == 0
+        want = [j for c0 in range(0, T, 32) for j in sorted(np.nonzero(h[l, c0:c0 + 32])[0] + c0, reverse=True)]
+        assert done[l] == want; assert cnt[l] == 0 and cm[l] == 0
 
 
 def _patterns(rng, n):
