@@ -186,7 +186,7 @@ def cells(s, n, within="id"):
     """Linked cells (Sec. 2.2, linked-cell reassignment and cell-wise reordering): cell of
     each particle, cell_start (ncell+1), and the ids in cell order. The paper does not fix
     the order inside a cell; within="id" orders a cell's members by id, within="x" by
-    (s_x, id), the order the library uses unless the random batch list is on."""
+    (s_x, id), the order the library and the random batch list use."""
     s = _s(s)
     n = np.ascontiguousarray(n, np.int32)
     ncell = int(np.prod(n.astype(np.int64)))
@@ -206,7 +206,9 @@ def cells(s, n, within="id"):
 
 
 def rbl(s, q, types, box, alpha, r_core, r_s, p, seed, step, replica, C, eps, sig):
-    """Random batch list short-range force with the mean-force correction (Eqs. RBL, F_corr)."""
+    """Random batch list short-range force with the mean-force correction (Eqs. RBL, F_corr).
+    Shells are enumerated over the 27 neighbour cells in (dz, dy, dx) order and inside a cell
+    in ascending (s_x, id) order, the order the draws index."""
     s = _s(s)
     N = len(s)
     eps, sig, nt = lj_tables(eps, sig)

@@ -380,6 +380,19 @@ int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
   int64_t *cell_start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncell + 1));
   int64_t *sorted_ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
   orc_cells(N, s, n, cell_of, cell_start, sorted_ids);
+  /* canonical order inside a cell: ascending (s_x, id) (the paper leaves it open) */
+  for (int64_t cc = 0; cc < ncell; ++cc)
+    for (int64_t k = cell_start[cc] + 1; k < cell_start[cc + 1]; ++k) {
+      const int64_t v = sorted_ids[k];
+      int64_t u = k - 1;
+      while (u >= cell_start[cc] &&
+             (s[3 * sorted_ids[u]] > s[3 * v] ||
+              (s[3 * sorted_ids[u]] == s[3 * v] && sorted_ids[u] > v))) {
+        sorted_ids[u + 1] = sorted_ids[u];
+        --u;
+      }
+      sorted_ids[u + 1] = v;
+    }
   double rcore2 = r_core * r_core, rs2 = r_s * r_s;
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ replica};
   double *Ft = (double *)malloc(sizeof(double) * 3 * (size_t)N);

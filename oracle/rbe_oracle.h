@@ -105,7 +105,7 @@ int orc_cells(int64_t N, const uint32_t *s, const int32_t n[3], int32_t *cell_of
 /* Random batch list (Eqs. Ci_Si, RBL, F_corr) on the r_s grid (n_d = floor(L_d / r_s)
  * cells, at least 3 per axis). For particle i the candidates are enumerated over the 27
  * neighbour cells in (dz, dy, dx) order, each from -1 to 1, and inside a cell in
- * (cell, id) order; j != i with r <= r_core is core, r_core < r <= r_s is shell. With
+ * ascending (s_x, id) order; j != i with r <= r_core is core, r_core < r <= r_s is shell. With
  * n_s = #shell: if n_s <= p all shell partners enter with weight 1; otherwise p draws
  * idx = floor(w * n_s / 2^32), w = word (t mod 4) of Philox(counter = (id_i, t / 4,
  * step_lo32, 1), key = (seed_lo32, seed_hi32 ^ replica)), t = 0..p-1, each entering with

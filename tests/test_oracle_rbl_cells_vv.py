@@ -89,7 +89,7 @@ def test_rbl_draws_match_brute_force_enumeration(orc):
     rb = orc.rbl(sy.s, sy.q, sy.types, sy.box, 0.09, r_core, r_s, p, seed, step, 0,
                  synth.COULOMB_C, sy.eps, sy.sig)
     n = np.floor(sy.box / r_s).astype(np.int32)
-    cell_of, cell_start, ids = orc.cells(sy.s, n)
+    cell_of, cell_start, ids = orc.cells(sy.s, n, within="x")  # the RBL's canonical order
     for i in (0, 13, 700, 1499):
         ci = cell_of[i]
         c3 = (ci % n[0], (ci // n[0]) % n[1], ci // (n[0] * n[1]))
