@@ -156,8 +156,8 @@ int rbe_get_step(rbe_handle h, uint64_t *step);
 int rbe_get_state(rbe_handle h, double *pos, double *vel, uint32_t *s_frac);
 
 /* Copy the linked cells of the last force evaluation: n_cells[3] cells per axis,
- * cell_start (n_x n_y n_z + 1 entries) and sorted_ids (N ids in (cell, id) order). Either
- * array may be NULL (query n_cells first to size cell_start). */
+ * cell_start (n_x n_y n_z + 1 entries) and sorted_ids (N ids in cell order, inside a cell
+ * by (s_x, id)). Either array may be NULL (query n_cells first to size cell_start). */
 int rbe_get_cells(rbe_handle h, int32_t n_cells[3], int64_t *cell_start, int64_t *sorted_ids);
 
 /* Copy the structure factor of the last evaluation, rho (P x 2: Re, Im, FP64), and the modes. */

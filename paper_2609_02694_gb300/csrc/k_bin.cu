@@ -2,11 +2,10 @@
 // reassignment and cell-wise reordering").
 //
 // Cell of a particle: c_d = floor(s_d n_d / 2^32) (exact on the fixed-point grid),
-// c = c_x + n_x (c_y + n_y c_z). Particles are reordered by (cell, s_x, id), or by
-// (cell, id) when the random batch list is on (its shell order is the (cell, id) order).
-// Either key is unique, so the order (and every sum taken in it) is independent of the
-// previous order and of atomic timing; with s_x in the key every row of cells is sorted by
-// x. The charged subset is reordered the same way into its own arrays.
+// c = c_x + n_x (c_y + n_y c_z). Particles are reordered by (cell, s_x, id), which is
+// unique, so the order (and every sum taken in it) is independent of the previous order and
+// of atomic timing, and every row of cells is sorted by x. The charged subset is reordered
+// the same way into its own arrays.
 // Pipeline: count (atomics give a provisional slot) -> exclusive scan of the counts ->
 // provisional scatter -> per-cell rank by key + permute of every field (warps per cells).
 // Integer work, HBM-bound.
@@ -171,13 +170,12 @@ struct PermuteArgs {
   uint32_t *cs; float *cqf; double *cqd; int32_t *cmap;
   uint4 *s4, *cs4;        // packed (s_x, s_y, s_z, q bits) copies, nullable
   const int32_t *gate;    // nullable: always run
-  bool xkey;              // order a cell's members by (s_x, id) instead of by id
 };
 
-// Within-cell order key: the id, or (s_x, id) so that every row of cells is sorted by x
-// (the pair kernel then trims each row's run to the x-range its group can reach).
+// Within-cell order key (s_x, id): every row of cells is then sorted by x, and the pair and
+// RBL kernels trim each row's run to the x-range their group can reach.
 __device__ __forceinline__ uint64_t member_key(const PermuteArgs &a, int32_t o, int32_t id) {
-  return a.xkey ? (((uint64_t)a.s0[o] << 32) | (uint32_t)id) : (uint64_t)(uint32_t)id;
+  return ((uint64_t)a.s0[o] << 32) | (uint32_t)id;
 }
 
 // Move every field of the particle in provisional slot o to its final slot p (and, when
@@ -334,7 +332,6 @@ cudaError_t launch_bin_sort(Ctx &c) {
     a.s4 = c.vl_on ? c.s4 : nullptr;
     a.cs4 = c.vl_on ? c.cs4 : nullptr;
     a.gate = gate;
-    a.xkey = !c.rbl;  // the random batch list enumerates candidates in (cell, id) order
     const int64_t threads = (nc + kCellsPerWarp - 1) / kCellsPerWarp * 32;
     bin_rank_permute_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(a);
     if (gate)

@@ -40,9 +40,9 @@ constexpr int kMaxSeg = 2 * kMaxRows;   // a row wraps into at most two runs of 
 constexpr int kWin = 4;                 // chunks of 32 candidates staged per window
 constexpr int kHitQ = 4;                // hit-mask queue entries per lane (at most 4 pending)
 
-template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
 // Seven blocks of four warps per SM (at most 72 registers): occupancy is worth more than
 // registers to this issue-bound loop (eight blocks spill and run slower).
+template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
 __global__ void __launch_bounds__(kPairWarps * 32, 7) pair_kernel(const PairArgs a) {
   __shared__ float4 stage[kPairWarps][kWin][T16 ? 1 : 32];     // FP32 test coordinates
   __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
@@ -111,12 +111,12 @@ __global__ void __launch_bounds__(kPairWarps * 32, 7) pair_kernel(const PairArgs
       const __half2 zi2 = __float2half2_rn((HL && !in) ? far_i : zi * a.scale16);
       const __half2 thr2 = __float2half2_rn(66.5f);
       const int span = cxhi - cxlo + 2 * R0 + 1;
-      // Trimming: when every row of cells is sorted by x, a row's run is cut to the x-range
+      // Trimming: every row of cells is sorted by x, so a row's run is cut to the x-range
       // that some member of the group can reach: members span [gxlo, gxhi] in x (frame
       // units), and a row whose cells lie at y/z distance d from the group's box reaches
       // only sqrt(r^2 - d^2) in x. (Not for the wrapping variant or a run that is a whole
       // row, whose frame coordinates are not monotone along the run.)
-      const bool trim = !WRAP && a.xsorted && span < n0;
+      const bool trim = !WRAP && a.trim && span < n0;
       const int gxlo = __reduce_min_sync(FULL, in ? dxi : INT_MAX);
       const int gxhi = __reduce_max_sync(FULL, in ? dxi : INT_MIN);
       const int gylo = __reduce_min_sync(FULL, in ? dyi : INT_MAX);
@@ -550,7 +550,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   a.comp = c.precision == RBE_FP32_COMP;
   a.scale16 = (float)(8.0 / c.rc);
   a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax, c.rc, c.grid.R) : 0;
-  a.xsorted = !c.rbl;  // cell members ordered by x (see the binning)
+  a.trim = 1;
   const bool wrap = a.smax == 0;
   for (int d = 0; d < 3; ++d) {
     a.L[d] = (float)c.box[d];
@@ -575,7 +575,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
       // FP32 pre-test: the dilute charged subset's groups then span more cells (the half-
       // precision test bounds a group's extent), so fewer groups walk their stencils
       b2.smax16 = 0;
-      b2.xsorted = 0;  // rows of the dilute subset are short: trimming costs more than it saves
+      b2.trim = 0;  // rows of the dilute subset are short: trimming costs more than it saves
       b2.epart = c.epart + c.off_coul;
       b2.nbr = nullptr;
       if (fp64) launch_one<double, false, true>(b2, c.Nq, false, wrap, c.stream);
@@ -604,7 +604,7 @@ cudaError_t launch_list_build(Ctx &c) {
   a.smax = frame_span_cells(c, rl);
   a.scale16 = (float)(8.0 / rl);
   a.smax16 = c.pair_test16 ? frame_span_cells_half(c, a.smax, rl, c.vl_R) : 0;
-  a.xsorted = !c.rbl;
+  a.trim = 1;
   const bool wrap = a.smax == 0;
   for (int d = 0; d < 3; ++d) {
     a.L[d] = (float)c.box[d];

@@ -6,7 +6,7 @@
 //   F_i  = F~_i - (1/N) sum_j F~_j
 // (The paper's core cutoff r_c is `r_core` here and its r_s is the real-space cutoff.)
 // S_i is enumerated in a canonical order shared with the oracle: the 27 neighbour cells
-// in (dz, dy, dx) order, each offset from -1 to 1, and inside each cell the (cell, id)
+// in (dz, dy, dx) order, each offset from -1 to 1, and inside each cell the (s_x, id)
 // order of the binning. Draw t takes idx = floor(w * #S_i / 2^32), where w is word
 // (t mod 4) of Philox4x32-10 with counter (id_i, t / 4, step, 1). When #S_i <= p the whole
 // shell enters with weight 1.
@@ -211,8 +211,19 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
       const float xi = __fmul_rn((float)dxi, a.pa.pc.h[0]);
       const float yi = __fmul_rn((float)dyi, a.pa.pc.h[1]);
       const float zi = __fmul_rn((float)dzi, a.pa.pc.h[2]);
-      // the 9 rows (dz, dy) in canonical order, each the x cells gx - 1 .. gx + gs (mod n_x)
-      // as at most two contiguous runs; one lane per run
+      // The 9 rows (dz, dy) in canonical order, each the x cells gx - 1 .. gx + gs (mod n_x)
+      // as at most two contiguous runs; one lane per run. Every row of cells is sorted by x,
+      // so each run is cut to the x-range some member can reach: members span [gxlo, gxhi]
+      // in x, and a row whose cells lie at y/z distance d from the group's box reaches only
+      // sqrt(r_s^2 - d^2) in x. The cut searches exact unwrapped coordinates (s_x plus the
+      // run's wrap shift), which are monotone along a run; trimmed candidates are beyond r_s
+      // of every member, so the canonical shell order of each lane is unchanged.
+      const int gxlo = __reduce_min_sync(FULL, in ? dxi : INT_MAX);
+      const int gxhi = __reduce_max_sync(FULL, in ? dxi : INT_MIN);
+      const int gylo = __reduce_min_sync(FULL, in ? dyi : INT_MAX);
+      const int gyhi = __reduce_max_sync(FULL, in ? dyi : INT_MIN);
+      const int gzlo = __reduce_min_sync(FULL, in ? dzi : INT_MAX);
+      const int gzhi = __reduce_max_sync(FULL, in ? dzi : INT_MIN);
       {
         int b0 = 0, l0 = 0;
         if (lane < 18) {
@@ -228,6 +239,37 @@ __global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
           if (c1 >= c0) {
             b0 = S.cell_start[rowbase + c0];
             l0 = S.cell_start[rowbase + c1 + 1] - b0;
+          }
+          if (!WRAP && l0 > 0) {
+            // row extent in frame units (cells gy + dy, gz + dz unwrapped, edges rounded
+            // outward by 2 units), distance from the group's box, x-reach (radius widened by
+            // 1e-9, rounded up, +2 units)
+            const double wy = 4294967296.0 / n1, wz = 4294967296.0 / n2;
+            const double ylo = (gy + dy) * wy - (double)oy - 2.0, yhi = (gy + dy + 1) * wy - (double)oy + 2.0;
+            const double zlo = (gz + dz) * wz - (double)oz - 2.0, zhi = (gz + dz + 1) * wz - (double)oz + 2.0;
+            const double ddy = fmax(0.0, fmax(ylo - gyhi, gylo - yhi)) * a.pa.pc.hd[1];
+            const double ddz = fmax(0.0, fmax(zlo - gzhi, gzlo - zhi)) * a.pa.pc.hd[2];
+            const double rx2 = a.pa.pc.rc2d * (1.0 + 1e-9) - ddy * ddy - ddz * ddz;
+            if (rx2 <= 0.0) {
+              l0 = 0;
+            } else {
+              const int64_t rx = (int64_t)(ceil(sqrt(rx2) / a.pa.pc.hd[0]) + 2.0);
+              // the part left of x = 0 (cell n_x - 1 standing for -1) or right of x = L
+              const int64_t sh = (xlo < 0 && !part) ? -((int64_t)1 << 32)
+                                 : (xhi >= n0 && part) ? ((int64_t)1 << 32) : 0;
+              auto first_ge = [&](int64_t key) {
+                int lo_ = 0, hi_ = l0;
+                while (lo_ < hi_) {
+                  const int mid = (lo_ + hi_) >> 1;
+                  if ((int64_t)S.sx[b0 + mid] + sh - (int64_t)ox < key) lo_ = mid + 1;
+                  else hi_ = mid;
+                }
+                return lo_;
+              };
+              const int u = first_ge((int64_t)gxlo - rx), v = first_ge((int64_t)gxhi + rx + 1);
+              b0 += u;
+              l0 = v - u;
+            }
           }
         }
         int incl = l0;

@@ -28,7 +28,7 @@ struct PairArgs {
   // A group spans at most `smax` cells in x (one cell in y and z); boxes too small for
   // even one cell use the wrapping variant, which folds every difference into [-L/2, L/2).
   int smax;
-  int xsorted;        // every row of cells is sorted by x (enables run trimming)
+  int trim;           // cut each row's run to the group's x-reach (rows are sorted by x)
   float L[3], invL[3];
   int comp;  // compensated (Kahan) Coulomb energy and virial sums
   // Packed half-precision candidate test: frame coordinates scaled by scale16 = 8 / r_c

@@ -74,13 +74,14 @@ def test_cells_bit_exact(orc, N, L, sub):
     assert np.array_equal(ids, idso)
 
 
-def test_cells_bit_exact_rbl_order(orc):
-    """Random batch list: members ordered by (cell, id), the order its shells enumerate."""
+def test_cells_bit_exact_rbl_grid(orc):
+    """Random batch list (cells of r_s): members ordered by (cell, s_x, id) as well, the
+    order its shells enumerate."""
     sy = synth.make_system(12000, density=0.1, frac_charged=0.1, seed=11)
     with handle(sy, 50, r_core=4.0, p_rbl=8) as h:
         h.forces(0)
         n, cs, ids = h.cells()
-    _, cso, idso = orc.cells(sy.s, n)
+    _, cso, idso = orc.cells(sy.s, n, within="x")
     assert np.array_equal(cs, cso)
     assert np.array_equal(ids, idso)
 
