@@ -136,30 +136,41 @@ struct TotalsArgs {
 };
 
 // Fixed-order reduction of every partial into the scalars (ACC = float for the plain
-// FP32 form, double otherwise).
+// FP32 form, double otherwise). One block of kTotalsThreads: strided per-thread sums (four
+// partials in flight per thread), then warp shuffles, then the warp sums in order.
+constexpr int kTotalsThreads = 1024;
+
 template <typename ACC>
-__global__ void __launch_bounds__(256) totals_kernel(TotalsArgs a) {
+__global__ void __launch_bounds__(kTotalsThreads) totals_kernel(TotalsArgs a) {
   constexpr int NV = 7;  // ureal ulj wreal wlj uk wk ke
-  __shared__ ACC sh[NV][256];
+  constexpr int NW = kTotalsThreads / 32;
+  __shared__ ACC sh[NV][NW];
   ACC acc[NV];
   for (int k = 0; k < NV; ++k) acc[k] = (ACC)0;
   const double *srcs[3] = {a.pair, a.coul, a.rbl};
   const int64_t ns[3] = {a.n_pair, a.n_coul, a.n_rbl};
-  for (int r = 0; r < 3; ++r)
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll 4
     for (int64_t b = threadIdx.x; b < ns[r]; b += blockDim.x)
       for (int k = 0; k < NQ_PAIR; ++k) acc[k] += (ACC)srcs[r][b * NQ_PAIR + k];
+  }
   for (int l = threadIdx.x; l < a.P; l += blockDim.x) {
     acc[4] += (ACC)a.emode[2 * l];
     acc[5] += (ACC)a.emode[2 * l + 1];
   }
   for (int64_t b = threadIdx.x; b < a.n_ke; b += blockDim.x) acc[6] += (ACC)a.ke[b];
-  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = acc[k];
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if (threadIdx.x < st)
-      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
-    __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < NV; ++k) {
+    const ACC v = warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = v;
   }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    ACC t = (ACC)0;
+    for (int w = 0; w < NW; ++w) t += sh[threadIdx.x][w];
+    sh[threadIdx.x][0] = t;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const double ur = (double)sh[Q_UREAL][0], ul = (double)sh[Q_ULJ][0];
     const double wr = (double)sh[Q_WREAL][0], wl = (double)sh[Q_WLJ][0];
@@ -282,10 +293,47 @@ static cudaError_t kick_impl(Ctx &c, int do_kick) {
 cudaError_t launch_kick(Ctx &c) { return kick_impl(c, 1); }
 cudaError_t launch_kinetic(Ctx &c) { return kick_impl(c, 0); }
 
+// Block partials of a pair pass ([nblk][NQ_PAIR]) summed over fixed contiguous ranges in a
+// fixed order into [gridDim.x][NQ_PAIR]: the FP64 adds are spread over many SMs (one SM's
+// FP64 rate is low) before the one-block totals.
+__global__ void __launch_bounds__(256) partials_compact_kernel(const double *__restrict__ in,
+                                                               int64_t nblk, int64_t per,
+                                                               double *__restrict__ out) {
+  __shared__ double sh[NQ_PAIR][256];
+  const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(nblk, b0 + per);
+  double acc[NQ_PAIR];
+#pragma unroll
+  for (int k = 0; k < NQ_PAIR; ++k) acc[k] = 0.0;
+  for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NQ_PAIR; ++k) acc[k] += in[b * NQ_PAIR + k];
+#pragma unroll
+  for (int k = 0; k < NQ_PAIR; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+#pragma unroll
+      for (int k = 0; k < NQ_PAIR; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < NQ_PAIR) out[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+int64_t partials_compact_count(int64_t nblk) { return std::min<int64_t>(nblk, kCompactMax); }
+
 cudaError_t launch_totals(Ctx &c) {
   TotalsArgs a;
-  a.pair = c.epart + c.off_pair; a.n_pair = c.n_pair_blk;
-  a.coul = c.epart + c.off_coul; a.n_coul = c.n_coul_blk;
+  // pair and Coulomb-pass partials, compacted first (at most kCompactMax per pass)
+  const int64_t ncp = partials_compact_count(c.n_pair_blk), ncc = partials_compact_count(c.n_coul_blk);
+  if (ncp > 0)
+    partials_compact_kernel<<<(unsigned)ncp, 256, 0, c.stream>>>(
+        c.epart + c.off_pair, c.n_pair_blk, (c.n_pair_blk + ncp - 1) / ncp, c.ecomp);
+  if (ncc > 0)
+    partials_compact_kernel<<<(unsigned)ncc, 256, 0, c.stream>>>(
+        c.epart + c.off_coul, c.n_coul_blk, (c.n_coul_blk + ncc - 1) / ncc,
+        c.ecomp + kCompactMax * NQ_PAIR);
+  a.pair = c.ecomp; a.n_pair = ncp;
+  a.coul = c.ecomp + kCompactMax * NQ_PAIR; a.n_coul = ncc;
   // RBL partials: the compacted ones (rbl_compact_kernel runs after the RBL kernel)
   a.rbl = c.rbl ? c.rbl_cpart : c.epart + c.off_rbl;
   a.n_rbl = c.rbl ? rbl_compact_count(c.n_rbl_blk) : 0;
@@ -294,8 +342,8 @@ cudaError_t launch_totals(Ctx &c) {
   a.U_self = c.U_self;
   a.scal = c.scal;
   a.ke_override = c.nvt ? c.thermo + 3 : nullptr;
-  if (c.precision == RBE_FP32) totals_kernel<float><<<1, 256, 0, c.stream>>>(a);
-  else totals_kernel<double><<<1, 256, 0, c.stream>>>(a);
+  if (c.precision == RBE_FP32) totals_kernel<float><<<1, kTotalsThreads, 0, c.stream>>>(a);
+  else totals_kernel<double><<<1, kTotalsThreads, 0, c.stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -40,10 +40,11 @@ constexpr int kMaxSeg = 2 * kMaxRows;   // a row wraps into at most two runs of 
 constexpr int kWin = 4;                 // chunks of 32 candidates staged per window
 constexpr int kHitQ = 4;                // hit-mask queue entries per lane (at most 4 pending)
 
-// Seven blocks of four warps per SM (at most 72 registers): occupancy is worth more than
-// registers to this issue-bound loop (eight blocks spill and run slower).
+// 28 warps per SM (at most 72 registers): occupancy is worth more than registers to this
+// issue-bound loop (32 warps spill and run slower). One-warp blocks: a warp that finishes
+// early frees its slot instead of waiting at a block barrier for the slowest warp.
 template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
-__global__ void __launch_bounds__(kPairWarps * 32, 7) pair_kernel(const PairArgs a) {
+__global__ void __launch_bounds__(kPairWarps * 32, 28 / kPairWarps) pair_kernel(const PairArgs a) {
   __shared__ float4 stage[kPairWarps][kWin][T16 ? 1 : 32];     // FP32 test coordinates
   __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
   __shared__ int4 stage_d[kPairWarps][kWin][32];               // exact integer frame coords, type

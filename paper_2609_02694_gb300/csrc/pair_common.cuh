@@ -7,7 +7,7 @@
 
 namespace rbe {
 
-constexpr int kPairWarps = 4;
+constexpr int kPairWarps = 1;  // one-warp blocks: a finished warp frees its slot at once
 
 struct PairArgs {
   PairSet set;

@@ -124,7 +124,7 @@ int free_all(Ctx &c) {
   for (int d = 0; d < 3; ++d) dfree(c.T[d]);
   dfree(c.m); dfree(c.kcf); dfree(c.kcd); dfree(c.sf_part); dfree(c.rho); dfree(c.abf);
   dfree(c.abd); dfree(c.emode); dfree(c.epart); dfree(c.scal); dfree(c.step_dev);
-  dfree(c.err); dfree(c.nbr); dfree(c.nshell); dfree(c.partners); dfree(c.rbl_mean);
+  dfree(c.err); dfree(c.nbr); dfree(c.ecomp); dfree(c.nshell); dfree(c.partners); dfree(c.rbl_mean);
   dfree(c.rbl_part); dfree(c.rbl_masks); dfree(c.rbl_slots); dfree(c.rbl_cpart); dfree(c.outf); dfree(c.outd); dfree(c.pos_stage); dfree(c.lj_dev);
   dfree(c.thermo);
   dfree(c.vl_list); dfree(c.vl_len); dfree(c.vl_listq); dfree(c.vl_lenq); dfree(c.vl_ref);
@@ -173,6 +173,8 @@ int64_t kernels_per_step(const Ctx &c) {
     k += 3 + ((c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2);
   k += c.Nq > 0 ? 1 : 0;                 // gather
   k += 2;                                // kick (+kinetic), totals
+  k += (partials_compact_count(c.n_pair_blk) > 0 ? 1 : 0) +  // partials compaction
+       (partials_compact_count(c.n_coul_blk) > 0 ? 1 : 0);
   if (c.nvt) k += 2;                     // thermostat, end-of-step velocity scaling
   return k;
 }
@@ -456,6 +458,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   rc |= dalloc(c, &c.abd, c.P);
   rc |= dalloc(c, &c.emode, 2 * c.P);
   rc |= dalloc(c, &c.epart, c.epart_slots);
+  rc |= dalloc(c, &c.ecomp, 2 * kCompactMax * NQ_PAIR);
   rc |= dalloc(c, &c.scal, S_COUNT);
   rc |= dalloc(c, &c.step_dev, 1);
   rc |= dalloc(c, &c.err, 1);

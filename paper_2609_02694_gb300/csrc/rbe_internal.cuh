@@ -28,6 +28,7 @@ enum : int { ERRBIT_SAMPLER = 1, ERRBIT_NONFINITE = 2, ERRBIT_CAPACITY = 4 };
 
 // Partial-sum slots (doubles per block) of the energy / virial reductions.
 enum : int { Q_UREAL = 0, Q_ULJ = 1, Q_WREAL = 2, Q_WLJ = 3, NQ_PAIR = 4 };
+constexpr int kCompactMax = 256;  // compacted partials per pair pass before the totals
 
 struct Grid {
   int n[3];       // cells per axis
@@ -123,6 +124,7 @@ struct Ctx {
   double *emode = nullptr;   // per-mode (E_l, W_l) pairs: 2P
   // reductions
   double *epart = nullptr;   // partial slots
+  double *ecomp = nullptr;   // compacted pair / Coulomb partials [2][kCompactMax][NQ_PAIR]
   int64_t epart_slots = 0;
   int64_t off_pair = 0, off_coul = 0, off_rbl = 0, off_ke = 0, n_pair_blk = 0,
           n_coul_blk = 0, n_rbl_blk = 0, n_ke_blk = 0;
@@ -241,6 +243,7 @@ cudaError_t launch_kick(Ctx &c);
 cudaError_t launch_kinetic(Ctx &c);
 cudaError_t launch_thermostat(Ctx &c, int mode);  // 0: end + next start half, 1: start half only
 cudaError_t launch_totals(Ctx &c);
+int64_t partials_compact_count(int64_t nblk);
 cudaError_t launch_set_step(Ctx &c, uint64_t step);
 cudaError_t launch_step_advance(Ctx &c);
 cudaError_t launch_scatter_forces(Ctx &c, bool to_double);
