@@ -142,8 +142,10 @@ __device__ __forceinline__ void rbl_acc_add(const RblArgs &a, bool on_, const Pa
   }
 }
 
+// 16 one-warp blocks per SM (at most 128 registers): the compiler's own choice spilled in
+// the eager variant.
 template <typename real, bool COUL, bool MULTI, bool WRAP, bool EAGER>
-__global__ void __launch_bounds__(kRblWarps * 32) rbl_kernel(const RblArgs a) {
+__global__ void __launch_bounds__(kRblWarps * 32, 16) rbl_kernel(const RblArgs a) {
   __shared__ float4 stage[kRblWarps][kRblWin][32];
   __shared__ int4 stage_d[kRblWarps][kRblWin][32];
   __shared__ float stage_q[kRblWarps][kRblWin][32];
