@@ -19,6 +19,9 @@
 // cells; in canonical order these form exactly the lane's own S_i order. Candidates are
 // staged in shared memory in FP32 coordinates relative to the group leader. Membership is decided exactly: FP32 outside
 // a +-1e-5 band around r_core^2 and r_s^2, the FP64 oracle expression inside it.
+// Cells keep their members in (s_x, id) order, so each row's run is sorted by x and is cut
+// to the x-range some member of the group can reach (binary searches on exact unwrapped
+// coordinates); trimmed candidates are beyond r_s of every member.
 // Pass 1 classifies every candidate once in canonical order, evaluates the core pairs from
 // the staged exact integer displacements (branch-light), and keeps per lane the shell
 // members of each 32-candidate chunk: their count in shared memory and their bit mask in a
@@ -30,7 +33,9 @@
 // compare-and-swap probes that always succeed, since at most that many blocks are resident)
 // and frees it when it ends.
 // Eager variant, for shells that are mostly no larger than p (dilute systems): pass 1 also
-// evaluates every shell pair, in canonical order, into a second accumulator. A particle
+// evaluates every shell pair, in canonical order, into a second accumulator; each lane
+// queues its chunks' pair masks and a window of four chunks is evaluated with one uniform
+// trip count (its heaviest lane). A particle
 // with #S_i <= p then keeps it (the same sum pass 2 would form, bit for bit) and skips
 // pass 2; one with #S_i > p discards it and draws as above.
 // The mean-force correction is a fixed-order FP64 reduction followed by a subtraction.
@@ -308,7 +313,8 @@ __global__ void __launch_bounds__(kRblWarps * 32, 16) rbl_kernel(const RblArgs a
             const uint32_t sxj = S.sx[j];
             const int dxj = (int)(sxj - ox), dyj = (int)(S.sy[j] - oy), dzj = (int)(S.sz[j] - oz);
             if (a.gs > 1) tc = run_offset(cell_of(sxj, n0), gx, n0);  // x offset in the run
-            // products rounded explicitly: pass 2 recomputes them and must classify identically
+            // products rounded explicitly (no contraction): the classification is a fixed
+            // function of the integer coordinates
             stage[wid][w][lane] = make_float4(__fmul_rn((float)dxj, a.pa.pc.h[0]),
                                               __fmul_rn((float)dyj, a.pa.pc.h[1]),
                                               __fmul_rn((float)dzj, a.pa.pc.h[2]), 0.f);
