@@ -51,6 +51,11 @@ def lib():
                               ct.c_double, ct.c_int, ct.c_uint64, ct.c_uint64, ct.c_uint32,
                               ct.c_double, ct.c_int, _f64p, _f64p, _f64p, _dp, _dp, _dp, _dp,
                               ct.c_void_p, ct.c_void_p, ct.c_void_p]
+        L.orc_rbl_rows.argtypes = [ct.c_int64, _u32p, _f64p, _i32p, _f64p, ct.c_double,
+                                   ct.c_double, ct.c_double, ct.c_int, ct.c_uint64,
+                                   ct.c_uint64, ct.c_uint32, ct.c_double, ct.c_int, _f64p,
+                                   _f64p, _i64p, ct.c_int64, _f64p, _f64p, ct.c_void_p,
+                                   ct.c_void_p, ct.c_void_p]
         L.orc_brute_coulomb.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, ct.c_double, ct.c_int,
                                         _f64p, _dp]
         L.orc_vv_drift.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, _f64p, _f64p, ct.c_double,
@@ -60,7 +65,7 @@ def lib():
                                   ct.c_double, ct.c_double, ct.c_double, _f64p]
         L.orc_num_threads.restype = ct.c_int
         for name in ("orc_kdim_table", "orc_sample_k", "orc_rho", "orc_rbe_kspace",
-                     "orc_ewald_kspace", "orc_real_space", "orc_cells", "orc_rbl",
+                     "orc_ewald_kspace", "orc_real_space", "orc_cells", "orc_rbl", "orc_rbl_rows",
                      "orc_brute_coulomb", "orc_vv_drift", "orc_vv_kick", "orc_nh_half"):
             getattr(L, name).restype = ct.c_int
         _LIB = L
@@ -224,6 +229,31 @@ def rbl(s, q, types, box, alpha, r_core, r_s, p, seed, step, replica, C, eps, si
                          partners.ctypes.data), "rbl")
     return dict(F=F, U_real=vals[0].value, U_lj=vals[1].value, W_real=vals[2].value,
                 W_lj=vals[3].value, n_core=nc, n_shell=ns, partners=partners)
+
+
+
+def rbl_rows(s, q, types, box, alpha, r_core, r_s, p, seed, step, replica, C, eps, sig,
+             i_list):
+    """Rows i_list of the random batch list before the mean-force correction (Eqs. Ci_Si,
+    RBL): F~_i, the weighted per-row sums (U_real, U_lj, W_real, W_lj), the set sizes and
+    the drawn partners, exactly as rbl computes those rows. The correction of Eq. F_corr is
+    a sum over every row; a sample of rows sees it as one common offset."""
+    s = _s(s)
+    N = len(s)
+    eps, sig, nt = lj_tables(eps, sig)
+    il = np.ascontiguousarray(i_list, np.int64)
+    m = len(il)
+    Ft = np.zeros((m, 3), np.float64)
+    u = np.zeros((m, 4), np.float64)
+    nc = np.zeros(m, np.int32)
+    ns = np.zeros(m, np.int32)
+    partners = np.zeros((m, p), np.int32)
+    _check(lib().orc_rbl_rows(N, s, _f(q), np.ascontiguousarray(types, np.int32), _f(box),
+                              float(alpha), float(r_core), float(r_s), int(p), int(seed),
+                              int(step), int(replica), float(C), nt, eps, sig, il, m, Ft, u,
+                              nc.ctypes.data, ns.ctypes.data, partners.ctypes.data),
+           "rbl_rows")
+    return dict(Ft=Ft, u=u, n_core=nc, n_shell=ns, partners=partners)
 
 
 def brute_coulomb(s, q, box, C, R):

@@ -363,14 +363,13 @@ int orc_cells(int64_t N, const uint32_t *s, const int32_t n[3], int32_t *cell_of
 
 /* ---------------------------------------------------------------------------------- */
 /* Random batch list, Eqs. Ci_Si, RBL and F_corr. */
-int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
-            const double box[3], double alpha, double r_core, double r_s, int p,
-            uint64_t seed, uint64_t step, uint32_t replica, double C, int ntypes,
-            const double *eps, const double *sig, double *F, double *U_real,
-            double *U_lj, double *W_real, double *W_lj, int32_t *n_core,
-            int32_t *n_shell, int32_t *partners) {
-  if (N <= 0 || p < 1 || !(r_core >= 0) || !(r_s > r_core) || ntypes < 1) return -1;
-  int32_t n[3];
+/* The r_s grid of the random batch list (n_d = floor(L_d / r_s) cells, at least 3 per axis,
+ * 2 r_s < L_d) with the members of every cell in ascending (s_x, id) order, the canonical
+ * order the draws index (the paper leaves the order inside a cell open). Returns -3 when the
+ * box is too small; otherwise the three arrays are the caller's to free. */
+static int rbl_grid(int64_t N, const uint32_t *s, const double box[3], double r_s,
+                    int32_t n[3], int32_t **cell_of_out, int64_t **cell_start_out,
+                    int64_t **sorted_ids_out) {
   for (int d = 0; d < 3; ++d) {
     n[d] = (int32_t)floor(box[d] / r_s);
     if (n[d] < 3 || !(2.0 * r_s < box[d])) return -3;
@@ -380,7 +379,6 @@ int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
   int64_t *cell_start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncell + 1));
   int64_t *sorted_ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
   orc_cells(N, s, n, cell_of, cell_start, sorted_ids);
-  /* canonical order inside a cell: ascending (s_x, id) (the paper leaves it open) */
   for (int64_t cc = 0; cc < ncell; ++cc)
     for (int64_t k = cell_start[cc] + 1; k < cell_start[cc + 1]; ++k) {
       const int64_t v = sorted_ids[k];
@@ -393,6 +391,100 @@ int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
       }
       sorted_ids[u + 1] = v;
     }
+  *cell_of_out = cell_of;
+  *cell_start_out = cell_start;
+  *sorted_ids_out = sorted_ids;
+  return 0;
+}
+
+/* Row i of the random batch list before the mean-force correction (Eqs. Ci_Si, RBL): the
+ * core sum, the shell in canonical order, the draws and the weighted shell sum. f receives
+ * F~_i, u the weighted per-i sums of (U_real, U_lj, W_real, W_lj), *nc and *ns the set
+ * sizes, partners_i (nullable, p entries) the drawn ids (-1 when unused). *shell / *cap is
+ * the caller's scratch, grown as needed. */
+static void rbl_row(int64_t i, const uint32_t *s, const double *q, const int32_t *type,
+                    const double box[3], double alpha, double rcore2, double rs2, int p,
+                    const uint32_t key[2], uint64_t step, double C, int ntypes,
+                    const double *eps, const double *sig, const int32_t n[3],
+                    const int32_t *cell_of, const int64_t *cell_start,
+                    const int64_t *sorted_ids, int64_t **shell, int64_t *cap, double f_out[3],
+                    double u_out[4], int64_t *nc_out, int64_t *ns_out, int32_t *partners_i) {
+  int64_t ci = cell_of[i];
+  int64_t c3[3] = {ci % n[0], (ci / n[0]) % n[1], ci / ((int64_t)n[0] * n[1])};
+  double f[3] = {0.0, 0.0, 0.0}, acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int64_t ns = 0, nc = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int64_t cx = (c3[0] + dx + n[0]) % n[0];
+        int64_t cy = (c3[1] + dy + n[1]) % n[1];
+        int64_t cz = (c3[2] + dz + n[2]) % n[2];
+        int64_t cj = cx + (int64_t)n[0] * (cy + (int64_t)n[1] * cz);
+        for (int64_t k = cell_start[cj]; k < cell_start[cj + 1]; ++k) {
+          int64_t j = sorted_ids[k];
+          if (j == i) continue;
+          double d[3];
+          double r2 = orc_min_image_r2(&s[3 * i], &s[3 * j], box, d);
+          if (r2 <= rcore2) {
+            ++nc;
+            int pt = type[i] * ntypes + type[j];
+            double g, a, b, c, e;
+            pair_terms(r2, q[i] * q[j], alpha, C, eps[pt], sig[pt], &g, &a, &b, &c, &e);
+            for (int kk = 0; kk < 3; ++kk) f[kk] += g * d[kk];
+            acc[0] += a; acc[1] += b; acc[2] += c; acc[3] += e;
+          } else if (r2 <= rs2) {
+            if (ns == *cap) {
+              *cap *= 2;
+              *shell = (int64_t *)realloc(*shell, sizeof(int64_t) * (size_t)*cap);
+            }
+            (*shell)[ns++] = j;
+          }
+        }
+      }
+  /* shell part: all partners with weight 1 when n_s <= p, else p i.i.d. draws */
+  double fs[3] = {0.0, 0.0, 0.0}, as[4] = {0.0, 0.0, 0.0, 0.0};
+  double weight = 1.0;
+  int64_t nuse = ns <= p ? ns : p;
+  if (ns > p) weight = (double)ns / (double)p;
+  for (int64_t t = 0; t < nuse; ++t) {
+    int64_t j;
+    if (ns <= p) {
+      j = (*shell)[t];
+    } else {
+      uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(t / 4), (uint32_t)step, 1u};
+      uint32_t w[4];
+      orc_philox4x32_10(ctr, key, w);
+      uint64_t idx = ((uint64_t)w[t % 4] * (uint64_t)ns) >> 32;
+      j = (*shell)[idx];
+    }
+    if (partners_i) partners_i[t] = (int32_t)j;
+    double d[3];
+    double r2 = orc_min_image_r2(&s[3 * i], &s[3 * j], box, d);
+    int pt = type[i] * ntypes + type[j];
+    double g, a, b, c, e;
+    pair_terms(r2, q[i] * q[j], alpha, C, eps[pt], sig[pt], &g, &a, &b, &c, &e);
+    for (int kk = 0; kk < 3; ++kk) fs[kk] += g * d[kk];
+    as[0] += a; as[1] += b; as[2] += c; as[3] += e;
+  }
+  if (partners_i)
+    for (int64_t t = nuse; t < p; ++t) partners_i[t] = -1;
+  for (int kk = 0; kk < 3; ++kk) f_out[kk] = f[kk] + weight * fs[kk];
+  for (int kk = 0; kk < 4; ++kk) u_out[kk] = acc[kk] + weight * as[kk];
+  *nc_out = nc;
+  *ns_out = ns;
+}
+
+int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
+            const double box[3], double alpha, double r_core, double r_s, int p,
+            uint64_t seed, uint64_t step, uint32_t replica, double C, int ntypes,
+            const double *eps, const double *sig, double *F, double *U_real,
+            double *U_lj, double *W_real, double *W_lj, int32_t *n_core,
+            int32_t *n_shell, int32_t *partners) {
+  if (N <= 0 || p < 1 || !(r_core >= 0) || !(r_s > r_core) || ntypes < 1) return -1;
+  int32_t n[3], *cell_of;
+  int64_t *cell_start, *sorted_ids;
+  int grc = rbl_grid(N, s, box, r_s, n, &cell_of, &cell_start, &sorted_ids);
+  if (grc) return grc;
   double rcore2 = r_core * r_core, rs2 = r_s * r_s;
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ replica};
   double *Ft = (double *)malloc(sizeof(double) * 3 * (size_t)N);
@@ -404,67 +496,10 @@ int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
     int64_t *shell = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
 #pragma omp for schedule(dynamic, 16)
     for (int64_t i = 0; i < N; ++i) {
-      int64_t ci = cell_of[i];
-      int64_t c3[3] = {ci % n[0], (ci / n[0]) % n[1], ci / ((int64_t)n[0] * n[1])};
-      double f[3] = {0.0, 0.0, 0.0}, acc[4] = {0.0, 0.0, 0.0, 0.0};
-      int64_t ns = 0, nc = 0;
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            int64_t cx = (c3[0] + dx + n[0]) % n[0];
-            int64_t cy = (c3[1] + dy + n[1]) % n[1];
-            int64_t cz = (c3[2] + dz + n[2]) % n[2];
-            int64_t cj = cx + (int64_t)n[0] * (cy + (int64_t)n[1] * cz);
-            for (int64_t k = cell_start[cj]; k < cell_start[cj + 1]; ++k) {
-              int64_t j = sorted_ids[k];
-              if (j == i) continue;
-              double d[3];
-              double r2 = orc_min_image_r2(&s[3 * i], &s[3 * j], box, d);
-              if (r2 <= rcore2) {
-                ++nc;
-                int pt = type[i] * ntypes + type[j];
-                double g, a, b, c, e;
-                pair_terms(r2, q[i] * q[j], alpha, C, eps[pt], sig[pt], &g, &a, &b, &c, &e);
-                for (int kk = 0; kk < 3; ++kk) f[kk] += g * d[kk];
-                acc[0] += a; acc[1] += b; acc[2] += c; acc[3] += e;
-              } else if (r2 <= rs2) {
-                if (ns == cap) {
-                  cap *= 2;
-                  shell = (int64_t *)realloc(shell, sizeof(int64_t) * (size_t)cap);
-                }
-                shell[ns++] = j;
-              }
-            }
-          }
-      /* shell part: all partners with weight 1 when n_s <= p, else p i.i.d. draws */
-      double fs[3] = {0.0, 0.0, 0.0}, as[4] = {0.0, 0.0, 0.0, 0.0};
-      double weight = 1.0;
-      int64_t nuse = ns <= p ? ns : p;
-      if (ns > p) weight = (double)ns / (double)p;
-      for (int64_t t = 0; t < nuse; ++t) {
-        int64_t j;
-        if (ns <= p) {
-          j = shell[t];
-        } else {
-          uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(t / 4), (uint32_t)step, 1u};
-          uint32_t w[4];
-          orc_philox4x32_10(ctr, key, w);
-          uint64_t idx = ((uint64_t)w[t % 4] * (uint64_t)ns) >> 32;
-          j = shell[idx];
-        }
-        if (partners) partners[(int64_t)p * i + t] = (int32_t)j;
-        double d[3];
-        double r2 = orc_min_image_r2(&s[3 * i], &s[3 * j], box, d);
-        int pt = type[i] * ntypes + type[j];
-        double g, a, b, c, e;
-        pair_terms(r2, q[i] * q[j], alpha, C, eps[pt], sig[pt], &g, &a, &b, &c, &e);
-        for (int kk = 0; kk < 3; ++kk) fs[kk] += g * d[kk];
-        as[0] += a; as[1] += b; as[2] += c; as[3] += e;
-      }
-      if (partners)
-        for (int64_t t = nuse; t < p; ++t) partners[(int64_t)p * i + t] = -1;
-      for (int kk = 0; kk < 3; ++kk) Ft[3 * i + kk] = f[kk] + weight * fs[kk];
-      for (int kk = 0; kk < 4; ++kk) ui[4 * i + kk] = acc[kk] + weight * as[kk];
+      int64_t nc, ns;
+      rbl_row(i, s, q, type, box, alpha, rcore2, rs2, p, key, step, C, ntypes, eps, sig, n,
+              cell_of, cell_start, sorted_ids, &shell, &cap, &Ft[3 * i], &ui[4 * i], &nc, &ns,
+              partners ? &partners[(int64_t)p * i] : NULL);
       if (n_core) n_core[i] = (int32_t)nc;
       if (n_shell) n_shell[i] = (int32_t)ns;
       if (nc > 2147483647 || ns > 2147483647) bad = 1;
@@ -486,6 +521,52 @@ int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
   if (W_real) *W_real = 0.5 * sums[2];
   if (W_lj) *W_lj = 0.5 * sums[3];
   free(cell_of); free(cell_start); free(sorted_ids); free(Ft); free(ui);
+  return bad ? -4 : 0;
+}
+
+/* Rows i_list[0..n_list) of the random batch list before the mean-force correction, with
+ * the grid, enumeration and draws of orc_rbl: Ft (n_list x 3) receives F~_i, u (nullable,
+ * n_list x 4) the weighted per-i sums of (U_real, U_lj, W_real, W_lj), n_core / n_shell
+ * (nullable, n_list) the set sizes and partners (nullable, n_list x p) the drawn ids. The
+ * correction -(1/N) sum_j F~_j of Eq. F_corr needs every row, so a sample of rows sees it
+ * as one offset common to all of them. */
+int orc_rbl_rows(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
+                 const double box[3], double alpha, double r_core, double r_s, int p,
+                 uint64_t seed, uint64_t step, uint32_t replica, double C, int ntypes,
+                 const double *eps, const double *sig, const int64_t *i_list, int64_t n_list,
+                 double *Ft, double *u, int32_t *n_core, int32_t *n_shell,
+                 int32_t *partners) {
+  if (N <= 0 || p < 1 || !(r_core >= 0) || !(r_s > r_core) || ntypes < 1 || n_list < 0)
+    return -1;
+  for (int64_t t = 0; t < n_list; ++t)
+    if (i_list[t] < 0 || i_list[t] >= N) return -1;
+  int32_t n[3], *cell_of;
+  int64_t *cell_start, *sorted_ids;
+  int grc = rbl_grid(N, s, box, r_s, n, &cell_of, &cell_start, &sorted_ids);
+  if (grc) return grc;
+  double rcore2 = r_core * r_core, rs2 = r_s * r_s;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ replica};
+  int bad = 0;
+#pragma omp parallel
+  {
+    int64_t cap = 1024;
+    int64_t *shell = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t t = 0; t < n_list; ++t) {
+      int64_t nc, ns;
+      double ut[4];
+      rbl_row(i_list[t], s, q, type, box, alpha, rcore2, rs2, p, key, step, C, ntypes, eps,
+              sig, n, cell_of, cell_start, sorted_ids, &shell, &cap, &Ft[3 * t], ut, &nc, &ns,
+              partners ? &partners[(int64_t)p * t] : NULL);
+      if (u)
+        for (int kk = 0; kk < 4; ++kk) u[4 * t + kk] = ut[kk];
+      if (n_core) n_core[t] = (int32_t)nc;
+      if (n_shell) n_shell[t] = (int32_t)ns;
+      if (nc > 2147483647 || ns > 2147483647) bad = 1;
+    }
+    free(shell);
+  }
+  free(cell_of); free(cell_start); free(sorted_ids);
   return bad ? -4 : 0;
 }
 

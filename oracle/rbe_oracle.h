@@ -121,6 +121,20 @@ int orc_rbl(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
             double *U_lj, double *W_real, double *W_lj, int32_t *n_core,
             int32_t *n_shell, int32_t *partners);
 
+/* Rows i_list[0..n_list) (ids in [0, N)) of the random batch list before the mean-force
+ * correction: the grid, enumeration, draws and weights of orc_rbl for those rows only.
+ * Ft (n_list x 3) receives F~_i, u (nullable, n_list x 4) the weighted per-i sums of
+ * (U_real, U_lj, W_real, W_lj), n_core / n_shell (nullable) the set sizes and partners
+ * (nullable, n_list x p) the drawn ids (-1 when unused). The correction -(1/N) sum_j F~_j
+ * needs every row: for a sample it is one offset common to all rows. Returns -1 on an
+ * invalid argument or id, -3 when the box holds fewer than 3 cells of r_s per axis. */
+int orc_rbl_rows(int64_t N, const uint32_t *s, const double *q, const int32_t *type,
+                 const double box[3], double alpha, double r_core, double r_s, int p,
+                 uint64_t seed, uint64_t step, uint32_t replica, double C, int ntypes,
+                 const double *eps, const double *sig, const int64_t *i_list, int64_t n_list,
+                 double *Ft, double *u, int32_t *n_core, int32_t *n_shell,
+                 int32_t *partners);
+
 /* Brute-force Coulomb lattice sum of Eq. Coul_potential over whole image cells with
  * |n o L| <= R L_x (spherical order), converted to the tin-foil convention of the Ewald sum by
  * subtracting 2 pi |M|^2 / (3V) from the energy and adding 4 pi q_i M / (3V) to the

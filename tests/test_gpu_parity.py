@@ -390,6 +390,49 @@ def test_full_size_one_million_sampled(orc):
     assert rel_l2(F[idx], Fo) < TOL_F32
 
 
+
+def kspace_force_sampled(sy, idx, m, S, rho):
+    """k-space force (Eq. F_long_RBE) of the particles idx from a structure factor rho."""
+    k = 2 * np.pi * m / sy.box
+    k2 = (k * k).sum(1)
+    V = np.prod(sy.box)
+    th = sy.positions()[idx] @ k.T
+    im = rho.imag[None, :] * np.cos(th) - rho.real[None, :] * np.sin(th)
+    c = (S / len(m)) * 4 * np.pi * C / (V * k2)
+    return -(sy.q[idx][:, None, None] * (c * im)[:, :, None] * k[None, :, :]).sum(1)
+
+
+def test_full_size_rbl_134m_sampled(orc):
+    """134,217,728 particles (5% charged, density 0.1, P = 500, random batch list with
+    r_core = 5 A, r_s = 10 A, p = 10, seed 1), in the benchmark's launch configuration. On
+    sampled particles: core and shell sizes bit for bit, and the force against the oracle's
+    rows of the random batch list plus the k-space force from the oracle's structure factor.
+    The mean-force correction (Eq. F_corr) sums all 2^27 rows, which the oracle cannot do in
+    a test: it is the one offset common to the sample, and it must be small."""
+    sy = synth.make_system(1 << 27, density=0.1, frac_charged=0.05, seed=5)
+    p, r_core, seed, step = 10, 5.0, 1, 0
+    with handle(sy, 500, r_core=r_core, p_rbl=p, seed=seed) as h:
+        F, E, W = h.forces_f64(step)
+        nc, ns = h.neighbor_counts()
+        m, S = h.sample_k(step)
+    rng = np.random.default_rng(0)
+    charged = np.flatnonzero(sy.q != 0)
+    idx = np.unique(np.concatenate([rng.choice(sy.n, 64, replace=False), charged[:16],
+                                    [0, sy.n - 1]]))
+    F, nc, ns = F[idx], nc[idx], ns[idx]
+    rows = orc.rbl_rows(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, RC, p, seed, step, 0, C,
+                        sy.eps, sy.sig, idx)
+    assert np.array_equal(nc, rows["n_core"])
+    assert np.array_equal(ns, rows["n_shell"])
+    assert (rows["n_shell"] > p).all()  # every sampled row draws
+    # zero charges add exact zeros to rho: the charged subset gives the same sums
+    rho_o = orc.rho(sy.s[charged], sy.q[charged], sy.box, m)
+    Fo = rows["Ft"] + kspace_force_sampled(sy, idx, m, S, rho_o)
+    off = (F - Fo).mean(0)
+    assert np.linalg.norm(off) < 1e-2 * np.sqrt((Fo * Fo).sum(1).mean())
+    assert rel_l2(F - off, Fo) < TOL_F32
+
+
 # -------------------------------------------------------------------------- tuning
 
 

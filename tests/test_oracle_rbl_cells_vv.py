@@ -115,6 +115,35 @@ def test_rbl_draws_match_brute_force_enumeration(orc):
         assert list(rb["partners"][i]) == want
 
 
+
+def test_rbl_rows_are_the_rows_of_the_full_list(orc):
+    """The sampled-rows entry (used where the whole list is too large for the oracle): over
+    every row it gives the full list's set sizes, draws, corrected forces (Eq. F_corr applied
+    here) and energies; a sample of rows gives exactly those rows, whatever the sample."""
+    sy = synth.make_system(12000, density=0.1, frac_charged=0.05, seed=5)
+    args = (sy.s, sy.q, sy.types, sy.box, 0.09, 5.0, 10.0, 10, 3, 7, 0, synth.COULOMB_C,
+            sy.eps, sy.sig)
+    rb = orc.rbl(*args)
+    al = orc.rbl_rows(*args, np.arange(sy.n))
+    assert np.array_equal(al["n_core"], rb["n_core"])
+    assert np.array_equal(al["n_shell"], rb["n_shell"])
+    assert np.array_equal(al["partners"], rb["partners"])
+    assert (rb["n_shell"] > 10).all()  # every row draws
+    mean = al["Ft"].sum(0) / sy.n
+    scale = np.abs(rb["F"]).max()
+    assert np.abs(al["Ft"] - mean - rb["F"]).max() < 1e-12 * scale
+    assert np.abs(mean).max() > 0.0  # the correction is not empty
+    half = 0.5 * al["u"].sum(0)
+    for k, key in enumerate(("U_real", "U_lj", "W_real", "W_lj")):
+        assert half[k] == pytest.approx(rb[key], rel=1e-12, abs=1e-9)
+    idx = np.array([sy.n - 1, 0, 4321, 17, 17, 9000])  # any order, repeats allowed
+    sm = orc.rbl_rows(*args, idx)
+    assert np.array_equal(sm["Ft"], al["Ft"][idx])
+    assert np.array_equal(sm["partners"], al["partners"][idx])
+    with pytest.raises(ValueError):
+        orc.rbl_rows(*args, np.array([sy.n]))
+
+
 @pytest.mark.slow
 def test_rbl_unbiased_over_seeds(orc):
     """E[F_i] over RBL draws equals the exact cutoff force (Eq. RBL is unbiased; the mean
