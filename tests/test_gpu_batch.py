@@ -97,3 +97,48 @@ def test_batch_mixed_traversals_equal_individual_steps():
     assert hb[1].neighbor_list_stats()["builds"] == hi[1].neighbor_list_stats()["builds"] >= 1
     for h in hb + hi:
         h.close()
+
+
+def test_full_size_batch96(orc):
+    """The benchmark's 96 replicas (log-uniform 2,000..250,000 particles, 10% charged, seeds
+    1000 + r, replica keys r, P = 200). Step-0 forces and neighbour counts of sampled
+    particles of every replica match the oracle; then two batched steps (one graph launch
+    each) leave every replica exactly where its own two steps leave it."""
+    import torch
+    import sampled
+    sizes = synth.replica_sizes(96)
+    systems = [synth.make_system(n, density=0.1, frac_charged=0.1, seed=1000 + r)
+               for r, n in enumerate(sizes)]
+
+    def make(r, sy):
+        return binding.from_system(sy, P=200, alpha=synth.ALPHA, r_c=synth.R_CUT,
+                                   coulomb_C=synth.COULOMB_C, dt=1.0, kappa=synth.ACCEL_KAPPA,
+                                   replica=r)
+
+    Fg, Fo = [], []
+    for r, sy in enumerate(systems):
+        with make(r, sy) as h:
+            F, _, _ = h.forces_f64(0)
+            nbr, _ = h.neighbor_counts()
+            m, S = h.sample_k(0)
+        rng = np.random.default_rng(r)
+        idx = np.unique(np.r_[rng.choice(sy.n, 4, replace=False), np.flatnonzero(sy.q)[:1]])
+        Fo_r, nbr_o = sampled.total_forces_sampled(orc, sy, idx, m, S)
+        assert np.array_equal(nbr[idx], nbr_o)
+        Fg.append(F[idx])
+        Fo.append(Fo_r)
+    Fg, Fo = np.concatenate(Fg), np.concatenate(Fo)
+    assert np.linalg.norm(Fg - Fo) / np.linalg.norm(Fo) < 1e-5
+    hb = [make(r, sy) for r, sy in enumerate(systems)]
+    hi = [make(r, sy) for r, sy in enumerate(systems)]
+    with binding.Batch(hb) as b:
+        b.step(2)
+        torch.cuda.synchronize()
+        for h in hi:
+            h.step(2)
+        for a, c in zip(hb, hi):
+            _, va, sa = a.state()
+            _, vc, sc = c.state()
+            assert np.array_equal(sa, sc) and np.array_equal(va, vc)
+    for h in hb + hi:
+        h.close()

@@ -11,6 +11,8 @@ import pytest
 
 from paper_2609_02694_gb300 import binding, build, synth
 
+import sampled
+
 pytestmark = pytest.mark.gpu
 
 C = synth.COULOMB_C
@@ -33,6 +35,14 @@ def rel_l2(a, b):
 def handle(sy, P, precision="fp32_comp", **kw):
     return binding.from_system(sy, P=P, alpha=kw.pop("alpha", ALPHA), r_c=kw.pop("r_c", RC),
                                precision=precision, coulomb_C=C, **kw)
+
+
+def sample_ids(sy, n, seed=0):
+    """n random particles, the first 16 charged ones, and the first and last id."""
+    rng = np.random.default_rng(seed)
+    charged = np.flatnonzero(sy.q != 0)
+    return np.unique(np.concatenate([rng.choice(sy.n, n, replace=False), charged[:16],
+                                     [0, sy.n - 1]]))
 
 
 def oracle_all(orc, sy, m, S, alpha=ALPHA, rc=RC):
@@ -364,43 +374,40 @@ def test_graph_replay_equals_single_steps():
 @pytest.mark.slow
 def test_full_size_one_million_sampled(orc):
     """1,048,576 particles (10% charged, density 0.1, P = 200), the launch configuration
-    of the benchmark: forces on 48 sampled particles against the oracle's O(N) sums."""
+    of the benchmark: forces and neighbour counts of sampled particles against the oracle's
+    O(N) sums."""
     sy = synth.make_system(1 << 20, density=0.1, frac_charged=0.1, seed=2)
     with handle(sy, 200) as h:
         F, E, W = h.forces_f64(0)
+        nbr, _ = h.neighbor_counts()
         m, S = h.sample_k(0)
         rho, _ = h.rho()
-    rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(sy.n, 48, replace=False))
-    charged = np.flatnonzero(sy.q != 0)
-    idx = np.unique(np.concatenate([idx, charged[:16]]))
-    rs = orc.real_space(sy.s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig, i_list=idx)
-    rho_o = orc.rho(sy.s, sy.q, sy.box, m)
-    assert rel_l2(rho, rho_o) < 2e-6
-    # k-space force of the sampled particles from the oracle's rho (Eq. F_long_RBE)
-    k = 2 * np.pi * m / sy.box
-    k2 = (k * k).sum(1)
-    V = np.prod(sy.box)
-    r = sy.positions()[idx]
-    th = r @ k.T
-    im = rho_o.imag[None, :] * np.cos(th) - rho_o.real[None, :] * np.sin(th)
-    c = (S / len(m)) * 4 * np.pi * C / (V * k2)
-    Fk = -(sy.q[idx][:, None, None] * (c * im)[:, :, None] * k[None, :, :]).sum(1)
-    Fo = rs["F"][idx] + Fk
+    idx = sample_ids(sy, 48)
+    assert rel_l2(rho, sampled.charged_rho(orc, sy, m)) < 2e-6
+    Fo, nbr_o = sampled.total_forces_sampled(orc, sy, idx, m, S)
+    assert np.array_equal(nbr[idx], nbr_o)
     assert rel_l2(F[idx], Fo) < TOL_F32
 
 
+@pytest.fixture(scope="module")
+def sys16m():
+    return synth.make_system(1 << 24, density=0.1, frac_charged=0.1, seed=3)
 
-def kspace_force_sampled(sy, idx, m, S, rho):
-    """k-space force (Eq. F_long_RBE) of the particles idx from a structure factor rho."""
-    k = 2 * np.pi * m / sy.box
-    k2 = (k * k).sum(1)
-    V = np.prod(sy.box)
-    th = sy.positions()[idx] @ k.T
-    im = rho.imag[None, :] * np.cos(th) - rho.real[None, :] * np.sin(th)
-    c = (S / len(m)) * 4 * np.pi * C / (V * k2)
-    return -(sy.q[idx][:, None, None] * (c * im)[:, :, None] * k[None, :, :]).sum(1)
 
+@pytest.mark.parametrize("precision,P,tol", [("fp32_comp", 2000, TOL_F32), ("fp32", 500, TOL_F32),
+                                             ("fp64", 100, TOL_F64)])
+def test_full_size_sixteen_million_sampled(orc, sys16m, precision, P, tol):
+    """16,777,216 particles (10% charged, density 0.1) in the three forms of the precision
+    sweep: forces and neighbour counts of sampled particles against the oracle's O(N) sums."""
+    sy = sys16m
+    with handle(sy, P, precision=precision) as h:
+        F, E, W = h.forces_f64(0)
+        nbr, _ = h.neighbor_counts()
+        m, S = h.sample_k(0)
+    idx = sample_ids(sy, 32)
+    Fo, nbr_o = sampled.total_forces_sampled(orc, sy, idx, m, S)
+    assert np.array_equal(nbr[idx], nbr_o)
+    assert rel_l2(F[idx], Fo) < tol
 
 def test_full_size_rbl_134m_sampled(orc):
     """134,217,728 particles (5% charged, density 0.1, P = 500, random batch list with
@@ -415,19 +422,15 @@ def test_full_size_rbl_134m_sampled(orc):
         F, E, W = h.forces_f64(step)
         nc, ns = h.neighbor_counts()
         m, S = h.sample_k(step)
-    rng = np.random.default_rng(0)
-    charged = np.flatnonzero(sy.q != 0)
-    idx = np.unique(np.concatenate([rng.choice(sy.n, 64, replace=False), charged[:16],
-                                    [0, sy.n - 1]]))
+    idx = sample_ids(sy, 64)
     F, nc, ns = F[idx], nc[idx], ns[idx]
     rows = orc.rbl_rows(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, RC, p, seed, step, 0, C,
                         sy.eps, sy.sig, idx)
     assert np.array_equal(nc, rows["n_core"])
     assert np.array_equal(ns, rows["n_shell"])
     assert (rows["n_shell"] > p).all()  # every sampled row draws
-    # zero charges add exact zeros to rho: the charged subset gives the same sums
-    rho_o = orc.rho(sy.s[charged], sy.q[charged], sy.box, m)
-    Fo = rows["Ft"] + kspace_force_sampled(sy, idx, m, S, rho_o)
+    Fo = rows["Ft"] + sampled.kspace_force_sampled(sy, idx, m, S,
+                                                   sampled.charged_rho(orc, sy, m))
     off = (F - Fo).mean(0)
     assert np.linalg.norm(off) < 1e-2 * np.sqrt((Fo * Fo).sum(1).mean())
     assert rel_l2(F - off, Fo) < TOL_F32
