@@ -21,8 +21,9 @@
 //     iterations that every lane has consumed its hits staged there; every lane with hits
 //     pending evaluates in each iteration, so lanes light on old chunks work ahead. Each
 //     lane recomputes the displacement exactly from the integer coordinates and applies
-//     the exact cutoff decision: FP32 outside a +-1e-5 band, FP64 inside it, which matches
-//     the oracle's decision bit for bit. Then it evaluates the pair force.
+//     the exact cutoff decision: FP32 outside a band of at least +-1e-5 (its top is the
+//     pre-test's threshold), FP64 inside it, which matches the oracle's decision bit for
+//     bit. Then it evaluates the pair force.
 // Forces are summed per i in a fixed j order with no atomics, so results are run-to-run
 // reproducible. The hot loop is FP32 ALU / SFU bound.
 // The BUILD variant walks the same windows with the list radius r_c + skin and, instead of
@@ -529,6 +530,39 @@ int frame_span_cells(const Ctx &c, double rc) {
 
 int64_t pair_blocks(int64_t n) { return (n + 32 * kPairWarps - 1) / (32 * kPairWarps); }
 
+// An FP32 r^2 formed from FP32 frame coordinates (each the integer offset from the group
+// leader, converted and scaled by L / 2^32: within 2u|x| of exact, u = 2^-24) is off by at
+// most, per axis, e_d = 4u X_d (both ends) + 2u r (the rounded difference and the rounded
+// scale), plus u L_d when the difference is folded into the box; so the sum of squares is
+// within 2 r |e| + |e|^2, and the fused sums add 3u r^2 more. The band is that bound, taken
+// 1.25 times and never below 1e-5, relative to r^2: outside it the FP32 comparison is exact.
+double frame_band(const double X[3], double r, const double box[3], bool wrap) {
+  const double u = std::ldexp(1.0, -24);
+  double s2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double e = 4.0 * u * X[d] + 2.0 * u * r + (wrap ? 2.0 * u * box[d] : 0.0);
+    s2 += e * e;
+  }
+  const double eps = 2.0 * std::sqrt(s2) / r + s2 / (r * r) + 5.0 * u;
+  return std::max(1e-5, 1.25 * eps);
+}
+
+// The FP32 pre-test compares an r^2 from FP32 frame coordinates with rc2_hi. A group's frame
+// coordinates lie within (span + R) cells of its leader in x (span = smax16 for the half test,
+// else smax) and R + 1 cells in y and z, or L/2 in a wrapping box, so rc2_hi is raised by the
+// band for that extent. rc2_hi is also the top of the evaluation's exact band, which then
+// only sends a few more pairs to the FP64 decision.
+static void set_pretest_band(const Ctx &c, PairArgs &a, double r, bool wrap) {
+  double X[3];
+  const int span = a.smax16 > 0 ? a.smax16 : a.smax;
+  for (int d = 0; d < 3; ++d) {
+    const double w = c.box[d] / c.grid.n[d];
+    const int cells = d == 0 ? span + a.grid.R[0] : a.grid.R[d] + 1;
+    X[d] = wrap ? 0.5 * c.box[d] : std::min(cells * w, 0.5 * c.box[d]);
+  }
+  a.pc.rc2_hi = (float)(r * r * (1.0 + frame_band(X, r, c.box, wrap)));
+}
+
 cudaError_t launch_pair(Ctx &c, bool want_counts) {
   const int b = c.cur;
   const bool fused = c.Nq * 2 > c.N;  // most particles charged: one LJ + Coulomb pass
@@ -557,6 +591,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
     a.L[d] = (float)c.box[d];
     a.invL[d] = (float)(1.0 / c.box[d]);
   }
+  set_pretest_band(c, a, c.rc, wrap);
   const bool fp64 = c.precision == RBE_FP64;
   if (fused) {
     if (fp64) launch_one<double, true, true>(a, c.N, multi, wrap, c.stream);
@@ -576,6 +611,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
       // FP32 pre-test: the dilute charged subset's groups then span more cells (the half-
       // precision test bounds a group's extent), so fewer groups walk their stencils
       b2.smax16 = 0;
+      set_pretest_band(c, b2, c.rc, wrap);
       b2.trim = 0;  // rows of the dilute subset are short: trimming costs more than it saves
       b2.epart = c.epart + c.off_coul;
       b2.nbr = nullptr;
@@ -597,8 +633,7 @@ cudaError_t launch_list_build(Ctx &c) {
   a.pc = c.pc;
   const double rl = c.rc + c.vl_skin, rl2 = rl * rl;
   a.pc.rc2d = rl2;
-  a.pc.rc2_lo = (float)(rl2 * (1.0 - 1e-5));
-  a.pc.rc2_hi = (float)(rl2 * (1.0 + 1e-5));
+  a.pc.rc2_lo = (float)(rl2 * (1.0 - 1e-5));  // (rc2_hi: the pre-test band, set below)
   a.set.sx = c.s[b]; a.set.sy = c.s[b] + c.N; a.set.sz = c.s[b] + 2 * c.N;
   a.set.qf = c.qf[b]; a.set.qd = c.qd[b]; a.set.type = nullptr;
   a.set.cell_start = c.cell_start; a.set.map = nullptr; a.set.n = c.N;
@@ -611,6 +646,7 @@ cudaError_t launch_list_build(Ctx &c) {
     a.L[d] = (float)c.box[d];
     a.invL[d] = (float)(1.0 / c.box[d]);
   }
+  set_pretest_band(c, a, rl, wrap);
   a.list = c.vl_list; a.len = c.vl_len; a.K = c.vl_K;
   a.gate = c.vl_flags; a.maxlen = c.vl_flags + 2; a.err = c.err;
   launch_one<float, false, false, true>(a, c.N, false, wrap, c.stream);

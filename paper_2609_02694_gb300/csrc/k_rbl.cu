@@ -17,8 +17,10 @@
 // 9 rows (dz, dy) in canonical order, each a run of gs + 2 cells in x. Every candidate
 // carries its x offset in that run, and a lane keeps only candidates of its own three x
 // cells; in canonical order these form exactly the lane's own S_i order. Candidates are
-// staged in shared memory in FP32 coordinates relative to the group leader. Membership is decided exactly: FP32 outside
-// a +-1e-5 band around r_core^2 and r_s^2, the FP64 oracle expression inside it.
+// staged in shared memory in FP32 coordinates relative to the group leader. Membership is
+// decided exactly: FP32 outside a band around r_core^2 and r_s^2 (+-1e-5, or the FP32
+// error bound of the group's extent where that is larger), the FP64 oracle expression
+// inside it.
 // Cells keep their members in (s_x, id) order, so each row's run is sorted by x and is cut
 // to the x-range some member of the group can reach (binary searches on exact unwrapped
 // coordinates); trimmed candidates are beyond r_s of every member.
@@ -78,8 +80,9 @@ __device__ __forceinline__ int run_offset(int cxj, int gx, int n0) {
   return d;
 }
 
-// Coarse FP32 classes with the exact FP64 decision inside the +-1e-5 bands of r_core^2 and
-// r_s^2: 0 outside, 1 core (r <= r_core), 2 shell (r_core < r <= r_s).
+// Coarse FP32 classes with the exact FP64 decision inside the bands of r_core^2 and r_s^2
+// (at least +-1e-5, wider for long groups): 0 outside, 1 core (r <= r_core), 2 shell
+// (r_core < r <= r_s).
 __device__ __forceinline__ int rbl_class(const RblArgs &a, float r2, int dsx, int dsy, int dsz) {
   if (r2 < a.rcore2_lo) return 1;
   if (r2 > a.rs2_hi) return 0;
@@ -687,8 +690,6 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   pa.nbr = nullptr;
   a.id = c.id[b];
   const double rc2 = c.rc * c.rc, rk2 = c.r_core * c.r_core;
-  a.rcore2_lo = (float)(rk2 * (1.0 - 1e-5)); a.rcore2_hi = (float)(rk2 * (1.0 + 1e-5));
-  a.rs2_lo = (float)(rc2 * (1.0 - 1e-5)); a.rs2_hi = (float)(rc2 * (1.0 + 1e-5));
   a.rcore2d = rk2; a.rs2d = rc2;
   a.p = c.p_rbl;
   a.key = make_uint2((uint32_t)c.seed, (uint32_t)(c.seed >> 32) ^ c.replica);
@@ -703,6 +704,19 @@ cudaError_t launch_rbl(Ctx &c, bool want_debug) {
   int gs;
   bool wrap;
   rbl_shape(c, &gs, &wrap);
+  {
+    // The classification compares an r^2 from FP32 frame coordinates with the bands: a
+    // group's candidates lie within gs + 1 cells of its leader in x and 2 in y and z (L/2
+    // in a wrapping box), and each band is at least that r^2's error bound.
+    double X[3];
+    for (int d = 0; d < 3; ++d) {
+      const double w = c.box[d] / c.grid.n[d];
+      X[d] = wrap ? 0.5 * c.box[d] : std::min((d == 0 ? gs + 1 : 2) * w, 0.5 * c.box[d]);
+    }
+    const double bk = frame_band(X, c.r_core, c.box, wrap), bs = frame_band(X, c.rc, c.box, wrap);
+    a.rcore2_lo = (float)(rk2 * (1.0 - bk)); a.rcore2_hi = (float)(rk2 * (1.0 + bk));
+    a.rs2_lo = (float)(rc2 * (1.0 - bs)); a.rs2_hi = (float)(rc2 * (1.0 + bs));
+  }
   for (int d = 0; d < 3; ++d) {
     pa.L[d] = (float)c.box[d];
     pa.invL[d] = (float)(1.0 / c.box[d]);

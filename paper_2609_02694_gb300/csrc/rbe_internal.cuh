@@ -60,7 +60,7 @@ struct LJTable {
 struct PairConst {
   float h[3];            // L_d / 2^32 (float)
   double hd[3];          // L_d / 2^32 (double)
-  float rc2_lo, rc2_hi;  // r_c^2 (1 -/+ 1e-5): outside this band FP32 decides
+  float rc2_lo, rc2_hi;  // r_c^2 (1 -/+ band): outside this band FP32 decides
   double rc2d;           // r_c^2, the exact decision inside the band
   float sqrt_alpha, alpha, C;   // Coulomb
   double sqrt_alpha_d, alpha_d, C_d;
@@ -244,6 +244,9 @@ cudaError_t launch_kinetic(Ctx &c);
 cudaError_t launch_thermostat(Ctx &c, int mode);  // 0: end + next start half, 1: start half only
 cudaError_t launch_totals(Ctx &c);
 int64_t partials_compact_count(int64_t nblk);
+// Relative half-width of the band around r^2 inside which the exact FP64 decision is taken,
+// for an FP32 r^2 formed from FP32 frame coordinates with |x_d| <= X[d] (at least 1e-5).
+double frame_band(const double X[3], double r, const double box[3], bool wrap);
 cudaError_t launch_set_step(Ctx &c, uint64_t step);
 cudaError_t launch_step_advance(Ctx &c);
 cudaError_t launch_scatter_forces(Ctx &c, bool to_double);
