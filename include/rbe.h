@@ -290,6 +290,16 @@ int rbe_batch_destroy(rbe_batch b);
 int rbe_structure_factor_noalloc(const uint32_t *s, const float *q, int64_t N,
                                  const int32_t *m, int P, double *rho, void *cuda_stream);
 
+/* Relative half-width of the band around r^2 inside which the kernels take the exact FP64
+ * cutoff decision (Eq. Ci_Si: r <= r_c inclusive), for an FP32 r^2 formed from FP32 frame
+ * coordinates: each coordinate's magnitude is at most X[d] (Angstrom, X[d] >= 0), the pair
+ * is at distance r > 0, the box edges are box[3] > 0, and wrap != 0 when differences are
+ * folded into the box. The band is 1.25 times the worst-case rounding bound of that r^2 and
+ * never below 1e-5; outside it the FP32 comparison decides exactly. Host-only: needs no GPU
+ * and no handle. Returns the band, or -1 for an invalid argument (NULL, non-finite or out
+ * of range). */
+double rbe_decision_band(const double X[3], double r, const double box[3], int wrap);
+
 /* Static description of an error code. */
 const char *rbe_error_string(int code);
 

@@ -95,11 +95,13 @@ def lib(build_if_missing: bool = False):
     L.rbe_get_neighbor_list.argtypes = [ct.c_void_p, _vp]
     L.rbe_structure_factor_noalloc.argtypes = [_vp, _vp, ct.c_int64, _vp, ct.c_int, _vp, _vp]
     L.rbe_destroy.argtypes = [h]
+    L.rbe_decision_band.argtypes = [_vp, ct.c_double, _vp, ct.c_int]
+    L.rbe_decision_band.restype = ct.c_double
     L.rbe_error_string.argtypes = [ct.c_int]
     L.rbe_error_string.restype = ct.c_char_p
     L.rbe_version.restype = ct.c_char_p
     for name in declared_functions():
-        if name not in ("rbe_error_string", "rbe_version"):
+        if name not in ("rbe_error_string", "rbe_version", "rbe_decision_band"):
             getattr(L, name).restype = ct.c_int
     _LIB = L
     return L
@@ -376,6 +378,17 @@ def measure_peak(kind: str) -> float:
     _check(lib().rbe_measure_peak({"fp32": 0, "sincos": 1, "fp64": 2}[kind], ct.addressof(v), None),
            "rbe_measure_peak")
     return v.value
+
+
+def decision_band(X, r: float, box, wrap: bool = False) -> float:
+    """Relative half-width of the exact-decision band the kernels use around r^2 for an FP32
+    r^2 from frame coordinates bounded by X (per axis), in a box of edges box."""
+    X = _f64(X).reshape(3).copy()
+    b = _f64(box).reshape(3).copy()
+    v = lib().rbe_decision_band(X.ctypes.data, float(r), b.ctypes.data, int(bool(wrap)))
+    if v < 0:
+        raise ValueError("rbe_decision_band: invalid argument")
+    return v
 
 
 def from_system(sy, *, P: int, alpha: float, r_c: float, **kw) -> RBE:

@@ -261,6 +261,14 @@ extern "C" {
 
 const char *rbe_version(void) { return "rbe-gb300 1.0 (sm_103a)"; }
 
+double rbe_decision_band(const double X[3], double r, const double box[3], int wrap) {
+  if (!X || !box || !(r > 0.0) || !std::isfinite(r)) return -1.0;
+  for (int d = 0; d < 3; ++d)
+    if (!(X[d] >= 0.0) || !std::isfinite(X[d]) || !(box[d] > 0.0) || !std::isfinite(box[d]))
+      return -1.0;
+  return frame_band(X, r, box, wrap != 0);
+}
+
 const char *rbe_error_string(int code) {
   switch (code) {
     case RBE_OK: return "ok";

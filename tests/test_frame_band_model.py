@@ -120,3 +120,23 @@ def test_f32_emulation_rounds_exactly():
                                          int(v.view(np.uint32)) & 1))
         assert got[k] == want, (a[k], b[k], c[k])
     assert got[-2] == np.float32(1 + 2 ** -11) and got[-1] > got[-2]
+
+
+def test_library_band_is_the_bound():
+    """The library's band (host code, no GPU) is 1.25 times this bound, never below 1e-5,
+    and so covers the observed FP32 error at every extent above; invalid input is refused."""
+    import pytest
+    from paper_2609_02694_gb300 import binding, build
+    build.build()
+    for label, L, X, r in CASES + [("half box 134m", 1103.07, (551.5, 15.0, 15.0), 10.0)]:
+        band = binding.decision_band(X, r, (L, L, L))
+        assert band == pytest.approx(max(1e-5, 1.25 * band_bound(X, r, (L, L, L))), rel=1e-12)
+        assert band >= observed_error(L, X, r, n=50000), label
+    wrap = binding.decision_band((16.0, 16.0, 16.0), 10.0, (32.0, 32.0, 32.0), wrap=True)
+    assert wrap == pytest.approx(max(1e-5, 1.25 * band_bound((16.0,) * 3, 10.0, (32.0,) * 3,
+                                                            wrap=True)), rel=1e-12)
+    assert binding.decision_band((0.0, 0.0, 0.0), 10.0, (100.0,) * 3) == 1e-5
+    for bad in [((1.0, 1.0, 1.0), 0.0, (10.0,) * 3), ((-1.0, 1.0, 1.0), 1.0, (10.0,) * 3),
+                ((1.0, 1.0, float("nan")), 1.0, (10.0,) * 3), ((1.0,) * 3, 1.0, (10.0, 0.0, 10.0))]:
+        with pytest.raises(ValueError):
+            binding.decision_band(*bad)
