@@ -223,6 +223,29 @@ def cpu_oracle_step(orc, sy, P, n_sample, seed=0):
     return (t1 - t0) + (t2 - t1) * sy.n / n_sample, t2 - t0
 
 
+def cpu_baseline_record(orc, sy, P, n_sample=512, n_sample_1=64):
+    """The oracle as it stands, timed on the host cores with all its OpenMP threads and on
+    one thread: one step-0 force evaluation each (cpu_oracle_step), real-space sums sampled
+    and extrapolated. The thread count is restored afterwards."""
+    cores = orc.num_threads()
+    t_all, spent = cpu_oracle_step(orc, sy, P, n_sample)
+    orc.set_num_threads(1)
+    try:
+        t_one, spent1 = cpu_oracle_step(orc, sy, P, n_sample_1, seed=1)
+    finally:
+        orc.set_num_threads(cores)
+
+    def sample(n, s):
+        return ("one step 0 force evaluation: full structure factor and k-space forces, O(N) "
+                f"real-space sums of {n} sampled particles extrapolated to {sy.n} "
+                f"({s:.1f} s measured)")
+
+    return {"value": sy.n / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample(n_sample, spent),
+            "single_thread": {"value": sy.n / t_one, "unit": UNIT, "cores": 1,
+                              "sample": sample(n_sample_1, spent1)}}
+
+
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -428,13 +451,7 @@ def run_ours(args):
                        "d2h_bytes_per_step": sy.n * 3 * 4 + 8 * (6 + 4) + 4,
                        "call": "rbe_set_positions(host f64) + rbe_forces(host f32 F, energies)"}
         # CPU baseline: the oracle on a bounded sample of the same workload
-        t_ext, spent = cpu_oracle_step(orc, sy, args.P, 512)
-        line["cpu_baseline"] = {"value": sy.n / t_ext, "unit": UNIT, "cores": orc.num_threads(),
-                                "kind": "oracle",
-                                "sample": "one step 0 force evaluation: full structure factor and "
-                                          "k-space forces, O(N) real-space sums of 512 sampled "
-                                          f"particles extrapolated to {sy.n} "
-                                          f"({spent:.1f} s measured)"}
+        line["cpu_baseline"] = cpu_baseline_record(orc, sy, args.P)
     h.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

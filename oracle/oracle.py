@@ -64,6 +64,8 @@ def lib():
         L.orc_nh_half.argtypes = [ct.c_int64, _f64p, _f64p, ct.c_double, ct.c_double,
                                   ct.c_double, ct.c_double, ct.c_double, _f64p]
         L.orc_num_threads.restype = ct.c_int
+        L.orc_set_num_threads.argtypes = [ct.c_int]
+        L.orc_set_num_threads.restype = None
         for name in ("orc_kdim_table", "orc_sample_k", "orc_rho", "orc_rbe_kspace",
                      "orc_ewald_kspace", "orc_real_space", "orc_cells", "orc_rbl", "orc_rbl_rows",
                      "orc_brute_coulomb", "orc_vv_drift", "orc_vv_kick", "orc_nh_half"):
@@ -87,6 +89,11 @@ def _f(x):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """Threads for later oracle calls (timing only: no result depends on it)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def philox4x32_10(ctr, key):

@@ -38,6 +38,14 @@ int orc_num_threads(void) {
 #endif
 }
 
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* ---------------------------------------------------------------------------------- */
 /* Philox4x32-10 (Salmon et al., SC'11, Sec. 4): ten rounds of two 32x32->64 products
  * with multipliers 0xD2511F53 and 0xCD9E8D57, the key bumped between rounds by the Weyl

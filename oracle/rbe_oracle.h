@@ -161,6 +161,10 @@ int orc_nh_half(int64_t N, double *v, const double *mass, double kappa, double N
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int orc_num_threads(void);
 
+/* Set the number of OpenMP threads for later calls (n >= 1; no effect without OpenMP),
+ * for timing the oracle on one core and on all of them. Results do not depend on it. */
+void orc_set_num_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif
