@@ -38,7 +38,8 @@ def _rank_main(rank, world, port, out):
 def test_two_gloo_ranks_replicas_and_max_time():
     pytest.importorskip("torch.distributed")
     port = _free_port()
-    with mp.Manager() as mgr:
+    # spawn, not fork: earlier tests may have started OpenMP threads in this process
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
