@@ -113,9 +113,12 @@ int rbe_sample_k(rbe_handle h, uint64_t step, int32_t *m_out, double *S_out);
 /* Replace the positions (N x 3, in id order) from host (on_device = 0) or device memory. */
 int rbe_set_positions(rbe_handle h, const double *pos, int on_device);
 
-/* One nonbonded force evaluation for step `step`:
- * bin + sort -> sample P modes -> structure factor -> real space (cell list or Verlet list,
- * or RBL with the mean-force correction when r_core > 0) -> k-space gather -> totals.
+/* One nonbonded force evaluation for step `step`: F_i = F_i^N (real space, Eqs. F_i,
+ * G_short and LJ over r <= r_c; or the random batch list, Eqs. Ci_Si and RBL, with the
+ * mean-force correction of Eq. F_corr when r_core > 0) + F_i^{F,*} (the random batch Ewald
+ * k-space force, Eq. F_long_RBE, on this step's modes), with the energies of Eqs.
+ * U_Coul_Fourier and U_self. Stages: bin + sort (Sec. 2.2) -> sample P modes -> structure
+ * factor -> real space -> k-space gather -> totals.
  *  F_out     N x 3 float forces in id order (nullable), in host (F_on_device = 0) or
  *            device memory
  *  energies  RBE_N_ENERGY doubles (nullable, host)
@@ -128,16 +131,20 @@ int rbe_forces(rbe_handle h, uint64_t step, float *F_out, int F_on_device, doubl
 int rbe_forces_f64(rbe_handle h, uint64_t step, double *F_out, double *energies,
                    double *virial);
 
-/* Advance nsteps velocity-Verlet steps (kick-drift, forces, kick) from the current step
- * counter, replaying one captured CUDA graph per step; asynchronous. The first call
- * computes the initial forces if none exist and captures the graph. */
+/* Advance nsteps velocity-Verlet steps (the time integrator of Sec. 2.1: kick-drift,
+ * forces as rbe_forces computes them, kick) from the current step counter, replaying one
+ * captured CUDA graph per step; asynchronous. The first call computes the initial forces
+ * if none exist and captures the graph. */
 int rbe_step(rbe_handle h, int nsteps);
 
 /* Energies and virials of the last force evaluation or Verlet step (host, nullable each;
- * RBE_N_ENERGY and RBE_N_VIRIAL doubles). Synchronises the stream. */
+ * RBE_N_ENERGY and RBE_N_VIRIAL doubles): real-space Coulomb and LJ sums, the k-space
+ * estimate of Eq. U_Coul_Fourier on the sampled modes, the self energy of Eq. U_self and
+ * the kinetic energy. Synchronises the stream. */
 int rbe_get_energies(rbe_handle h, double *energies, double *virial);
 
-/* Nose-Hoover NVT thermostat for rbe_step (a chain of one thermostat, Trotter-split
+/* Nose-Hoover NVT thermostat for rbe_step (the NVT runs of Sec. 3; a chain of one
+ * thermostat, Trotter-split
  * around each velocity-Verlet step: half step before the first half-kick and after the
  * second). Q = N_f kB T tau^2 with N_f = 3N - 3. tau <= 0 switches it off (NVE, the
  * default). kB is in the caller's energy unit per kelvin (0.0019872067 for kcal/mol).
@@ -155,12 +162,14 @@ int rbe_get_step(rbe_handle h, uint64_t *step);
  * 2^-32 grid, wrapped into [0, L)), velocities, and the raw fractional coordinates. */
 int rbe_get_state(rbe_handle h, double *pos, double *vel, uint32_t *s_frac);
 
-/* Copy the linked cells of the last force evaluation: n_cells[3] cells per axis,
+/* Copy the linked cells (Sec. 2.2) of the last force evaluation: n_cells[3] cells per axis,
  * cell_start (n_x n_y n_z + 1 entries) and sorted_ids (N ids in cell order, inside a cell
  * by (s_x, id)). Either array may be NULL (query n_cells first to size cell_start). */
 int rbe_get_cells(rbe_handle h, int32_t n_cells[3], int64_t *cell_start, int64_t *sorted_ids);
 
-/* Copy the structure factor of the last evaluation, rho (P x 2: Re, Im, FP64), and the modes. */
+/* Copy the structure factor rho(k) = sum_j q_j exp(i k . r_j) (Eq. U_Coul_Fourier) of the
+ * last evaluation, rho (P x 2: Re, Im, FP64, host), and the modes (P x 3 int32, host);
+ * either pointer may be NULL. */
 int rbe_get_rho(rbe_handle h, double *rho, int32_t *m_out);
 
 /* Per-particle neighbour counts of the last evaluation (id order, nullable):
@@ -169,7 +178,8 @@ int rbe_get_rho(rbe_handle h, double *rho, int32_t *m_out);
  * comparison of dx^2 + dy^2 + dz^2 with r^2, dx_d = (int32)(s_i - s_j) * (L_d / 2^32). */
 int rbe_get_neighbor_counts(rbe_handle h, int32_t *n_core, int32_t *n_shell);
 
-/* RBL draws of the last evaluation (N x p_rbl ids in id order; -1 where unused). */
+/* RBL draws of the last evaluation (Eq. RBL: p i.i.d. members of S_i, in S_i's canonical
+ * order; N x p_rbl ids in id order, host; -1 where unused). */
 int rbe_get_rbl_partners(rbe_handle h, int32_t *partners);
 
 /* Phases timed by the profiler (CUDA events recorded on the library's stream). */
