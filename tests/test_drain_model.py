@@ -25,9 +25,10 @@ from test_trim_model import M32, _cells, _i32
 K_WIN = 4
 
 
-def group_streams(s, box, rc=10.0, sub=2, smax=10, n_warps=120, seed=0):
+def group_streams(s, box, rc=10.0, sub=2, smax=10, n_warps=120, seed=0, width=32):
     """Yield (member rows of S, ordered candidate rows of S, S, leader coordinates) for the
-    groups of n_warps random warps, with the kernel's rows, segments and trimming."""
+    groups of n_warps random warps, with the kernel's rows, segments and trimming. Groups form
+    within windows of `width` lanes (32: the kernel; 16: half-warp groups, a design option)."""
     n = [int(math.floor(box[d] * sub / rc)) for d in range(3)]
     a = [box[d] / n[d] for d in range(3)]
     R = [int(math.ceil(rc / a[d])) for d in range(3)]
@@ -38,48 +39,53 @@ def group_streams(s, box, rc=10.0, sub=2, smax=10, n_warps=120, seed=0):
     ny, nrows = 2 * R[1] + 1, (2 * R[1] + 1) * (2 * R[2] + 1)
     rng = np.random.default_rng(seed)
     for w in rng.choice(N // 32, n_warps, replace=False):
-        remaining = list(range(32 * w, 32 * w + 32))
-        while remaining:
-            ld = remaining[0]
-            gy, gz, gx0 = cy[ld], cz[ld], cx[ld]
-            ins = [l for l in remaining if cy[l] == gy and cz[l] == gz and cx[l] - gx0 < smax]
-            remaining = [l for l in remaining if l not in ins]
-            cxlo, cxhi = min(cx[l] for l in ins), max(cx[l] for l in ins)
-            o = [int(v) for v in S[ld]]
-            fr = [[_i32(int(S[l, d]) - o[d]) for l in ins] for d in range(3)]
-            gxlo, gxhi = min(fr[0]), max(fr[0])
-            gylo, gyhi, gzlo, gzhi = min(fr[1]), max(fr[1]), min(fr[2]), max(fr[2])
-            span = cxhi - cxlo + 2 * R[0] + 1
-            runs = []
-            for r in range(nrows):
-                dz, dy = r // ny - R[2], r % ny - R[1]
-                rowbase = n[0] * ((gy + dy) % n[1] + n[1] * ((gz + dz) % n[2]))
-                if span >= n[0]:
-                    segs = [(0, n[0] - 1, 0)]
-                else:
-                    lo, hi = cxlo - R[0], cxhi + R[0]
-                    if lo < 0:
-                        segs = [(lo + n[0], n[0] - 1, -M32), (0, hi, 0)]
-                    elif hi >= n[0]:
-                        segs = [(lo, n[0] - 1, 0), (0, hi - n[0], M32)]
+        for h0 in range(32 * w, 32 * w + 32, width):
+            remaining = list(range(h0, h0 + width))
+            while remaining:
+                ld = remaining[0]
+                gy, gz, gx0 = cy[ld], cz[ld], cx[ld]
+                ins = [l for l in remaining
+                       if cy[l] == gy and cz[l] == gz and cx[l] - gx0 < smax]
+                remaining = [l for l in remaining if l not in ins]
+                cxlo, cxhi = min(cx[l] for l in ins), max(cx[l] for l in ins)
+                o = [int(v) for v in S[ld]]
+                fr = [[_i32(int(S[l, d]) - o[d]) for l in ins] for d in range(3)]
+                gxlo, gxhi = min(fr[0]), max(fr[0])
+                gylo, gyhi, gzlo, gzhi = min(fr[1]), max(fr[1]), min(fr[2]), max(fr[2])
+                span = cxhi - cxlo + 2 * R[0] + 1
+                runs = []
+                for r in range(nrows):
+                    dz, dy = r // ny - R[2], r % ny - R[1]
+                    rowbase = n[0] * ((gy + dy) % n[1] + n[1] * ((gz + dz) % n[2]))
+                    if span >= n[0]:
+                        segs = [(0, n[0] - 1, 0)]
                     else:
-                        segs = [(lo, hi, 0)]
-                wy, wz = M32 / n[1], M32 / n[2]
-                ddy = max(0.0, (gy + dy) * wy - o[1] - 2.0 - gyhi, gylo - ((gy + dy + 1) * wy - o[1] + 2.0))
-                ddz = max(0.0, (gz + dz) * wz - o[2] - 2.0 - gzhi, gzlo - ((gz + dz + 1) * wz - o[2] + 2.0))
-                rx2 = rc * rc * (1 + 1e-9) - (ddy * hd[1]) ** 2 - (ddz * hd[2]) ** 2
-                for c0, c1, sh in segs:
-                    b, ln = int(cs[rowbase + c0]), int(cs[rowbase + c1 + 1] - cs[rowbase + c0])
-                    if span < n[0]:
-                        if rx2 <= 0:
-                            continue
-                        rx = int(math.ceil(math.sqrt(rx2) / hd[0]) + 2.0)
-                        xs = S[b:b + ln, 0] + sh - o[0]  # sorted: the unwrapped coordinate
-                        u = int(np.searchsorted(xs, gxlo - rx, side="left"))
-                        v = int(np.searchsorted(xs, gxhi + rx + 1, side="left"))
-                        b, ln = b + u, v - u
-                    runs.append(np.arange(b, b + ln))
-            yield ins, np.concatenate(runs) if runs else np.zeros(0, np.int64), S, o
+                        lo, hi = cxlo - R[0], cxhi + R[0]
+                        if lo < 0:
+                            segs = [(lo + n[0], n[0] - 1, -M32), (0, hi, 0)]
+                        elif hi >= n[0]:
+                            segs = [(lo, n[0] - 1, 0), (0, hi - n[0], M32)]
+                        else:
+                            segs = [(lo, hi, 0)]
+                    wy, wz = M32 / n[1], M32 / n[2]
+                    ylo, yhi = (gy + dy) * wy - o[1] - 2.0, (gy + dy + 1) * wy - o[1] + 2.0
+                    zlo, zhi = (gz + dz) * wz - o[2] - 2.0, (gz + dz + 1) * wz - o[2] + 2.0
+                    ddy = max(0.0, ylo - gyhi, gylo - yhi)
+                    ddz = max(0.0, zlo - gzhi, gzlo - zhi)
+                    rx2 = rc * rc * (1 + 1e-9) - (ddy * hd[1]) ** 2 - (ddz * hd[2]) ** 2
+                    for c0, c1, sh in segs:
+                        b = int(cs[rowbase + c0])
+                        ln = int(cs[rowbase + c1 + 1]) - b
+                        if span < n[0]:
+                            if rx2 <= 0:
+                                continue
+                            rx = int(math.ceil(math.sqrt(rx2) / hd[0]) + 2.0)
+                            xs = S[b:b + ln, 0] + sh - o[0]  # sorted: the unwrapped coordinate
+                            u = int(np.searchsorted(xs, gxlo - rx, side="left"))
+                            v = int(np.searchsorted(xs, gxhi + rx + 1, side="left"))
+                            b, ln = b + u, v - u
+                        runs.append(np.arange(b, b + ln))
+                yield ins, np.concatenate(runs) if runs else np.zeros(0, np.int64), S, o
 
 
 def lane_hits(ins, cand, S, o, L, rc):
