@@ -25,10 +25,12 @@ from test_trim_model import M32, _cells, _i32
 K_WIN = 4
 
 
-def group_streams(s, box, rc=10.0, sub=2, smax=10, n_warps=120, seed=0, width=32):
+def group_streams(s, box, rc=10.0, sub=2, smax=10, n_warps=120, seed=0, width=32,
+                  trim=True):
     """Yield (member rows of S, ordered candidate rows of S, S, leader coordinates) for the
     groups of n_warps random warps, with the kernel's rows, segments and trimming. Groups form
-    within windows of `width` lanes (32: the kernel; 16: half-warp groups, a design option)."""
+    within windows of `width` lanes (32: the kernel; 16: half-warp groups, a design option);
+    trim=False keeps whole runs (the kernel's charged-subset Coulomb pass)."""
     n = [int(math.floor(box[d] * sub / rc)) for d in range(3)]
     a = [box[d] / n[d] for d in range(3)]
     R = [int(math.ceil(rc / a[d])) for d in range(3)]
@@ -76,7 +78,7 @@ def group_streams(s, box, rc=10.0, sub=2, smax=10, n_warps=120, seed=0, width=32
                     for c0, c1, sh in segs:
                         b = int(cs[rowbase + c0])
                         ln = int(cs[rowbase + c1 + 1]) - b
-                        if span < n[0]:
+                        if trim and span < n[0]:
                             if rx2 <= 0:
                                 continue
                             rx = int(math.ceil(math.sqrt(rx2) / hd[0]) + 2.0)
