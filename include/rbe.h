@@ -47,8 +47,10 @@ enum {
   RBE_ERR_SAMPLER = -7,     /* 64 redraws of a mode all gave k = 0 (device flag) */
   RBE_ERR_NONFINITE = -8,   /* a non-finite velocity or position update (device flag) */
   RBE_ERR_STATE = -9,       /* call not valid in this state (e.g. no forces computed yet) */
-  RBE_ERR_CAPACITY = -10    /* an RBL stencil (27 cells) held more than 6144 candidates, or a
-                               Verlet list outgrew its capacity (device flag) */
+  RBE_ERR_CAPACITY = -10    /* an RBL stencil (27 cells) held more than 6144 candidates, a
+                               Verlet list outgrew its capacity, or one 8-particle cluster of
+                               the cluster-pair kernel spanned more than L - 2 r_c in x (device
+                               flag) */
 };
 
 enum {
@@ -215,9 +217,15 @@ int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kernels_per_step);
  *                        is 1 when the mean shell size N/V * 4/3 pi (r_s^3 - r_core^3) <= p.
  *  RBE_TUNE_RBL_SPAN     random batch list only: cells in x that one warp's particle group may
  *                        span (1..14; 0 = automatic, floor(32 / particles per cell), at least 1,
- *                        at most n_x - 2). Results are bit-identical for every span. */
+ *                        at most n_x - 2). Results are bit-identical for every span.
+ *  RBE_TUNE_PAIR_CLUSTER 1 (default): the cell-list pair pass over all particles runs over
+ *                        clusters of 8 particles and evaluates each pair once (Newton's third
+ *                        law), summing forces in 64-bit fixed point (results independent of the
+ *                        order of the sums), where the box allows it (a cell width plus 2 r_c
+ *                        below L in y and z); 0: the per-particle kernel (each pair from both
+ *                        sides). Neighbour sets are the same exact ones either way. */
 enum { RBE_TUNE_PAIR_TEST16 = 0, RBE_TUNE_SF_TILE = 1, RBE_TUNE_RBL_EAGER = 2,
-       RBE_TUNE_RBL_SPAN = 3, RBE_N_TUNE = 4 };
+       RBE_TUNE_RBL_SPAN = 3, RBE_TUNE_PAIR_CLUSTER = 4, RBE_N_TUNE = 5 };
 int rbe_set_tuning(rbe_handle h, int key, int value);
 int rbe_get_tuning(rbe_handle h, int key, int *value);
 
@@ -295,8 +303,12 @@ int rbe_batch_destroy(rbe_batch b);
  * held by every GPU that loads the library until the process exits, and shared by all
  * calls on that GPU: calls that overlap on the GPU race and must be ordered by the
  * caller. The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture. Asynchronous:
- * synchronise the stream before reading rho. */
+ * (cudaGetSymbolAddress) and its SM count; make that first call before any stream capture.
+ * The looked-up address is kept for the life of the process, i.e. of the device's primary
+ * context: after cudaDeviceReset, or from a thread bound to another (non-primary) context,
+ * it is not valid. All pointers and cuda_stream must belong to the device that is current
+ * on the calling thread: the array and the launches are taken from that device.
+ * Asynchronous: synchronise the stream before reading rho. */
 int rbe_structure_factor_noalloc(const uint32_t *s, const float *q, int64_t N,
                                  const int32_t *m, int P, double *rho, void *cuda_stream);
 

@@ -21,7 +21,7 @@ RBE_OK = 0
 PRECISION = {"fp32_comp": 0, "fp32": 1, "fp64": 2}
 ENERGY_KEYS = ("real", "lj", "kspace", "self", "total", "kinetic")
 VIRIAL_KEYS = ("real", "lj", "kspace", "total")
-TUNABLES = {"pair_test16": 0, "sf_tile": 1, "rbl_eager": 2, "rbl_span": 3}
+TUNABLES = {"pair_test16": 0, "sf_tile": 1, "rbl_eager": 2, "rbl_span": 3, "pair_cluster": 4}
 PHASES = ("kick_drift", "bin", "sample", "sf", "list", "pair", "pair2", "gather", "tail")
 
 

@@ -1,0 +1,757 @@
+// k_cpair.cu -- real-space pair forces over clusters of particles, each pair evaluated once
+// (Newton's third law), for the cell-list real space (Eqs. F_i, G_short, LJ):
+//
+//   F_i += sum_{j != i, r_ij <= r_c} (C q_i q_j G(r) + G_LJ(r)) (r_i - r_j),   F_j -= the same.
+//
+// Clusters. Particles are sorted by (cell, s_x, id) with cells of r_c / sub, so each row of
+// cells (c_y, c_z) holds its particles in ascending s_x. A cluster is 8 consecutive
+// particles of a row (the last cluster of a row may hold fewer) and a super-cluster is up
+// to NC consecutive clusters of a row: one warp's work. Global cluster indices run over the
+// rows in order (cl_base per row), and so do the super-clusters (sc_base per row).
+//
+// Half list. The cluster pair (I, J) is evaluated once, by the super-cluster that holds I,
+// when I <= J (global index) and the bounding boxes of I and J are within r_c of each
+// other. Every particle pair within r_c lies in one such pair of clusters, or inside one
+// cluster (I = J: then only particle a with particle b > a of the cluster).
+//
+// Lanes. Lane (h, a) = (lane / 8, lane % 8) holds particle a of every i-cluster of the
+// super-cluster (coordinates and force in registers) and particles h and h + 4 of the
+// j-cluster being visited, so one visit evaluates the 8 x 8 pairs of every i-cluster the
+// visit's mask names, two per lane. The reaction on j is summed over the 8 lanes that
+// share h by shuffles, once per visit, and added to j's force.
+//
+// Forces are summed in 64-bit fixed point by integer atomics. Integer sums do not depend on
+// their order, so the forces are the same run to run; a final pass converts them to
+// floating point. Energies and virials are per-block partial sums, as in the other kernels.
+//
+// Frame. A super-cluster's coordinates are the exact integer offsets of its particles from
+// the centre of its bounding box, converted to FP32 (kept as integers in the FP64 form).
+// The difference of two offsets is the minimum-image displacement of a pair within r_c as
+// long as the super-cluster's extent plus 2 r_c stays below L on every axis: the host
+// checks y and z (a cell width), the kernel splits a super-cluster whose x extent is
+// larger into groups of clusters that fit. The cutoff decision is exact: FP32 outside a
+// band around r_c^2 that covers the rounding of the frame coordinates, and the oracle's
+// FP64 expression of the integer displacement inside it (a rare branch per visit whose
+// pairs are added by atomics); the FP64 form always takes the FP64 expression.
+#include <climits>
+#include <cmath>
+
+#include "pair_common.cuh"
+
+namespace rbe {
+
+constexpr int kClSize = 8;              // particles per cluster
+constexpr int kCpMaxRows = 49;          // (2R+1)^2 stencil rows for R <= 3
+constexpr int kCpMaxSeg = 2 * kCpMaxRows;
+
+struct ClusterArgs {
+  PairSet set;                 // full sorted set
+  Grid grid;
+  PairConst pc;
+  float ljA, ljB, ljA12, ljB6;
+  double ljAd, ljBd, ljA12d, ljB6d;
+  const LJTable *table;        // device copy, multi-type only
+  const int32_t *cl_base;      // nrows + 1: first global cluster of each row
+  const int32_t *sc_base;      // nrows + 1: first super-cluster of each row
+  const uint4 *cl_lo, *cl_hi;  // per cluster: (min s_x, s_y, s_z, first particle), (max..., count)
+  int nrows;
+  long long *facc;             // 3 x N fixed-point forces (x block, y, z)
+  int64_t N;
+  float fscale;                // fixed-point scale (FP32 forms)
+  double fscale_d;             // (FP64 form)
+  double *epart;               // per-block partials (NQ_PAIR doubles)
+  int32_t *nbr;                // neighbour counts (sorted order, zeroed before), nullable
+  int comp;                    // Kahan sums for the Coulomb energy and virial
+  uint32_t xlim;               // largest x extent of a cluster group the frame allows
+  float bb2;                   // bounding-box test: squared gap <= bb2 (r_c^2, widened)
+  int *err;
+};
+
+// ---------------------------------------------------------------------------------------
+// Per-step cluster tables
+
+// One block: clusters and super-clusters of every row, as exclusive prefix sums.
+__global__ void __launch_bounds__(1024) cluster_rows_kernel(const int32_t *__restrict__ cell_start,
+                                                            int n0, int nrows, int nc_sc,
+                                                            int32_t *__restrict__ cl_base,
+                                                            int32_t *__restrict__ sc_base) {
+  __shared__ int2 ws[32];
+  const unsigned FULL = 0xffffffffu;
+  const int t = threadIdx.x, ln = t & 31;
+  const int per = (nrows + 1023) / 1024;
+  const int r0 = min(nrows, t * per), r1 = min(nrows, r0 + per);
+  int cl = 0, sc = 0;
+  for (int r = r0; r < r1; ++r) {
+    const int n = cell_start[(int64_t)(r + 1) * n0] - cell_start[(int64_t)r * n0];
+    const int k = (n + kClSize - 1) / kClSize;
+    cl += k;
+    sc += (k + nc_sc - 1) / nc_sc;
+  }
+  int icl = cl, isc = sc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(FULL, icl, o), v = __shfl_up_sync(FULL, isc, o);
+    if (ln >= o) { icl += u; isc += v; }
+  }
+  if (ln == 31) ws[t >> 5] = make_int2(icl, isc);
+  __syncthreads();
+  if (t < 32) {
+    const int2 v = ws[t];
+    int u = v.x, w = v.y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int p = __shfl_up_sync(FULL, u, o), q = __shfl_up_sync(FULL, w, o);
+      if (ln >= o) { u += p; w += q; }
+    }
+    ws[t] = make_int2(u - v.x, w - v.y);
+  }
+  __syncthreads();
+  int bc = ws[t >> 5].x + icl - cl, bs = ws[t >> 5].y + isc - sc;
+  for (int r = r0; r < r1; ++r) {
+    const int n = cell_start[(int64_t)(r + 1) * n0] - cell_start[(int64_t)r * n0];
+    const int k = (n + kClSize - 1) / kClSize;
+    cl_base[r] = bc;
+    sc_base[r] = bs;
+    bc += k;
+    bs += (k + nc_sc - 1) / nc_sc;
+  }
+  if (t == 1023) {
+    cl_base[nrows] = bc;
+    sc_base[nrows] = bs;
+  }
+}
+
+// Largest r in [0, nrows) with base[r] <= g (base is non-decreasing; g < base[nrows]).
+__device__ __forceinline__ int row_of(const int32_t *__restrict__ base, int nrows, int g) {
+  int lo = 0, hi = nrows - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Bounding box (integer fractional coordinates), first particle and count of every cluster.
+__global__ void __launch_bounds__(256) cluster_bounds_kernel(
+    const uint32_t *__restrict__ sx, const uint32_t *__restrict__ sy,
+    const uint32_t *__restrict__ sz, const int32_t *__restrict__ cell_start, int n0, int nrows,
+    const int32_t *__restrict__ cl_base, int64_t cap, uint4 *__restrict__ lo,
+    uint4 *__restrict__ hi) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cap || g >= cl_base[nrows]) return;
+  const int r = row_of(cl_base, nrows, (int)g);
+  const int ps = cell_start[(int64_t)r * n0], pe = cell_start[(int64_t)(r + 1) * n0];
+  const int b = ps + (int)(g - cl_base[r]) * kClSize;
+  const int n = min(kClSize, pe - b);
+  uint32_t x0 = 0xffffffffu, y0 = 0xffffffffu, z0 = 0xffffffffu, x1 = 0u, y1 = 0u, z1 = 0u;
+  for (int k = 0; k < n; ++k) {
+    const uint32_t x = sx[b + k], y = sy[b + k], z = sz[b + k];
+    x0 = min(x0, x); x1 = max(x1, x);
+    y0 = min(y0, y); y1 = max(y1, y);
+    z0 = min(z0, z); z1 = max(z1, z);
+  }
+  lo[g] = make_uint4(x0, y0, z0, (uint32_t)b);
+  hi[g] = make_uint4(x1, y1, z1, (uint32_t)n);
+}
+
+// F = fixed-point sums / scale (overwriting), and the sums cleared for the next pass.
+template <typename real>
+__global__ void __launch_bounds__(256) cpair_finalize_kernel(long long *__restrict__ facc,
+                                                             real *__restrict__ F, int64_t n3,
+                                                             double inv_scale) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n3) return;
+  const long long v = facc[k];
+  facc[k] = 0;
+  F[k] = (real)((double)v * inv_scale);
+}
+
+// ---------------------------------------------------------------------------------------
+// Pair evaluation
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Add v * scale to a fixed-point sum (round to nearest); an out-of-range value sets the
+// non-finite flag instead (its sum would wrap).
+__device__ __forceinline__ void fx_add(long long *p, float v, float scale, int *err) {
+  const float s = v * scale;
+  if (fabsf(s) < 4.0e18f) atomicAdd(reinterpret_cast<unsigned long long *>(p),
+                                    (unsigned long long)__float2ll_rn(s));
+  else atomicOr(err, ERRBIT_NONFINITE);
+}
+__device__ __forceinline__ void fx_add(long long *p, double v, double scale, int *err) {
+  const double s = v * scale;
+  if (fabs(s) < 4.0e18) atomicAdd(reinterpret_cast<unsigned long long *>(p),
+                                  (unsigned long long)__double2ll_rn(s));
+  else atomicOr(err, ERRBIT_NONFINITE);
+}
+
+template <typename real>
+struct CpAcc {
+  real u0, u1;   // single type: sum r^-12, sum r^-6; several types: U_LJ, W_LJ
+  real uc, wc, cuc, cwc;  // Coulomb energy and virial (Kahan compensations)
+};
+
+// LJ and Coulomb terms of one pair at squared distance r2 inside the cutoff (1/r^2 = 0 and
+// qq = 0 give exact zeros); returns the force factor g (F_i += g (r_i - r_j)).
+template <typename real, bool COUL, bool MULTI>
+__device__ __forceinline__ real cp_terms(const ClusterArgs &a, bool in, real r2, real ir2,
+                                         real qi, real qj, int ti, int tj, CpAcc<real> &acc) {
+  real g;
+  const real ir6 = ir2 * ir2 * ir2;
+  if (MULTI) {
+    const LJTable *tab = a.table;
+    const int pt = ti * tab->nt + tj;
+    real A, B, A12, B6;
+    if (sizeof(real) == 8) { A = (real)tab->Ad[pt]; B = (real)tab->Bd[pt]; A12 = (real)tab->A12d[pt]; B6 = (real)tab->B6d[pt]; }
+    else { A = (real)tab->A[pt]; B = (real)tab->B[pt]; A12 = (real)tab->A12[pt]; B6 = (real)tab->B6[pt]; }
+    const real w = ir6 * (A12 * ir6 - B6);
+    g = w * ir2;
+    acc.u0 += ir6 * (A * ir6 - B);
+    acc.u1 += w;
+  } else {
+    const real A12 = sizeof(real) == 8 ? (real)a.ljA12d : (real)a.ljA12;
+    const real B6 = sizeof(real) == 8 ? (real)a.ljB6d : (real)a.ljB6;
+    g = ir6 * ir2 * (A12 * ir6 - B6);
+    acc.u0 += ir6 * ir6;
+    acc.u1 += ir6;
+  }
+  if (COUL) {
+    const real qq = qi * qj;
+    if (in && qq != (real)0) {
+      const PairConst &pc = a.pc;
+      real r, rinv, erfcv, expv;
+      if (sizeof(real) == 8) {
+        r = (real)sqrt((double)r2);
+        rinv = (real)1 / r;
+        erfcv = (real)erfc(pc.sqrt_alpha_d * (double)r);
+        expv = (real)exp(-pc.alpha_d * (double)r2);
+      } else {
+        rinv = (real)rsqrtf((float)r2);
+        r = r2 * rinv;
+        erfcv = (real)erfcf(pc.sqrt_alpha * (float)r);
+        expv = (real)expf(-pc.alpha * (float)r2);
+      }
+      const real Cqq = (sizeof(real) == 8 ? (real)pc.C_d : (real)pc.C) * qq;
+      const real tsp = sizeof(real) == 8 ? (real)pc.two_sqrt_alpha_over_sqrt_pi_d
+                                         : (real)pc.two_sqrt_alpha_over_sqrt_pi;
+      const real rinv2 = rinv * rinv;
+      const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
+      g += gc;
+      if (a.comp) {
+        kahan_add(acc.uc, acc.cuc, Cqq * erfcv * rinv);
+        kahan_add(acc.wc, acc.cwc, gc * r2);
+      } else {
+        acc.uc += Cqq * erfcv * rinv;
+        acc.wc += gc * r2;
+      }
+    }
+  }
+  return g;
+}
+
+// ---------------------------------------------------------------------------------------
+// The kernel: one warp per super-cluster.
+
+template <typename real, bool COUL, bool MULTI, bool COUNT>
+__global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kernel(const ClusterArgs a) {
+  constexpr bool F64 = sizeof(real) == 8;
+  constexpr int NC = F64 ? 4 : 8;          // clusters per super-cluster
+  constexpr int NP = NC * kClSize;         // particles per super-cluster
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ uint4 si[NP];                 // s_x, s_y, s_z, charge bits
+  __shared__ int32_t sti[MULTI ? NP : 1];
+  __shared__ float4 ibl[NC], ibh[NC];      // i-cluster boxes in frame coordinates
+  __shared__ int32_t seg_beg[kCpMaxSeg], seg_pre[kCpMaxSeg + 1];
+  const int lane = threadIdx.x, a8 = lane & 7, hh = lane >> 3;
+  const int w = blockIdx.x;
+  const PairConst &pc = a.pc;
+  const int64_t N = a.N;
+  CpAcc<real> acc;
+  acc.u0 = acc.u1 = acc.uc = acc.wc = acc.cuc = acc.cwc = (real)0;
+  const int nrows = a.nrows;
+  if (w < a.sc_base[nrows]) {
+    const int r = row_of(a.sc_base, nrows, w);
+    const int n0 = a.grid.n[0], n1 = a.grid.n[1], n2 = a.grid.n[2];
+    const int ps = a.set.cell_start[(int64_t)r * n0], pe = a.set.cell_start[(int64_t)(r + 1) * n0];
+    const int ksc = w - a.sc_base[r];
+    const int g0 = a.cl_base[r] + ksc * NC;
+    const int nc = min(NC, a.cl_base[r + 1] - a.cl_base[r] - ksc * NC);
+    const int p0 = ps + ksc * NP;
+    const int np = min(NP, pe - p0);
+    const int cy = r % n1, cz = r / n1;
+    for (int t = lane; t < NP; t += 32) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (t < np) {
+        const int p = p0 + t;
+        v = make_uint4(a.set.sx[p], a.set.sy[p], a.set.sz[p],
+                       COUL ? __float_as_uint(a.set.qf[p]) : 0u);
+        if (MULTI) sti[t] = a.set.type[p];
+      }
+      si[t] = v;
+    }
+    __syncwarp();
+    // Groups of consecutive clusters whose x extent the frame allows (normally one group).
+    int cb = 0;
+    while (cb < nc) {
+      const uint32_t xfirst = si[kClSize * cb].x;
+      int ce = cb + 1;
+      while (ce < nc && si[min(np, kClSize * (ce + 1)) - 1].x - xfirst <= a.xlim) ++ce;
+      if (si[min(np, kClSize * ce) - 1].x - xfirst > a.xlim) {
+        if (lane == 0) atomicOr(a.err, ERRBIT_CAPACITY);  // one cluster wider than the frame
+        break;
+      }
+      const int q0 = kClSize * cb, q1 = min(np, kClSize * ce);
+      // group box and frame centre (no wrap inside a row: x ascending, y and z in one cell)
+      uint32_t ylo = 0xffffffffu, yhi = 0u, zlo = 0xffffffffu, zhi = 0u;
+      for (int t = q0 + lane; t < q1; t += 32) {
+        const uint4 v = si[t];
+        ylo = min(ylo, v.y); yhi = max(yhi, v.y);
+        zlo = min(zlo, v.z); zhi = max(zhi, v.z);
+      }
+      ylo = __reduce_min_sync(FULL, ylo); yhi = __reduce_max_sync(FULL, yhi);
+      zlo = __reduce_min_sync(FULL, zlo); zhi = __reduce_max_sync(FULL, zhi);
+      const uint32_t xlo = si[q0].x, xhi = si[q1 - 1].x;
+      const uint32_t rx = xlo + ((xhi - xlo) >> 1), ry = ylo + ((yhi - ylo) >> 1),
+                     rz = zlo + ((zhi - zlo) >> 1);
+      // i particles of this lane: particle a8 of each cluster of the group
+      real xi[NC], yi[NC], zi[NC], fxi[NC], fyi[NC], fzi[NC], qi[NC];
+      int oxi[NC], oyi[NC], ozi[NC], ti[NC], cnti[NC];
+      bool vi[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int t = kClSize * c + a8;
+        const bool v = c >= cb && c < ce && t < np;
+        vi[c] = v;
+        const uint4 s = si[t];
+        oxi[c] = (int)(s.x - rx); oyi[c] = (int)(s.y - ry); ozi[c] = (int)(s.z - rz);
+        if (!F64) {
+          xi[c] = v ? (real)((float)oxi[c] * pc.h[0]) : (real)3e18f;
+          yi[c] = v ? (real)((float)oyi[c] * pc.h[1]) : (real)3e18f;
+          zi[c] = v ? (real)((float)ozi[c] * pc.h[2]) : (real)3e18f;
+        } else {
+          xi[c] = yi[c] = zi[c] = (real)0;  // the FP64 form works on the integer offsets
+        }
+        qi[c] = COUL ? (real)__uint_as_float(s.w) : (real)0;
+        if (COUL && F64 && v) qi[c] = (real)a.set.qd[p0 + t];
+        ti[c] = MULTI ? sti[t] : 0;
+        fxi[c] = fyi[c] = fzi[c] = (real)0;
+        cnti[c] = 0;
+      }
+      // i-cluster boxes in the frame (lanes cb..ce-1)
+      if (lane < NC) {
+        float4 lo4 = make_float4(3e18f, 3e18f, 3e18f, 0.f), hi4 = make_float4(3e18f, 3e18f, 3e18f, 0.f);
+        if (lane >= cb && lane < ce) {
+          const uint4 l = a.cl_lo[g0 + lane], u = a.cl_hi[g0 + lane];
+          lo4 = make_float4((float)(int)(l.x - rx) * pc.h[0], (float)(int)(l.y - ry) * pc.h[1],
+                            (float)(int)(l.z - rz) * pc.h[2], 0.f);
+          hi4 = make_float4((float)(int)(u.x - rx) * pc.h[0], (float)(int)(u.y - ry) * pc.h[1],
+                            (float)(int)(u.z - rz) * pc.h[2], 0.f);
+        }
+        ibl[lane] = lo4;
+        ibh[lane] = hi4;
+      }
+      // Candidate j-clusters: for each stencil row (dy, dz), the clusters holding the row's
+      // particles within the group's x-reach (one lane per row; a row wraps into at most
+      // two parts), from the group's first global cluster on; a warp scan gives offsets.
+      const int R1 = a.grid.R[1], R2 = a.grid.R[2];
+      const int ny = 2 * R1 + 1, nrst = ny * (2 * R2 + 1);
+      const int gxlo = (int)(xlo - rx), gxhi = (int)(xhi - rx);
+      const int gylo = (int)(ylo - ry), gyhi = (int)(yhi - ry);
+      const int gzlo = (int)(zlo - rz), gzhi = (int)(zhi - rz);
+      const int jmin = g0 + cb;
+      int carry = 0;
+      for (int rb = 0; rb < nrst; rb += 32) {
+        const int t = rb + lane;
+        int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
+        if (t < nrst) {
+          const int dz = t / ny - R2, dy = t % ny - R1;
+          const int ryw = ((cy + dy) % n1 + n1) % n1, rzw = ((cz + dz) % n2 + n2) % n2;
+          const int r2i = ryw + n1 * rzw;
+          const int qs = a.set.cell_start[(int64_t)r2i * n0];
+          const int qe = a.set.cell_start[(int64_t)(r2i + 1) * n0];
+          if (qe > qs) {
+            // the row's y and z extent in frame units (unwrapped, widened by 2 units), its
+            // distance from the group's box, and the x-reach that is left
+            const int64_t W32 = (int64_t)1 << 32;
+            const int64_t y0 = (int64_t)(cy + dy) * W32 / n1 - (int64_t)ry - 2;
+            const int64_t y1 = (int64_t)(cy + dy + 1) * W32 / n1 - (int64_t)ry + 2;
+            const int64_t z0 = (int64_t)(cz + dz) * W32 / n2 - (int64_t)rz - 2;
+            const int64_t z1 = (int64_t)(cz + dz + 1) * W32 / n2 - (int64_t)rz + 2;
+            const int64_t ey = max((int64_t)0, max(y0 - gyhi, (int64_t)gylo - y1));
+            const int64_t ez = max((int64_t)0, max(z0 - gzhi, (int64_t)gzlo - z1));
+            const float dyl = (float)ey * pc.h[1], dzl = (float)ez * pc.h[2];
+            const float rx2 = a.bb2 - dyl * dyl - dzl * dzl;
+            if (rx2 > 0.f) {
+              const int64_t reach = (int64_t)(sqrtf(rx2) * (1.0f + 1e-5f) / pc.h[0]) + 4;
+              const int64_t X0 = (int64_t)rx + gxlo - reach, X1 = (int64_t)rx + gxhi + reach;
+              const int64_t W = (int64_t)1 << 32;
+              // first particle of [qs, qe) with s_x >= key (rows are sorted by s_x)
+              auto first_ge = [&](int64_t key) {
+                int lo = qs, hi = qe;
+                while (lo < hi) {
+                  const int mid = (lo + hi) >> 1;
+                  if ((int64_t)a.set.sx[mid] < key) lo = mid + 1;
+                  else hi = mid;
+                }
+                return lo;
+              };
+              int uH = qs, vH = qs, uL = qs, vL = qs;  // particle ranges: high part, low part
+              if (X1 - X0 + 1 >= W) { uL = qs; vL = qe; }
+              else if (X0 < 0) { uH = first_ge(X0 + W); vH = qe; uL = qs; vL = first_ge(X1 + 1); }
+              else if (X1 >= W) { uH = first_ge(X0); vH = qe; uL = qs; vL = first_ge(X1 - W + 1); }
+              else { uL = first_ge(X0); vL = first_ge(X1 + 1); }
+              // to cluster ranges of the row (merged when both parts reach one cluster)
+              int kL0 = 0, kL1 = -1, kH0 = 0, kH1 = -1;
+              if (vL > uL) { kL0 = (uL - qs) / kClSize; kL1 = (vL - 1 - qs) / kClSize; }
+              if (vH > uH) { kH0 = (uH - qs) / kClSize; kH1 = (vH - 1 - qs) / kClSize; }
+              if (kL1 >= kL0 && kH1 >= kH0 && kL1 >= kH0 - 1) { kL1 = max(kL1, kH1); kH1 = kH0 - 1; }
+              const int base = a.cl_base[r2i];
+              if (kL1 >= kL0) {
+                const int j0 = max(base + kL0, jmin), j1 = base + kL1;
+                if (j1 >= j0) { b0 = j0; l0 = j1 - j0 + 1; }
+              }
+              if (kH1 >= kH0) {
+                const int j0 = max(base + kH0, jmin), j1 = base + kH1;
+                if (j1 >= j0) { b1 = j0; l1 = j1 - j0 + 1; }
+              }
+            }
+          }
+        }
+        const int tot = l0 + l1;
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int excl = carry + incl - tot;
+        if (t < nrst) {
+          seg_beg[2 * t] = b0;
+          seg_pre[2 * t] = excl;
+          seg_beg[2 * t + 1] = b1;
+          seg_pre[2 * t + 1] = excl + l0;
+        }
+        carry += __shfl_sync(FULL, incl, 31);
+      }
+      if (lane == 0) seg_pre[2 * nrst] = carry;
+      __syncwarp();
+      const int T = carry;
+      // Candidates in chunks of 32, one per lane: the box test against every i-cluster of
+      // the group gives a mask; the warp then visits each candidate with a mask.
+      int sg = 0;
+      for (int base = 0; base < T; base += 32) {
+        const int cc = base + lane;
+        int s = sg, J = 0, jb = 0, jn = 0;
+        uint32_t msk = 0u;
+        if (cc < T) {
+          while (seg_pre[s + 1] <= cc) ++s;
+          J = seg_beg[s] + (cc - seg_pre[s]);
+          const uint4 l = a.cl_lo[J], u = a.cl_hi[J];
+          jb = (int)l.w;
+          jn = (int)u.w;
+          const float jx0 = (float)(int)(l.x - rx) * pc.h[0], jx1 = (float)(int)(u.x - rx) * pc.h[0];
+          const float jy0 = (float)(int)(l.y - ry) * pc.h[1], jy1 = (float)(int)(u.y - ry) * pc.h[1];
+          const float jz0 = (float)(int)(l.z - rz) * pc.h[2], jz1 = (float)(int)(u.z - rz) * pc.h[2];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const float4 lo4 = ibl[c], hi4 = ibh[c];
+            const float gx = fmaxf(0.f, fmaxf(jx0 - hi4.x, lo4.x - jx1));
+            const float gy = fmaxf(0.f, fmaxf(jy0 - hi4.y, lo4.y - jy1));
+            const float gz = fmaxf(0.f, fmaxf(jz0 - hi4.z, lo4.z - jz1));
+            const bool hit = c >= cb && c < ce && J >= g0 + c &&
+                             fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= a.bb2;
+            msk |= hit ? (1u << c) : 0u;
+          }
+        }
+        sg = __shfl_sync(FULL, s, 31);
+        unsigned vis = __ballot_sync(FULL, msk != 0u);
+        while (vis) {
+          const int t0 = __ffs(vis) - 1;
+          vis &= vis - 1u;
+          const int Jv = __shfl_sync(FULL, J, t0);
+          const uint32_t M = __shfl_sync(FULL, msk, t0);
+          const int vb = __shfl_sync(FULL, jb, t0), vn = __shfl_sync(FULL, jn, t0);
+          const int cdiag = Jv - g0;  // the visited cluster's place in the super-cluster
+          // this lane's j particles: h and h + 4 of the cluster
+          real xj[2], yj[2], zj[2], qj[2], fxj[2], fyj[2], fzj[2];
+          int oxj[2], oyj[2], ozj[2], tj[2], cntj[2];
+          bool vj[2];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int t = hh + 4 * k;
+            vj[k] = t < vn;
+            const int p = vb + (vj[k] ? t : 0);
+            oxj[k] = (int)(a.set.sx[p] - rx);
+            oyj[k] = (int)(a.set.sy[p] - ry);
+            ozj[k] = (int)(a.set.sz[p] - rz);
+            if (!F64) {
+              xj[k] = vj[k] ? (real)((float)oxj[k] * pc.h[0]) : (real)-3e18f;
+              yj[k] = vj[k] ? (real)((float)oyj[k] * pc.h[1]) : (real)-3e18f;
+              zj[k] = vj[k] ? (real)((float)ozj[k] * pc.h[2]) : (real)-3e18f;
+            } else {
+              xj[k] = yj[k] = zj[k] = (real)0;
+            }
+            qj[k] = (real)0;
+            if (COUL) qj[k] = F64 ? (real)a.set.qd[p] : (real)a.set.qf[p];
+            tj[k] = MULTI ? a.set.type[p] : 0;
+            fxj[k] = fyj[k] = fzj[k] = (real)0;
+            cntj[k] = 0;
+          }
+          bool band = false;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if ((M >> c) & 1u) {
+#pragma unroll
+              for (int k = 0; k < 2; ++k) {
+                const bool ok = c != cdiag || a8 < hh + 4 * k;
+                real dx, dy, dz, r2, ir2;
+                bool in;
+                if (F64) {
+                  // the offsets' difference (mod 2^32) is the exact minimum-image displacement
+                  const int dsx = (int)((uint32_t)oxi[c] - (uint32_t)oxj[k]);
+                  const int dsy = (int)((uint32_t)oyi[c] - (uint32_t)oyj[k]);
+                  const int dsz = (int)((uint32_t)ozi[c] - (uint32_t)ozj[k]);
+                  dx = (real)__dmul_rn((double)dsx, pc.hd[0]);
+                  dy = (real)__dmul_rn((double)dsy, pc.hd[1]);
+                  dz = (real)__dmul_rn((double)dsz, pc.hd[2]);
+                  r2 = (real)__dadd_rn(__dadd_rn(__dmul_rn((double)dx, (double)dx),
+                                                 __dmul_rn((double)dy, (double)dy)),
+                                       __dmul_rn((double)dz, (double)dz));
+                  in = ok && vi[c] && vj[k] && (double)r2 <= pc.rc2d;
+                  ir2 = in ? (real)(1.0 / (double)r2) : (real)0;
+                } else {
+                  dx = xi[c] - xj[k];
+                  dy = yi[c] - yj[k];
+                  dz = zi[c] - zj[k];
+                  r2 = (real)fmaf((float)dx, (float)dx, fmaf((float)dy, (float)dy, (float)(dz * dz)));
+                  in = ok && (float)r2 < pc.rc2_lo;
+                  band |= ok && (float)r2 >= pc.rc2_lo && (float)r2 <= pc.rc2_hi;
+                  ir2 = in ? (real)rcp_approx((float)r2) : (real)0;
+                }
+                const real g = cp_terms<real, COUL, MULTI>(a, in, r2, ir2, qi[c], qj[k], ti[c],
+                                                           tj[k], acc);
+                fxi[c] += g * dx; fyi[c] += g * dy; fzi[c] += g * dz;
+                fxj[k] -= g * dx; fyj[k] -= g * dy; fzj[k] -= g * dz;
+                if (COUNT) { cnti[c] += in ? 1 : 0; cntj[k] += in ? 1 : 0; }
+              }
+            }
+          }
+          // Band pairs (FP32 forms): the exact decision; a pair inside is added by atomics.
+          if (!F64 && __any_sync(FULL, band)) {
+            for (int c = cb; c < ce; ++c) {
+              if (!((M >> c) & 1u)) continue;
+              const int t = kClSize * c + a8;
+              if (t >= np) continue;
+              const uint4 s = si[t];
+              const float x0 = (float)(int)(s.x - rx) * pc.h[0];
+              const float y0 = (float)(int)(s.y - ry) * pc.h[1];
+              const float z0 = (float)(int)(s.z - rz) * pc.h[2];
+              for (int k = 0; k < 2; ++k) {
+                if (!vj[k] || !(c != cdiag || a8 < hh + 4 * k)) continue;
+                const float dx = x0 - (float)xj[k], dy = y0 - (float)yj[k], dz = z0 - (float)zj[k];
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (!(r2 >= pc.rc2_lo && r2 <= pc.rc2_hi)) continue;
+                const int pj = vb + hh + 4 * k;
+                const int dsx = (int)(s.x - a.set.sx[pj]), dsy = (int)(s.y - a.set.sy[pj]),
+                          dsz = (int)(s.z - a.set.sz[pj]);
+                if (!(exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d)) continue;
+                const real qis = COUL ? (real)__uint_as_float(s.w) : (real)0;
+                const real g = cp_terms<real, COUL, MULTI>(a, true, (real)r2, (real)rcp_approx(r2),
+                                                           qis, qj[k], MULTI ? sti[t] : 0, tj[k],
+                                                           acc);
+                const int pi = p0 + t;
+                fx_add(a.facc + pi, (float)(g * dx), a.fscale, a.err);
+                fx_add(a.facc + N + pi, (float)(g * dy), a.fscale, a.err);
+                fx_add(a.facc + 2 * N + pi, (float)(g * dz), a.fscale, a.err);
+                fx_add(a.facc + pj, (float)(-g * dx), a.fscale, a.err);
+                fx_add(a.facc + N + pj, (float)(-g * dy), a.fscale, a.err);
+                fx_add(a.facc + 2 * N + pj, (float)(-g * dz), a.fscale, a.err);
+                if (COUNT) { atomicAdd(a.nbr + pi, 1); atomicAdd(a.nbr + pj, 1); }
+              }
+            }
+          }
+          // reaction on the visited cluster: sum over the 8 lanes sharing h, then lane a8 < 6
+          // adds component a8 % 3 of particle h + 4 (a8 / 3)
+          real v6[6] = {fxj[0], fyj[0], fzj[0], fxj[1], fyj[1], fzj[1]};
+#pragma unroll
+          for (int e = 0; e < 6; ++e) {
+            v6[e] += __shfl_xor_sync(FULL, v6[e], 1);
+            v6[e] += __shfl_xor_sync(FULL, v6[e], 2);
+            v6[e] += __shfl_xor_sync(FULL, v6[e], 4);
+          }
+          if (a8 < 6) {
+            const int k = a8 / 3, d = a8 - 3 * k;
+            real v = v6[0];
+#pragma unroll
+            for (int e = 1; e < 6; ++e) v = (a8 == e) ? v6[e] : v;
+            if (vj[k]) {
+              if (F64) fx_add(a.facc + (int64_t)d * N + vb + hh + 4 * k, (double)v, a.fscale_d, a.err);
+              else fx_add(a.facc + (int64_t)d * N + vb + hh + 4 * k, (float)v, a.fscale, a.err);
+            }
+          }
+          if (COUNT) {
+            const unsigned gm = 0xffu << (8 * hh);
+            const int c0 = __reduce_add_sync(gm, cntj[0]);
+            const int c1 = __reduce_add_sync(gm, cntj[1]);
+            if (a8 == 0) {
+              if (vj[0] && c0) atomicAdd(a.nbr + vb + hh, c0);
+              if (vj[1] && c1) atomicAdd(a.nbr + vb + hh + 4, c1);
+            }
+          }
+        }
+      }
+      // i forces: sum over the four lanes sharing a8, then lane (h, a8) adds clusters c with
+      // c % 4 == h
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        fxi[c] += __shfl_xor_sync(FULL, fxi[c], 8); fxi[c] += __shfl_xor_sync(FULL, fxi[c], 16);
+        fyi[c] += __shfl_xor_sync(FULL, fyi[c], 8); fyi[c] += __shfl_xor_sync(FULL, fyi[c], 16);
+        fzi[c] += __shfl_xor_sync(FULL, fzi[c], 8); fzi[c] += __shfl_xor_sync(FULL, fzi[c], 16);
+        if (COUNT) {
+          cnti[c] += __shfl_xor_sync(FULL, cnti[c], 8);
+          cnti[c] += __shfl_xor_sync(FULL, cnti[c], 16);
+        }
+        const int t = kClSize * c + a8;
+        if ((c & 3) == hh && c >= cb && c < ce && t < np) {
+          const int64_t pi = p0 + t;
+          if (F64) {
+            fx_add(a.facc + pi, (double)fxi[c], a.fscale_d, a.err);
+            fx_add(a.facc + N + pi, (double)fyi[c], a.fscale_d, a.err);
+            fx_add(a.facc + 2 * N + pi, (double)fzi[c], a.fscale_d, a.err);
+          } else {
+            fx_add(a.facc + pi, (float)fxi[c], a.fscale, a.err);
+            fx_add(a.facc + N + pi, (float)fyi[c], a.fscale, a.err);
+            fx_add(a.facc + 2 * N + pi, (float)fzi[c], a.fscale, a.err);
+          }
+          if (COUNT && cnti[c]) atomicAdd(a.nbr + pi, cnti[c]);
+        }
+      }
+      __syncwarp();
+      cb = ce;
+    }
+  }
+  // block partials of the energies and virials (each pair counted once)
+  double ulj, wlj;
+  if (MULTI) {
+    ulj = (double)acc.u0;
+    wlj = (double)acc.u1;
+  } else {
+    const double A = F64 ? a.ljAd : (double)a.ljA, B = F64 ? a.ljBd : (double)a.ljB;
+    ulj = A * (double)acc.u0 - B * (double)acc.u1;
+    wlj = 12.0 * A * (double)acc.u0 - 6.0 * B * (double)acc.u1;
+  }
+  double v[NQ_PAIR] = {(double)acc.uc - (double)acc.cuc, ulj, (double)acc.wc - (double)acc.cwc, wlj};
+#pragma unroll
+  for (int k = 0; k < NQ_PAIR; ++k) {
+    const double s = warp_sum(v[k]);
+    if (lane == 0) a.epart[(int64_t)blockIdx.x * NQ_PAIR + k] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side
+
+int cpair_nc(const Ctx &c) { return c.precision == RBE_FP64 ? 4 : 8; }
+
+// Upper bound of the super-clusters of N particles in the rows of the grid.
+int64_t cpair_blocks_bound(const Ctx &c) {
+  const int64_t nrows = (int64_t)c.grid.n[1] * c.grid.n[2];
+  return c.N / (kClSize * cpair_nc(c)) + nrows + 1;
+}
+int64_t cpair_clusters_bound(const Ctx &c) {
+  const int64_t nrows = (int64_t)c.grid.n[1] * c.grid.n[2];
+  return c.N / kClSize + nrows + 1;
+}
+
+// The cluster kernel applies when a super-cluster's frame is a valid minimum image for y
+// and z (one cell width plus 2 r_c below L) and a group of at least one typical cluster
+// fits in x, with a stencil of at most 3 cells.
+bool cpair_usable(const Ctx &c) {
+  if (c.rbl || !c.pair_cluster) return false;
+  for (int d = 1; d < 3; ++d) {
+    if (c.grid.R[d] > 3) return false;
+    const double w = c.box[d] / c.grid.n[d];
+    if (!(w + 2.0 * c.rc < c.box[d] * (1.0 - 1e-9))) return false;
+  }
+  // room in x for at least a few cells' worth of a group
+  return c.box[0] - 2.0 * c.rc > 2.0 * c.box[0] / c.grid.n[0];
+}
+
+cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts) {
+  const int b = c.cur;
+  const int nrows = c.grid.n[1] * c.grid.n[2];
+  const int nc = cpair_nc(c);
+  cluster_rows_kernel<<<1, 1024, 0, c.stream>>>(c.cell_start, c.grid.n[0], nrows, nc, c.cl_base,
+                                                c.sc_base);
+  const int64_t ccap = cpair_clusters_bound(c);
+  cluster_bounds_kernel<<<(unsigned)((ccap + 255) / 256), 256, 0, c.stream>>>(
+      c.s[b], c.s[b] + c.N, c.s[b] + 2 * c.N, c.cell_start, c.grid.n[0], nrows, c.cl_base, ccap,
+      c.cl_lo, c.cl_hi);
+  ClusterArgs a;
+  a.set.sx = c.s[b]; a.set.sy = c.s[b] + c.N; a.set.sz = c.s[b] + 2 * c.N;
+  a.set.qf = c.qf[b]; a.set.qd = c.qd[b]; a.set.type = c.type[b];
+  a.set.cell_start = c.cell_start; a.set.map = nullptr; a.set.n = c.N;
+  a.grid = c.grid;
+  a.pc = c.pc;
+  a.ljA = c.lj.A[0]; a.ljB = c.lj.B[0]; a.ljA12 = c.lj.A12[0]; a.ljB6 = c.lj.B6[0];
+  a.ljAd = c.lj.Ad[0]; a.ljBd = c.lj.Bd[0]; a.ljA12d = c.lj.A12d[0]; a.ljB6d = c.lj.B6d[0];
+  a.table = reinterpret_cast<const LJTable *>(c.lj_dev);
+  a.cl_base = c.cl_base; a.sc_base = c.sc_base; a.cl_lo = c.cl_lo; a.cl_hi = c.cl_hi;
+  a.nrows = nrows;
+  a.facc = c.facc;
+  a.N = c.N;
+  a.fscale = (float)kFixScale32;
+  a.fscale_d = kFixScale64;
+  a.epart = c.epart + c.off_pair;
+  a.nbr = want_counts ? c.nbr : nullptr;
+  a.comp = c.precision == RBE_FP32_COMP;
+  {
+    // x extent of a group: (extent + 2 r_c) < L, in fractional units, with margin
+    const double lim = (c.box[0] - 2.0 * c.rc) / c.box[0] * kTwo32 * (1.0 - 1e-7) - 16.0;
+    a.xlim = (uint32_t)std::max(0.0, std::min(lim, 4294967295.0));
+    // frame coordinates within L/2 on every axis: the exact-decision band for that extent
+    double X[3];
+    for (int d = 0; d < 3; ++d) X[d] = 0.5 * c.box[d];
+    const double band = frame_band(X, c.rc, c.box, false);
+    a.pc.rc2_lo = (float)(c.rc * c.rc * (1.0 - band));
+    a.pc.rc2_hi = (float)(c.rc * c.rc * (1.0 + band));
+    // box test: squared gap of FP32 frame boxes (each bound within 2u L/2, the gap within
+    // u L more), widened so that no pair within r_c is lost
+    const double u = std::ldexp(1.0, -24);
+    double e = 0.0;
+    for (int d = 0; d < 3; ++d) e = std::max(e, 3.0 * u * c.box[d]);
+    const double rr = c.rc * (1.0 + 1e-5) + 2.0 * e;
+    a.bb2 = (float)(rr * rr);
+  }
+  a.err = c.err;
+  if (want_counts) cudaMemsetAsync(c.nbr, 0, sizeof(int32_t) * c.N, c.stream);
+  const int64_t blocks = cpair_blocks_bound(c);
+  const dim3 g((unsigned)blocks), bl(32);
+  const bool fp64 = c.precision == RBE_FP64;
+#define RBE_CP_LAUNCH(R, CO, MU)                                                             \
+  do {                                                                                       \
+    if (want_counts) cpair_kernel<R, CO, MU, true><<<g, bl, 0, c.stream>>>(a);               \
+    else cpair_kernel<R, CO, MU, false><<<g, bl, 0, c.stream>>>(a);                          \
+  } while (0)
+  if (fp64) {
+    if (coul) { if (multi) RBE_CP_LAUNCH(double, true, true); else RBE_CP_LAUNCH(double, true, false); }
+    else { if (multi) RBE_CP_LAUNCH(double, false, true); else RBE_CP_LAUNCH(double, false, false); }
+  } else {
+    if (coul) { if (multi) RBE_CP_LAUNCH(float, true, true); else RBE_CP_LAUNCH(float, true, false); }
+    else { if (multi) RBE_CP_LAUNCH(float, false, true); else RBE_CP_LAUNCH(float, false, false); }
+  }
+#undef RBE_CP_LAUNCH
+  const int64_t n3 = 3 * c.N;
+  const unsigned fb = (unsigned)((n3 + 255) / 256);
+  if (fp64) cpair_finalize_kernel<double><<<fb, 256, 0, c.stream>>>(c.facc, c.Fd, n3, 1.0 / kFixScale64);
+  else cpair_finalize_kernel<float><<<fb, 256, 0, c.stream>>>(c.facc, c.F, n3, 1.0 / kFixScale32);
+  return cudaGetLastError();
+}
+
+}  // namespace rbe

@@ -179,6 +179,9 @@ __global__ void __launch_bounds__(kRblWarps * 32, 16) rbl_kernel(const RblArgs a
       if (atomicCAS(&a.slots[sl], 0, 1) == 0) got = sl;
     }
     if (got < 0) atomicOr(a.err, ERRBIT_CAPACITY);
+    // acquire: the previous owner released the slot after a device-scope fence, so its
+    // stores to the slot's rows are ordered before every access of this block
+    __threadfence();
     slot_s = got;
   }
   __syncthreads();
@@ -550,7 +553,12 @@ __global__ void __launch_bounds__(kRblWarps * 32, 16) rbl_kernel(const RblArgs a
     if (threadIdx.x < NQ_PAIR) a.pa.epart[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = 0.5 * s;
     else a.fsum_part[(int64_t)blockIdx.x * 3 + threadIdx.x - NQ_PAIR] = s;
   }
-  if (threadIdx.x == 0 && slot >= 0) atomicExch(&a.slots[slot], 0);  // after the block's last use
+  // release, after the block's last use of its rows (every warp is past the barrier above):
+  // the fence orders all of the block's row stores before the flag store that frees the slot
+  if (threadIdx.x == 0 && slot >= 0) {
+    __threadfence();
+    atomicExch(&a.slots[slot], 0);
+  }
 }
 
 // The RBL kernel leaves one partial per block (energies, virials: NQ_PAIR doubles; sum of
@@ -662,11 +670,14 @@ static void rbl_shape(const Ctx &c, int *gs_out, bool *wrap_out) {
 
 // Slots of the scratch pool: the most 128-thread blocks the GPU can hold at once (thread
 // limit per SM), never more than the grid has blocks.
-int64_t rbl_slot_count(int64_t n) {
-  int dev = 0, sms = 152, thr = 2048;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+int64_t rbl_slot_count(int64_t n, int sms) {
+  int dev = 0, thr = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      thr < 1) {
+    cudaGetLastError();
+    thr = 2048;  // the largest per-SM thread count of current GPUs: an upper bound on residency
+  }
   const int64_t per_sm = std::max(1, thr / (kRblWarps * 32));
   return std::max<int64_t>(1, std::min<int64_t>(rbl_blocks(n), (int64_t)sms * per_sm));
 }

@@ -19,7 +19,7 @@ using namespace rbe;
 namespace rbe {
 int64_t pair_blocks(int64_t n);
 int64_t rbl_blocks(int64_t n);
-int64_t rbl_slot_count(int64_t n);
+int64_t rbl_slot_count(int64_t n, int sms);
 int64_t rbl_compact_count(int64_t nblk);
 int64_t rbl_mask_words(int64_t slots);
 }  // namespace rbe
@@ -118,7 +118,8 @@ int free_all(Ctx &c) {
     if (c.graph[b]) cudaGraphExecDestroy(c.graph[b]);
     c.graph[b] = nullptr;
   }
-  dfree(c.F); dfree(c.Fd); dfree(c.cs); dfree(c.cqf); dfree(c.cqd); dfree(c.cmap);
+  dfree(c.F); dfree(c.Fd); dfree(c.facc); dfree(c.cl_base); dfree(c.sc_base); dfree(c.cl_lo);
+  dfree(c.cl_hi); dfree(c.cs); dfree(c.cqf); dfree(c.cqd); dfree(c.cmap);
   dfree(c.cell_count); dfree(c.cell_start); dfree(c.key); dfree(c.off); dfree(c.tmp);
   dfree(c.scan_blk);
   for (int d = 0; d < 3; ++d) dfree(c.T[d]);
@@ -169,6 +170,8 @@ int64_t kernels_per_step(const Ctx &c) {
   k += c.Nq > 0 ? 2 : 0;                 // structure factor + combine
   if (c.rbl) k += 4;                     // RBL, compact partials, mean, subtract
   else k += (c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2;  // pair passes
+  if (!c.rbl && !c.vl_on && cpair_usable(c))
+    k += 3;                              // cluster tables (rows, bounds) and the finishing pass
   if (c.vl_on)                           // check, identity copy, build(s), commit
     k += 3 + ((c.Nq * 2 > c.N || c.Nq == 0) ? 1 : 2);
   k += c.Nq > 0 ? 1 : 0;                 // gather
@@ -406,11 +409,22 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   }
   c.S = Z[0] * Z[1] * Z[2] - 1.0;
 
+  // SM count of the current device (for the launch shapes below)
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      delete h;
+      return RBE_ERR_CUDA;
+    }
+    c.sms = sms;
+  }
   // structure-factor launch shape: one thread per mode, particle tiles per block
   c.sf_mb = std::min(256, ((c.P + 31) / 32) * 32);
   c.sf_nblk_m = (c.P + c.sf_mb - 1) / c.sf_mb;
   {
-    const int64_t target_blocks = 152 * 8;
+    const int64_t target_blocks = (int64_t)c.sms * 8;
     int64_t tile = Nq * c.sf_nblk_m / std::max<int64_t>(1, target_blocks);
     tile = std::max<int64_t>(32, std::min<int64_t>(512, ((tile + 31) / 32) * 32));
     c.sf_tile = (int)tile;
@@ -419,10 +433,10 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   }
 
   // reductions layout
-  c.n_pair_blk = rbl ? 0 : pair_blocks(N);
+  c.n_pair_blk = rbl ? 0 : std::max(pair_blocks(N), cpair_blocks_bound(c));
   c.n_coul_blk = rbl ? 0 : pair_blocks(Nq);
   c.n_rbl_blk = rbl ? rbl_blocks(N) : 0;
-  c.rbl_nslots = rbl ? rbl_slot_count(N) : 0;
+  c.rbl_nslots = rbl ? rbl_slot_count(N, c.sms) : 0;
   c.n_ke_blk = (N + 255) / 256;
   c.off_pair = 0;
   c.off_coul = c.off_pair + c.n_pair_blk * NQ_PAIR;
@@ -446,6 +460,14 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   }
   if (fp64) rc |= dalloc(c, &c.Fd, 3 * N);
   else rc |= dalloc(c, &c.F, 3 * N);
+  if (!rbl) {
+    const int64_t nrows = (int64_t)c.grid.n[1] * c.grid.n[2];
+    rc |= dalloc(c, &c.facc, 3 * N);
+    rc |= dalloc(c, &c.cl_base, nrows + 1);
+    rc |= dalloc(c, &c.sc_base, nrows + 1);
+    rc |= dalloc(c, &c.cl_lo, cpair_clusters_bound(c));
+    rc |= dalloc(c, &c.cl_hi, cpair_clusters_bound(c));
+  }
   rc |= dalloc(c, &c.cs, 3 * Nq);
   rc |= dalloc(c, &c.cqf, Nq);
   if (fp64) rc |= dalloc(c, &c.cqd, Nq);
@@ -537,6 +559,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
     e |= cudaMemset(c.epart, 0, sizeof(double) * c.epart_slots);
     e |= cudaMemset(c.emode, 0, sizeof(double) * 2 * c.P);
     e |= cudaMemset(c.err, 0, sizeof(int));
+    if (c.facc) e |= cudaMemset(c.facc, 0, sizeof(long long) * 3 * N);
     if (c.rbl_slots) e |= cudaMemset(c.rbl_slots, 0, sizeof(int) * c.rbl_nslots);
     e |= cudaMemset(c.step_dev, 0, sizeof(uint64_t));
     e |= cudaMemset(c.scal, 0, sizeof(double) * S_COUNT);
@@ -872,6 +895,9 @@ int rbe_set_tuning(rbe_handle h, int key, int value) {
   if (key == RBE_TUNE_PAIR_TEST16) {
     if (value != 0 && value != 1) return RBE_ERR_INVALID;
     c.pair_test16 = value != 0;
+  } else if (key == RBE_TUNE_PAIR_CLUSTER) {
+    if (value != 0 && value != 1) return RBE_ERR_INVALID;
+    c.pair_cluster = value != 0;
   } else if (key == RBE_TUNE_RBL_EAGER) {
     if (value != 0 && value != 1) return RBE_ERR_INVALID;
     c.rbl_eager = value != 0;
@@ -897,6 +923,7 @@ int rbe_get_tuning(rbe_handle h, int key, int *value) {
   else if (key == RBE_TUNE_SF_TILE) *value = h->sf_tile;
   else if (key == RBE_TUNE_RBL_EAGER) *value = h->rbl_eager ? 1 : 0;
   else if (key == RBE_TUNE_RBL_SPAN) *value = h->rbl_span;
+  else if (key == RBE_TUNE_PAIR_CLUSTER) *value = h->pair_cluster ? 1 : 0;
   else return RBE_ERR_INVALID;
   return RBE_OK;
 }
@@ -926,14 +953,31 @@ int rbe_autotune(rbe_handle h, int reps, int *chosen) {
   RBE_CUDA_TRY(launch_set_step(c, c.step));
   float best = 0.f;
   int best16 = c.pair_test16 ? 1 : 0;
+  // the per-particle kernel's two pre-tests, then the cluster-pair kernel against the better
+  const bool cl_saved = c.pair_cluster;
+  c.pair_cluster = false;
   for (int v = 0; v <= 1; ++v) {
     c.pair_test16 = v != 0;
     float ms = 0.f;
     int rc = time_forces(c, reps, &ms);
-    if (rc != RBE_OK) { c.timing = saved_timing; return rc; }
+    if (rc != RBE_OK) { c.timing = saved_timing; c.pair_cluster = cl_saved; return rc; }
     if (v == 0 || ms < best) { best = ms; best16 = v; }
   }
   c.pair_test16 = best16 != 0;
+  int best_cl = 0;
+  if (!c.rbl && cl_saved) {
+    c.pair_cluster = true;
+    if (cpair_usable(c)) {
+      float ms = 0.f;
+      int rc = time_forces(c, reps, &ms);
+      if (rc != RBE_OK) { c.timing = saved_timing; return rc; }
+      if (ms < best) { best = ms; best_cl = 1; }
+    }
+    c.pair_cluster = best_cl != 0;
+  } else {
+    c.pair_cluster = cl_saved;
+    best_cl = cl_saved ? 1 : 0;
+  }
   int best_eager = c.rbl_eager ? 1 : 0;
   if (c.rbl) {
     for (int v = 0; v <= 1; ++v) {
@@ -976,7 +1020,10 @@ int rbe_autotune(rbe_handle h, int reps, int *chosen) {
   c.timing = saved_timing;
   drop_graphs(c);
   c.have_forces = false;
-  if (chosen) { chosen[0] = best16; chosen[1] = best_tile; chosen[2] = best_eager; chosen[3] = c.rbl_span; }
+  if (chosen) {
+    chosen[0] = best16; chosen[1] = best_tile; chosen[2] = best_eager; chosen[3] = c.rbl_span;
+    chosen[4] = best_cl;
+  }
   return RBE_OK;
 }
 

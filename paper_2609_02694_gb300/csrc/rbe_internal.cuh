@@ -29,6 +29,10 @@ enum : int { ERRBIT_SAMPLER = 1, ERRBIT_NONFINITE = 2, ERRBIT_CAPACITY = 4 };
 // Partial-sum slots (doubles per block) of the energy / virial reductions.
 enum : int { Q_UREAL = 0, Q_ULJ = 1, Q_WREAL = 2, Q_WLJ = 3, NQ_PAIR = 4 };
 constexpr int kCompactMax = 256;  // compacted partials per pair pass before the totals
+// Fixed-point scales of the cluster kernel's force sums (64-bit integers): 2^32 in the FP32
+// forms, 2^40 in the FP64 form.
+constexpr double kFixScale32 = 4294967296.0;
+constexpr double kFixScale64 = 1099511627776.0;
 
 struct Grid {
   int n[3];       // cells per axis
@@ -75,6 +79,7 @@ struct Ctx {
   double alpha = 0, rc = 0, r_core = 0, C = 0, dt = 0, kappa = 0;
   int P = 0, p_rbl = 0, precision = RBE_FP32_COMP, nt = 1, sub = 2;
   bool pair_test16 = true;  // packed half-precision candidate pre-test in the pair kernel
+  bool pair_cluster = false; // cluster-pair kernel (each pair once) for the main pair pass
   bool rbl_eager = false;   // RBL: evaluate every shell pair in the classifying pass
   int rbl_span = 0;         // RBL: group extent in x cells (0: automatic)
   uint64_t seed = 0;
@@ -82,6 +87,7 @@ struct Ctx {
   bool rbl = false;
   double sum_q2 = 0, U_self = 0, S = 0, V = 0;
   cudaStream_t stream = nullptr;
+  int sms = 1;                // SM count of the device the handle was created on
   Grid grid{};
   LJTable lj{};
   void *lj_dev = nullptr;     // device copy of lj (multi-type pair kernels)
@@ -98,6 +104,11 @@ struct Ctx {
   float *invm[2] = {nullptr, nullptr};
   float *F = nullptr;
   double *Fd = nullptr;
+  // cluster-pair kernel: fixed-point force sums (3N, sorted order), per-row cluster and
+  // super-cluster offsets (rows + 1 each), per-cluster bounds
+  long long *facc = nullptr;
+  int32_t *cl_base = nullptr, *sc_base = nullptr;
+  uint4 *cl_lo = nullptr, *cl_hi = nullptr;
   // charged subset
   uint32_t *cs = nullptr;
   float *cqf = nullptr;
@@ -232,6 +243,12 @@ cudaError_t launch_bin_sort(Ctx &c);
 cudaError_t launch_structure_factor(Ctx &c);
 cudaError_t launch_kspace_gather(Ctx &c);
 cudaError_t launch_pair(Ctx &c, bool want_counts);   // main pass, then mark, then Coulomb pass
+// Cluster-pair kernel (k_cpair.cu): whether it applies to the handle's box and tuning, the
+// launch bounds of its super-clusters and clusters, and the launch (tables, pairs, finish).
+bool cpair_usable(const Ctx &c);
+int64_t cpair_blocks_bound(const Ctx &c);
+int64_t cpair_clusters_bound(const Ctx &c);
+cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts);
 void mark(Ctx &c, int k);  // record the profiling event k (no-op when profiling is off)
 cudaError_t launch_rbl(Ctx &c, bool want_debug);
 cudaError_t launch_list_check(Ctx &c);    // rebuild flag from the displacements

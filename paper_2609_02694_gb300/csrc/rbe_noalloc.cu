@@ -29,6 +29,7 @@ static __device__ __align__(256) double g_noalloc_partials[kNoallocScratchDouble
 
 std::mutex g_setup_mutex;
 double *g_partials_ptr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
 
 // Block b sums tiles b, b + nblk, ... of the particles for one mode per thread, with
 // Kahan-compensated FP32 accumulation (the compensated form of the handle path), and
@@ -100,8 +101,9 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
-int partials_on_current_device(double **out) {
+// Device address of the scratch array on the current device and that device's SM count,
+// looked up once per device.
+int partials_on_current_device(double **out, int *sms) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
@@ -114,9 +116,16 @@ int partials_on_current_device(double **out) {
       cudaGetLastError();
       return RBE_ERR_CUDA;
     }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      return RBE_ERR_CUDA;
+    }
+    g_sm_count[dev] = n;
     g_partials_ptr[dev] = ptr;
   }
   *out = g_partials_ptr[dev];
+  *sms = g_sm_count[dev];
   return RBE_OK;
 }
 
@@ -128,13 +137,14 @@ extern "C" int rbe_structure_factor_noalloc(const uint32_t *s, const float *q, i
   if (N < 0 || P < 1 || !m || !rho || (N > 0 && (!s || !q))) return RBE_ERR_INVALID;
   if (P > kNoallocMaxP) return RBE_ERR_INVALID;  // beyond the fixed scratch this build holds
   double *part = nullptr;
-  const int rc = partials_on_current_device(&part);
+  int sms = 1;
+  const int rc = partials_on_current_device(&part, &sms);
   if (rc != RBE_OK) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int mode_blocks = (P + kNoallocThreads - 1) / kNoallocThreads;
   // as many particle blocks as the scratch holds for P modes, at most two per SM
   int64_t nblk = kNoallocScratchDoubles / (2 * (int64_t)P);
-  nblk = std::min<int64_t>(nblk, 2 * 152);
+  nblk = std::min<int64_t>(nblk, 2 * (int64_t)sms);
   nblk = std::min<int64_t>(nblk, std::max<int64_t>(1, (N + kNoallocTile - 1) / kNoallocTile));
   nblk = std::max<int64_t>(nblk, 1);
   noalloc_sf_kernel<<<dim3((unsigned)nblk, (unsigned)mode_blocks), kNoallocThreads, 0, st>>>(

@@ -37,3 +37,15 @@ def total_forces_sampled(orc, sy, idx, m, S, alpha=synth.ALPHA, rc=synth.R_CUT,
     rs = orc.real_space(sy.s, sy.q, sy.types, sy.box, alpha, rc, C, sy.eps, sy.sig, i_list=idx)
     F = rs["F"][idx] + kspace_force_sampled(sy, idx, m, S, charged_rho(orc, sy, m), C)
     return F, rs["nbr"][idx]
+
+
+def oracle_modes(orc, h, sy, P, step, seed=1, replica=0, alpha=synth.ALPHA):
+    """The oracle's own draw of a step's modes (the sampling density of Eq. F_long_RBE),
+    after checking that the GPU drew exactly the same set and normaliser. A force test
+    then hands the oracle its own modes, so a sampler fault at any box, seed or step
+    fails the test instead of being copied into the reference."""
+    mo, So = orc.sample_k(seed, step, replica, np.asarray(sy.box, np.float64), alpha, P)
+    m, S = h.sample_k(step)
+    assert np.array_equal(m, mo), "GPU mode set differs from the oracle's draw"
+    assert S == So, "GPU normaliser S differs from the oracle's"
+    return mo, So

@@ -120,7 +120,7 @@ def test_full_size_batch96(orc):
         with make(r, sy) as h:
             F, _, _ = h.forces_f64(0)
             nbr, _ = h.neighbor_counts()
-            m, S = h.sample_k(0)
+            m, S = sampled.oracle_modes(orc, h, sy, 200, 0, replica=r)
         rng = np.random.default_rng(r)
         idx = np.unique(np.r_[rng.choice(sy.n, 4, replace=False), np.flatnonzero(sy.q)[:1]])
         Fo_r, nbr_o = sampled.total_forces_sampled(orc, sy, idx, m, S)

@@ -105,7 +105,9 @@ def test_structure_factor(orc, precision, tol):
     with handle(sy, 200, precision=precision) as h:
         h.forces(0)
         rho, m = h.rho()
-    ro = orc.rho(sy.s, sy.q, sy.box, m)
+    mo, _ = orc.sample_k(1, 0, 0, sy.box, ALPHA, 200)
+    assert np.array_equal(m, mo)
+    ro = orc.rho(sy.s, sy.q, sy.box, mo)
     assert rel_l2(rho, ro) < tol
 
 
@@ -128,7 +130,7 @@ def test_forces_match_oracle(orc, name, skw, P, hkw, precision):
     sy = synth.make_system(**skw)
     with handle(sy, P, precision=precision, **hkw) as h:
         F, E, W = h.forces_f64(0)
-        m, S = h.sample_k(0)
+        m, S = sampled.oracle_modes(orc, h, sy, P, 0)
         nbr, _ = h.neighbor_counts()
     ref = oracle_all(orc, sy, m, S)
     tol = TOL_F64 if precision == "fp64" else TOL_F32
@@ -153,7 +155,7 @@ def test_orthorhombic_two_types(orc):
     sy.sig = np.array([3.0, 2.8, 2.8, 2.6])
     with handle(sy, 150) as h:
         F, E, W = h.forces_f64(4)
-        m, S = h.sample_k(4)
+        m, S = sampled.oracle_modes(orc, h, sy, 150, 4)
         nbr, _ = h.neighbor_counts()
     ref = oracle_all(orc, sy, m, S)
     assert rel_l2(F, ref["F"]) < TOL_F32
@@ -186,7 +188,7 @@ def test_tiny_box_edge(orc):
     sy = synth.make_system(12, L=25.1, all_charged=True, seed=8)
     with handle(sy, 16) as h:
         F, E, W = h.forces_f64(2)
-        m, S = h.sample_k(2)
+        m, S = sampled.oracle_modes(orc, h, sy, 16, 2)
         nbr, _ = h.neighbor_counts()
     ref = oracle_all(orc, sy, m, S)
     assert rel_l2(F, ref["F"]) < TOL_F32
@@ -234,7 +236,7 @@ def test_rbl_bit_exact_sets_and_draws(orc, precision, tol):
         F, E, W = h.forces_f64(step)
         nc, ns = h.neighbor_counts()
         partners = h.rbl_partners()
-        m, S = h.sample_k(step)
+        m, S = sampled.oracle_modes(orc, h, sy, 100, step, seed=seed)
     ref = orc.rbl(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, RC, p, seed, step, 0, C,
                   sy.eps, sy.sig)
     assert np.array_equal(nc, ref["n_core"])
@@ -247,12 +249,46 @@ def test_rbl_bit_exact_sets_and_draws(orc, precision, tol):
     assert E["real"] == pytest.approx(ref["U_real"], rel=etol, abs=1e-6)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32_comp", TOL_F32), ("fp64", TOL_F64)])
+@pytest.mark.parametrize("eager", [0, 1])
+def test_rbl_wrapping_box_matches_oracle(orc, precision, tol, eager):
+    """A box of three cells of r_s per axis (6,000 particles at density 0.1, L = 39.1 A):
+    a cell plus r_s reaches past L/2, so the random batch list runs its wrapping variant,
+    which folds every difference into the box. Core and shell sizes and the drawn partners
+    (Eqs. Ci_Si, RBL) match the oracle bit for bit, and forces and energies (with the
+    correction of Eq. F_corr) match it within the form's tolerance, with eager shell sums
+    on and off."""
+    sy = synth.make_system(6000, density=0.1, frac_charged=0.1, seed=17)
+    p, r_core, seed, step, P = 10, 5.0, 4, 2, 64
+    with handle(sy, P, precision=precision, r_core=r_core, p_rbl=p, seed=seed) as h:
+        h.set_tuning("rbl_eager", eager)
+        F, E, W = h.forces_f64(step)
+        nc, ns = h.neighbor_counts()
+        partners = h.rbl_partners()
+        n, _, _ = h.cells()
+        m, S = sampled.oracle_modes(orc, h, sy, P, step, seed=seed)
+    assert tuple(n) == (3, 3, 3)
+    assert RC + sy.box[0] / 3 >= sy.box[0] / 2  # the condition that selects the variant
+    ref = orc.rbl(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, RC, p, seed, step, 0, C,
+                  sy.eps, sy.sig)
+    assert np.array_equal(nc, ref["n_core"])
+    assert np.array_equal(ns, ref["n_shell"])
+    assert np.array_equal(partners, ref["partners"])
+    assert (ns > p).any()
+    Fk, Uk, Wk = orc.rbe_kspace(sy.s, sy.q, sy.box, ALPHA, C, m, S)
+    assert rel_l2(F, ref["F"] + Fk) < tol
+    etol = 1e-10 if precision == "fp64" else 2e-6
+    assert E["lj"] == pytest.approx(ref["U_lj"], rel=etol)
+    assert E["real"] == pytest.approx(ref["U_real"], rel=etol, abs=1e-6)
+    assert W["lj"] == pytest.approx(ref["W_lj"], rel=etol)
+
+
 def test_rbl_small_shell_takes_all(orc):
     """p >= #S_i: every shell partner enters with weight 1 (exact cutoff sum)."""
     sy = synth.make_system(4000, density=0.1, frac_charged=0.1, seed=6)
     with handle(sy, 50, r_core=8.0, p_rbl=32, r_c=8.1) as h:
         F, E, W = h.forces_f64(0)
-        m, S = h.sample_k(0)
+        m, S = sampled.oracle_modes(orc, h, sy, 50, 0)
     ex = oracle_all(orc, sy, m, S, rc=8.1)
     assert rel_l2(F, ex["F"]) < TOL_F32
 
@@ -349,7 +385,7 @@ def test_verlet_shadowing_fp32(orc):
         assert h.step_count() == 20
         pos, vel, s = h.state()
         F, E, W = h.forces_f64(20)
-        m, S = h.sample_k(20)
+        m, S = sampled.oracle_modes(orc, h, sy, 100, 20)
     sy2 = synth.System(box=sy.box, s=s, q=sy.q, types=sy.types, mass=sy.mass, v=vel,
                        eps=sy.eps, sig=sy.sig)
     ref = oracle_all(orc, sy2, m, S)
@@ -380,7 +416,7 @@ def test_full_size_one_million_sampled(orc):
     with handle(sy, 200) as h:
         F, E, W = h.forces_f64(0)
         nbr, _ = h.neighbor_counts()
-        m, S = h.sample_k(0)
+        m, S = sampled.oracle_modes(orc, h, sy, 200, 0)
         rho, _ = h.rho()
     idx = sample_ids(sy, 48)
     assert rel_l2(rho, sampled.charged_rho(orc, sy, m)) < 2e-6
@@ -403,7 +439,7 @@ def test_full_size_sixteen_million_sampled(orc, sys16m, precision, P, tol):
     with handle(sy, P, precision=precision) as h:
         F, E, W = h.forces_f64(0)
         nbr, _ = h.neighbor_counts()
-        m, S = h.sample_k(0)
+        m, S = sampled.oracle_modes(orc, h, sy, P, 0)
     idx = sample_ids(sy, 32)
     Fo, nbr_o = sampled.total_forces_sampled(orc, sy, idx, m, S)
     assert np.array_equal(nbr[idx], nbr_o)
@@ -421,7 +457,7 @@ def test_full_size_rbl_134m_sampled(orc):
     with handle(sy, 500, r_core=r_core, p_rbl=p, seed=seed) as h:
         F, E, W = h.forces_f64(step)
         nc, ns = h.neighbor_counts()
-        m, S = h.sample_k(step)
+        m, S = sampled.oracle_modes(orc, h, sy, 500, step, seed=seed)
     idx = sample_ids(sy, 64)
     F, nc, ns = F[idx], nc[idx], ns[idx]
     rows = orc.rbl_rows(sy.s, sy.q, sy.types, sy.box, ALPHA, r_core, RC, p, seed, step, 0, C,
@@ -449,7 +485,7 @@ def test_pair_pretest_variants_match_oracle(orc, test16, skw):
         h.set_tuning("pair_test16", test16)
         assert h.get_tuning("pair_test16") == test16
         F, E, W = h.forces_f64(0)
-        m, S = h.sample_k(0)
+        m, S = sampled.oracle_modes(orc, h, sy, 100, 0)
         nbr, _ = h.neighbor_counts()
     ref = oracle_all(orc, sy, m, S)
     assert np.array_equal(nbr, ref["nbr"])
@@ -462,7 +498,7 @@ def test_autotune_keeps_results(orc):
         chosen = h.autotune(2)
         assert chosen["pair_test16"] in (0, 1) and chosen["sf_tile"] % 32 == 0
         F, E, W = h.forces_f64(0)
-        m, S = h.sample_k(0)
+        m, S = sampled.oracle_modes(orc, h, sy, 200, 0)
         h.step(3)
     ref = oracle_all(orc, sy, m, S)
     assert rel_l2(F, ref["F"]) < TOL_F32
@@ -534,7 +570,7 @@ def test_lj_electrolyte_reduced_units(orc):
                              coulomb_C=prm["coulomb_C"], dt=prm["dt"], kappa=prm["kappa"],
                              seed=9) as h:
         F, E, W = h.forces_f64(3)
-        m, S = h.sample_k(3)
+        m, S = sampled.oracle_modes(orc, h, sy, prm["P"], 3, seed=9, alpha=prm["alpha"])
         nc, ns = h.neighbor_counts()
     ref = orc.rbl(sy.s, sy.q, sy.types, sy.box, prm["alpha"], prm["r_core"], prm["r_c"],
                   prm["p_rbl"], 9, 3, 0, prm["coulomb_C"], sy.eps, sy.sig)

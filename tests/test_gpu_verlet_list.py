@@ -9,6 +9,8 @@ import pytest
 
 from paper_2609_02694_gb300 import binding, build, synth
 
+import sampled
+
 pytestmark = pytest.mark.gpu
 
 ALPHA, RC, C = synth.ALPHA, synth.R_CUT, synth.COULOMB_C
@@ -54,7 +56,7 @@ def test_list_forces_match_oracle(orc, kind, precision, tol):
         h.set_neighbor_list(1.0)
         F, E, W = h.forces_f64(3)
         nbr, _ = h.neighbor_counts()
-        m, S = h.sample_k(3)
+        m, S = sampled.oracle_modes(orc, h, sy, 120, 3)
         st = h.neighbor_list_stats()
     ref = oracle_all(orc, sy, m, S)
     assert rel_l2(F, ref["F"]) < tol
@@ -77,7 +79,7 @@ def test_list_and_cells_agree_over_steps(orc):
         pos, vel, s = h.state()
         F_list, E_list, _ = h.forces_f64(12)
         nbr_list, _ = h.neighbor_counts()
-        m, S = h.sample_k(12)
+        m, S = sampled.oracle_modes(orc, h, sy, 64, 12)
     assert st["evaluations"] == 13  # the first step's priming force evaluation + 12 steps
     assert 2 <= st["builds"] < st["evaluations"]
     sy2 = synth.System(box=sy.box, s=s, q=sy.q, types=sy.types, mass=sy.mass, v=vel,
@@ -122,7 +124,7 @@ def test_set_positions_rebuilds_only_when_moved(orc):
         h.set_positions(other.positions())
         F, E, W = h.forces_f64(0)
         nbr, _ = h.neighbor_counts()
-        m, S = h.sample_k(0)
+        m, S = sampled.oracle_modes(orc, h, sy, 64, 0)
         assert h.neighbor_list_stats()["builds"] == 2
     sy3 = synth.System(box=sy.box, s=other.s, q=sy.q, types=sy.types, mass=sy.mass, v=sy.v,
                        eps=sy.eps, sig=sy.sig)
