@@ -47,10 +47,8 @@ enum {
   RBE_ERR_SAMPLER = -7,     /* 64 redraws of a mode all gave k = 0 (device flag) */
   RBE_ERR_NONFINITE = -8,   /* a non-finite velocity or position update (device flag) */
   RBE_ERR_STATE = -9,       /* call not valid in this state (e.g. no forces computed yet) */
-  RBE_ERR_CAPACITY = -10    /* an RBL stencil (27 cells) held more than 6144 candidates, a
-                               Verlet list outgrew its capacity, or one 8-particle cluster of
-                               the cluster-pair kernel spanned more than L - 2 r_c in x (device
-                               flag) */
+  RBE_ERR_CAPACITY = -10    /* an RBL stencil (27 cells) held more than 6144 candidates, or a
+                               Verlet list outgrew its capacity (device flag) */
 };
 
 enum {
@@ -129,7 +127,9 @@ int rbe_set_positions(rbe_handle h, const double *pos, int on_device);
 int rbe_forces(rbe_handle h, uint64_t step, float *F_out, int F_on_device, double *energies,
                double *virial);
 
-/* Same as rbe_forces, with FP64 forces written to host memory (for parity checks). */
+/* Same as rbe_forces, with FP64 forces written to host memory (for parity checks); it also
+ * records the neighbour counts and RBL draws that rbe_get_neighbor_counts and
+ * rbe_get_rbl_partners return. */
 int rbe_forces_f64(rbe_handle h, uint64_t step, double *F_out, double *energies,
                    double *virial);
 
@@ -174,14 +174,15 @@ int rbe_get_cells(rbe_handle h, int32_t n_cells[3], int64_t *cell_start, int64_t
  * either pointer may be NULL. */
 int rbe_get_rho(rbe_handle h, double *rho, int32_t *m_out);
 
-/* Per-particle neighbour counts of the last evaluation (id order, nullable):
+/* Per-particle neighbour counts of the last rbe_forces_f64 evaluation (id order, nullable;
+ * rbe_forces and rbe_step do not count):
  * plain cell list: n_core = #{j != i: r_ij <= r_c}, n_shell = 0;
  * RBL: n_core = #C_i, n_shell = #S_i (Eq. Ci_Si). Cutoff decisions are exact: the FP64
  * comparison of dx^2 + dy^2 + dz^2 with r^2, dx_d = (int32)(s_i - s_j) * (L_d / 2^32). */
 int rbe_get_neighbor_counts(rbe_handle h, int32_t *n_core, int32_t *n_shell);
 
-/* RBL draws of the last evaluation (Eq. RBL: p i.i.d. members of S_i, in S_i's canonical
- * order; N x p_rbl ids in id order, host; -1 where unused). */
+/* RBL draws of the last rbe_forces_f64 evaluation (Eq. RBL: p i.i.d. members of S_i, in S_i's
+ * canonical order; N x p_rbl ids in id order, host; -1 where unused). */
 int rbe_get_rbl_partners(rbe_handle h, int32_t *partners);
 
 /* Phases timed by the profiler (CUDA events recorded on the library's stream). */
@@ -206,7 +207,9 @@ int rbe_set_profiling(rbe_handle h, int enable);
  * or Verlet step, and the number of kernels one Verlet step launches. Synchronises. */
 int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kernels_per_step);
 
-/* Tunables of the launch shapes (none changes results beyond FP32 rounding order):
+/* Tunables of the launch shapes (none changes results beyond FP32 rounding order; the
+ * defaults: pair_test16 1, pair_cluster 1 except in the FP64 form, sf_tile by the
+ * particle count, RBL ones automatic):
  *  RBE_TUNE_PAIR_TEST16  1: packed half-precision candidate pre-test in the cell-list pair
  *                        kernel (exact decision still at evaluation), 0: FP32 pre-test
  *  RBE_TUNE_SF_TILE      particles per block tile of the structure factor (32..1024, x32;

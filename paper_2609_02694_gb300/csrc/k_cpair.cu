@@ -29,7 +29,7 @@
 // The difference of two offsets is the minimum-image displacement of a pair within r_c as
 // long as the super-cluster's extent plus 2 r_c stays below L on every axis: the host
 // checks y and z (a cell width), the kernel splits a super-cluster whose x extent is
-// larger into groups of clusters that fit. The cutoff decision is exact: FP32 outside a
+// larger into groups of clusters that fit, down to single particles. The cutoff decision is exact: FP32 outside a
 // band around r_c^2 that covers the rounding of the frame coordinates, and the oracle's
 // FP64 expression of the integer displacement inside it (a rare branch per visit whose
 // pairs are added by atomics); the FP64 form always takes the FP64 expression.
@@ -64,6 +64,7 @@ struct ClusterArgs {
   int comp;                    // Kahan sums for the Coulomb energy and virial
   uint32_t xlim;               // largest x extent of a cluster group the frame allows
   float bb2;                   // bounding-box test: squared gap <= bb2 (r_c^2, widened)
+  float rc2_mid, rc2_half;     // band test: |r^2 - rc2_mid| <= rc2_half covers [rc2_lo, rc2_hi]
   int *err;
 };
 
@@ -155,7 +156,9 @@ __global__ void __launch_bounds__(256) cluster_bounds_kernel(
   hi[g] = make_uint4(x1, y1, z1, (uint32_t)n);
 }
 
-// F = fixed-point sums / scale (overwriting), and the sums cleared for the next pass.
+// F = fixed-point sums / scale (overwriting), and the sums cleared for the next pass. The
+// 64-bit sum converts as its two 32-bit halves (a 64-bit integer conversion is slow here):
+// v = hi 2^32 + lo with hi signed and lo unsigned.
 template <typename real>
 __global__ void __launch_bounds__(256) cpair_finalize_kernel(long long *__restrict__ facc,
                                                              real *__restrict__ F, int64_t n3,
@@ -164,7 +167,14 @@ __global__ void __launch_bounds__(256) cpair_finalize_kernel(long long *__restri
   if (k >= n3) return;
   const long long v = facc[k];
   facc[k] = 0;
-  F[k] = (real)((double)v * inv_scale);
+  const int hi = (int)(v >> 32);
+  const unsigned lo = (unsigned)(v & 0xffffffffll);
+  if (sizeof(real) == 8) {
+    F[k] = (real)(((double)hi * 4294967296.0 + (double)lo) * inv_scale);
+  } else {
+    const float s = (float)inv_scale;
+    F[k] = (real)fmaf((float)hi, (float)(4294967296.0 * inv_scale), (float)lo * s);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -259,7 +269,10 @@ __device__ __forceinline__ real cp_terms(const ClusterArgs &a, bool in, real r2,
 // The kernel: one warp per super-cluster.
 
 template <typename real, bool COUL, bool MULTI, bool COUNT>
-__global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kernel(const ClusterArgs a) {
+// (occupancy: 20 warps per SM for the FP32 LJ pass, fewer for the register-heavy Coulomb and
+// FP64 instances)
+__global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (COUL ? 12 : 20)))
+    cpair_kernel(const ClusterArgs a) {
   constexpr bool F64 = sizeof(real) == 8;
   constexpr int NC = F64 ? 4 : 8;          // clusters per super-cluster
   constexpr int NP = NC * kClSize;         // particles per super-cluster
@@ -285,28 +298,34 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
     const int p0 = ps + ksc * NP;
     const int np = min(NP, pe - p0);
     const int cy = r % n1, cz = r / n1;
+    // (slots past the particles hold type 0 and no charge: masked lanes still look up the
+    // LJ table by type before their result is zeroed)
     for (int t = lane; t < NP; t += 32) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      int ty = 0;
       if (t < np) {
         const int p = p0 + t;
         v = make_uint4(a.set.sx[p], a.set.sy[p], a.set.sz[p],
                        COUL ? __float_as_uint(a.set.qf[p]) : 0u);
-        if (MULTI) sti[t] = a.set.type[p];
+        if (MULTI) ty = a.set.type[p];
       }
       si[t] = v;
+      if (MULTI) sti[t] = ty;
     }
     __syncwarp();
     // Groups of consecutive clusters whose x extent the frame allows (normally one group).
-    int cb = 0;
+    // A single cluster wider than that is taken one particle at a time (asub), as a group
+    // of one point.
+    int cb = 0, asub = -1;
     while (cb < nc) {
-      const uint32_t xfirst = si[kClSize * cb].x;
       int ce = cb + 1;
-      while (ce < nc && si[min(np, kClSize * (ce + 1)) - 1].x - xfirst <= a.xlim) ++ce;
-      if (si[min(np, kClSize * ce) - 1].x - xfirst > a.xlim) {
-        if (lane == 0) atomicOr(a.err, ERRBIT_CAPACITY);  // one cluster wider than the frame
-        break;
+      if (asub < 0) {
+        const uint32_t xfirst = si[kClSize * cb].x;
+        while (ce < nc && si[min(np, kClSize * (ce + 1)) - 1].x - xfirst <= a.xlim) ++ce;
+        if (si[min(np, kClSize * ce) - 1].x - xfirst > a.xlim) asub = 0;
       }
-      const int q0 = kClSize * cb, q1 = min(np, kClSize * ce);
+      const int q0 = asub < 0 ? kClSize * cb : kClSize * cb + asub;
+      const int q1 = asub < 0 ? min(np, kClSize * ce) : q0 + 1;
       // group box and frame centre (no wrap inside a row: x ascending, y and z in one cell)
       uint32_t ylo = 0xffffffffu, yhi = 0u, zlo = 0xffffffffu, zhi = 0u;
       for (int t = q0 + lane; t < q1; t += 32) {
@@ -326,7 +345,7 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int t = kClSize * c + a8;
-        const bool v = c >= cb && c < ce && t < np;
+        const bool v = c >= cb && c < ce && t < np && (asub < 0 || a8 == asub);
         vi[c] = v;
         const uint4 s = si[t];
         oxi[c] = (int)(s.x - rx); oyi[c] = (int)(s.y - ry); ozi[c] = (int)(s.z - rz);
@@ -347,7 +366,9 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
       if (lane < NC) {
         float4 lo4 = make_float4(3e18f, 3e18f, 3e18f, 0.f), hi4 = make_float4(3e18f, 3e18f, 3e18f, 0.f);
         if (lane >= cb && lane < ce) {
-          const uint4 l = a.cl_lo[g0 + lane], u = a.cl_hi[g0 + lane];
+          uint4 l, u;
+          if (asub < 0) { l = a.cl_lo[g0 + lane]; u = a.cl_hi[g0 + lane]; }
+          else { l = u = si[q0]; }  // the one particle of a point group
           lo4 = make_float4((float)(int)(l.x - rx) * pc.h[0], (float)(int)(l.y - ry) * pc.h[1],
                             (float)(int)(l.z - rz) * pc.h[2], 0.f);
           hi4 = make_float4((float)(int)(u.x - rx) * pc.h[0], (float)(int)(u.y - ry) * pc.h[1],
@@ -455,15 +476,24 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
           const uint4 l = a.cl_lo[J], u = a.cl_hi[J];
           jb = (int)l.w;
           jn = (int)u.w;
-          const float jx0 = (float)(int)(l.x - rx) * pc.h[0], jx1 = (float)(int)(u.x - rx) * pc.h[0];
-          const float jy0 = (float)(int)(l.y - ry) * pc.h[1], jy1 = (float)(int)(u.y - ry) * pc.h[1];
-          const float jz0 = (float)(int)(l.z - rz) * pc.h[2], jz1 = (float)(int)(u.z - rz) * pc.h[2];
+          const float jx0 = (float)(int)(l.x - rx) * pc.h[0];
+          const float jy0 = (float)(int)(l.y - ry) * pc.h[1];
+          const float jz0 = (float)(int)(l.z - rz) * pc.h[2];
+          const float jx1 = (float)(int)(u.x - rx) * pc.h[0];
+          const float jy1 = (float)(int)(u.y - ry) * pc.h[1];
+          const float jz1 = (float)(int)(u.z - rz) * pc.h[2];
+          // a box that reaches past L/2 from the frame centre wraps (its ends swap sides): its
+          // distance is then that of the nearer of its two pieces
+          const bool wx = jx0 > jx1, wy = jy0 > jy1, wz = jz0 > jz1;
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const float4 lo4 = ibl[c], hi4 = ibh[c];
-            const float gx = fmaxf(0.f, fmaxf(jx0 - hi4.x, lo4.x - jx1));
-            const float gy = fmaxf(0.f, fmaxf(jy0 - hi4.y, lo4.y - jy1));
-            const float gz = fmaxf(0.f, fmaxf(jz0 - hi4.z, lo4.z - jz1));
+            const float ax = jx0 - hi4.x, bx = lo4.x - jx1;
+            const float ay = jy0 - hi4.y, by = lo4.y - jy1;
+            const float az = jz0 - hi4.z, bz = lo4.z - jz1;
+            const float gx = fmaxf(0.f, wx ? fminf(ax, bx) : fmaxf(ax, bx));
+            const float gy = fmaxf(0.f, wy ? fminf(ay, by) : fmaxf(ay, by));
+            const float gz = fmaxf(0.f, wz ? fminf(az, bz) : fmaxf(az, bz));
             const bool hit = c >= cb && c < ce && J >= g0 + c &&
                              fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= a.bb2;
             msk |= hit ? (1u << c) : 0u;
@@ -478,7 +508,8 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
           const uint32_t M = __shfl_sync(FULL, msk, t0);
           const int vb = __shfl_sync(FULL, jb, t0), vn = __shfl_sync(FULL, jn, t0);
           const int cdiag = Jv - g0;  // the visited cluster's place in the super-cluster
-          // this lane's j particles: h and h + 4 of the cluster
+          // This lane's j particles, h and h + 4 of the cluster: exact integer offsets from the
+          // frame centre, converted to FP32 (kept as integers in the FP64 form).
           real xj[2], yj[2], zj[2], qj[2], fxj[2], fyj[2], fzj[2];
           int oxj[2], oyj[2], ozj[2], tj[2], cntj[2];
           bool vj[2];
@@ -487,67 +518,121 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
             const int t = hh + 4 * k;
             vj[k] = t < vn;
             const int p = vb + (vj[k] ? t : 0);
-            oxj[k] = (int)(a.set.sx[p] - rx);
-            oyj[k] = (int)(a.set.sy[p] - ry);
-            ozj[k] = (int)(a.set.sz[p] - rz);
-            if (!F64) {
-              xj[k] = vj[k] ? (real)((float)oxj[k] * pc.h[0]) : (real)-3e18f;
-              yj[k] = vj[k] ? (real)((float)oyj[k] * pc.h[1]) : (real)-3e18f;
-              zj[k] = vj[k] ? (real)((float)ozj[k] * pc.h[2]) : (real)-3e18f;
-            } else {
-              xj[k] = yj[k] = zj[k] = (real)0;
-            }
+            oxj[k] = oyj[k] = ozj[k] = 0;
             qj[k] = (real)0;
-            if (COUL) qj[k] = F64 ? (real)a.set.qd[p] : (real)a.set.qf[p];
+            if (!F64) {
+              xj[k] = vj[k] ? (real)((float)(int)(a.set.sx[p] - rx) * pc.h[0]) : (real)-3e18f;
+              yj[k] = vj[k] ? (real)((float)(int)(a.set.sy[p] - ry) * pc.h[1]) : (real)-3e18f;
+              zj[k] = vj[k] ? (real)((float)(int)(a.set.sz[p] - rz) * pc.h[2]) : (real)-3e18f;
+              if (COUL) qj[k] = (real)a.set.qf[p];
+            } else {
+              oxj[k] = (int)(a.set.sx[p] - rx);
+              oyj[k] = (int)(a.set.sy[p] - ry);
+              ozj[k] = (int)(a.set.sz[p] - rz);
+              xj[k] = yj[k] = zj[k] = (real)0;
+              if (COUL) qj[k] = (real)a.set.qd[p];
+            }
             tj[k] = MULTI ? a.set.type[p] : 0;
             fxj[k] = fyj[k] = fzj[k] = (real)0;
             cntj[k] = 0;
           }
-          bool band = false;
+          float bmin = 3e38f;  // FP32 forms: smallest |r^2 - r_c^2| of the visit (band test)
+          // Pair force of i (frame coordinates or integer offsets) with this lane's j particle k,
+          // when `ok`; adds the reaction to j and returns the force factor and displacement.
+          auto pair_one = [&](bool ok, real xi_, real yi_, real zi_, int oxi_, int oyi_,
+                              int ozi_, real qi_, int ti_, int k, real &dx, real &dy, real &dz,
+                              bool &in) -> real {
+            real r2, ir2;
+            if (F64) {
+              // the offsets' difference (mod 2^32) is the exact minimum-image displacement
+              const int dsx = (int)((uint32_t)oxi_ - (uint32_t)oxj[k]);
+              const int dsy = (int)((uint32_t)oyi_ - (uint32_t)oyj[k]);
+              const int dsz = (int)((uint32_t)ozi_ - (uint32_t)ozj[k]);
+              dx = (real)__dmul_rn((double)dsx, pc.hd[0]);
+              dy = (real)__dmul_rn((double)dsy, pc.hd[1]);
+              dz = (real)__dmul_rn((double)dsz, pc.hd[2]);
+              r2 = (real)__dadd_rn(__dadd_rn(__dmul_rn((double)dx, (double)dx),
+                                             __dmul_rn((double)dy, (double)dy)),
+                                   __dmul_rn((double)dz, (double)dz));
+              in = ok && vj[k] && (double)r2 <= pc.rc2d;
+              ir2 = in ? (real)(1.0 / (double)r2) : (real)0;
+            } else {
+              dx = xi_ - xj[k];
+              dy = yi_ - yj[k];
+              dz = zi_ - zj[k];
+              r2 = (real)fmaf((float)dx, (float)dx, fmaf((float)dy, (float)dy, (float)(dz * dz)));
+              in = ok && (float)r2 < pc.rc2_lo;
+              bmin = fminf(bmin, fabsf((float)r2 - a.rc2_mid));
+              ir2 = in ? (real)rcp_approx((float)r2) : (real)0;
+            }
+            const real g = cp_terms<real, COUL, MULTI>(a, in, r2, ir2, qi_, qj[k], ti_, tj[k], acc);
+            fxj[k] -= g * dx; fyj[k] -= g * dy; fzj[k] -= g * dz;
+            if (COUNT) cntj[k] += in ? 1 : 0;
+            return g;
+          };
+          // The visited cluster may be one of the super-cluster's own (cdiag): its pairs with
+          // itself count once (particle a8 with particle h + 4k > a8). They are taken here, with
+          // the i particle read from shared memory and its force added by atomics, so that the
+          // loop below carries no exclusion.
+          uint32_t Mh = M;
+          if (cdiag >= 0 && cdiag < NC && ((M >> cdiag) & 1u)) {
+            Mh &= ~(1u << cdiag);
+            const int t = kClSize * cdiag + a8;
+            const bool vd = t < np && (asub < 0 || a8 == asub);
+            const uint4 sd = si[t];
+            const int ox = (int)(sd.x - rx), oy = (int)(sd.y - ry), oz = (int)(sd.z - rz);
+            const real xd = vd ? (real)((float)ox * pc.h[0]) : (real)3e18f;
+            const real yd = vd ? (real)((float)oy * pc.h[1]) : (real)3e18f;
+            const real zd = vd ? (real)((float)oz * pc.h[2]) : (real)3e18f;
+            real qd = (real)0;
+            if (COUL) qd = F64 ? (vd ? (real)a.set.qd[p0 + t] : (real)0) : (real)__uint_as_float(sd.w);
+            const int td = MULTI ? sti[t] : 0;
+            real fdx = (real)0, fdy = (real)0, fdz = (real)0;
+            int cd = 0;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              real dx, dy, dz;
+              bool in;
+              const real g = pair_one(vd && a8 < hh + 4 * k, xd, yd, zd, ox, oy, oz, qd, td, k,
+                                      dx, dy, dz, in);
+              fdx += g * dx; fdy += g * dy; fdz += g * dz;
+              if (COUNT) cd += in ? 1 : 0;
+            }
+            fdx += __shfl_xor_sync(FULL, fdx, 8); fdx += __shfl_xor_sync(FULL, fdx, 16);
+            fdy += __shfl_xor_sync(FULL, fdy, 8); fdy += __shfl_xor_sync(FULL, fdy, 16);
+            fdz += __shfl_xor_sync(FULL, fdz, 8); fdz += __shfl_xor_sync(FULL, fdz, 16);
+            if (COUNT) {
+              cd += __shfl_xor_sync(FULL, cd, 8);
+              cd += __shfl_xor_sync(FULL, cd, 16);
+            }
+            if (vd && hh < 3) {
+              const real v = hh == 0 ? fdx : (hh == 1 ? fdy : fdz);
+              long long *dst = a.facc + (int64_t)hh * N + p0 + t;
+              if (F64) fx_add(dst, (double)v, a.fscale_d, a.err);
+              else fx_add(dst, (float)v, a.fscale, a.err);
+            }
+            if (COUNT && vd && hh == 3 && cd) atomicAdd(a.nbr + p0 + t, cd);
+          }
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            if ((M >> c) & 1u) {
+            if ((Mh >> c) & 1u) {
 #pragma unroll
               for (int k = 0; k < 2; ++k) {
-                const bool ok = c != cdiag || a8 < hh + 4 * k;
-                real dx, dy, dz, r2, ir2;
+                real dx, dy, dz;
                 bool in;
-                if (F64) {
-                  // the offsets' difference (mod 2^32) is the exact minimum-image displacement
-                  const int dsx = (int)((uint32_t)oxi[c] - (uint32_t)oxj[k]);
-                  const int dsy = (int)((uint32_t)oyi[c] - (uint32_t)oyj[k]);
-                  const int dsz = (int)((uint32_t)ozi[c] - (uint32_t)ozj[k]);
-                  dx = (real)__dmul_rn((double)dsx, pc.hd[0]);
-                  dy = (real)__dmul_rn((double)dsy, pc.hd[1]);
-                  dz = (real)__dmul_rn((double)dsz, pc.hd[2]);
-                  r2 = (real)__dadd_rn(__dadd_rn(__dmul_rn((double)dx, (double)dx),
-                                                 __dmul_rn((double)dy, (double)dy)),
-                                       __dmul_rn((double)dz, (double)dz));
-                  in = ok && vi[c] && vj[k] && (double)r2 <= pc.rc2d;
-                  ir2 = in ? (real)(1.0 / (double)r2) : (real)0;
-                } else {
-                  dx = xi[c] - xj[k];
-                  dy = yi[c] - yj[k];
-                  dz = zi[c] - zj[k];
-                  r2 = (real)fmaf((float)dx, (float)dx, fmaf((float)dy, (float)dy, (float)(dz * dz)));
-                  in = ok && (float)r2 < pc.rc2_lo;
-                  band |= ok && (float)r2 >= pc.rc2_lo && (float)r2 <= pc.rc2_hi;
-                  ir2 = in ? (real)rcp_approx((float)r2) : (real)0;
-                }
-                const real g = cp_terms<real, COUL, MULTI>(a, in, r2, ir2, qi[c], qj[k], ti[c],
-                                                           tj[k], acc);
+                const real g = pair_one(!F64 || vi[c], xi[c], yi[c], zi[c], oxi[c], oyi[c], ozi[c], qi[c],
+                                        ti[c], k, dx, dy, dz, in);
                 fxi[c] += g * dx; fyi[c] += g * dy; fzi[c] += g * dz;
-                fxj[k] -= g * dx; fyj[k] -= g * dy; fzj[k] -= g * dz;
-                if (COUNT) { cnti[c] += in ? 1 : 0; cntj[k] += in ? 1 : 0; }
+                if (COUNT) cnti[c] += in ? 1 : 0;
               }
             }
           }
           // Band pairs (FP32 forms): the exact decision; a pair inside is added by atomics.
-          if (!F64 && __any_sync(FULL, band)) {
+          if (!F64 && __any_sync(FULL, bmin <= a.rc2_half)) {
             for (int c = cb; c < ce; ++c) {
               if (!((M >> c) & 1u)) continue;
               const int t = kClSize * c + a8;
-              if (t >= np) continue;
+              if (t >= np || (asub >= 0 && a8 != asub)) continue;
               const uint4 s = si[t];
               const float x0 = (float)(int)(s.x - rx) * pc.h[0];
               const float y0 = (float)(int)(s.y - ry) * pc.h[1];
@@ -576,23 +661,27 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
               }
             }
           }
-          // reaction on the visited cluster: sum over the 8 lanes sharing h, then lane a8 < 6
-          // adds component a8 % 3 of particle h + 4 (a8 / 3)
-          real v6[6] = {fxj[0], fyj[0], fzj[0], fxj[1], fyj[1], fzj[1]};
+          // Reaction on the visited cluster, reduce-scattered over the 8 lanes sharing h: lanes
+          // a8 < 4 end with particle h's sums, lanes a8 >= 4 with particle h + 4's, and lane
+          // a8 adds component a8 % 4 (x, y, z; the fourth lane has none).
+          {
+            real v6[6] = {fxj[0], fyj[0], fzj[0], fxj[1], fyj[1], fzj[1]};
 #pragma unroll
-          for (int e = 0; e < 6; ++e) {
-            v6[e] += __shfl_xor_sync(FULL, v6[e], 1);
-            v6[e] += __shfl_xor_sync(FULL, v6[e], 2);
-            v6[e] += __shfl_xor_sync(FULL, v6[e], 4);
-          }
-          if (a8 < 6) {
-            const int k = a8 / 3, d = a8 - 3 * k;
-            real v = v6[0];
+            for (int e = 0; e < 6; ++e) {
+              v6[e] += __shfl_xor_sync(FULL, v6[e], 1);
+              v6[e] += __shfl_xor_sync(FULL, v6[e], 2);
+              v6[e] += __shfl_xor_sync(FULL, v6[e], 4);
+            }
+            if (a8 < 6) {
+              const int k = a8 / 3, d = a8 - 3 * k;
+              real v = v6[0];
 #pragma unroll
-            for (int e = 1; e < 6; ++e) v = (a8 == e) ? v6[e] : v;
-            if (vj[k]) {
-              if (F64) fx_add(a.facc + (int64_t)d * N + vb + hh + 4 * k, (double)v, a.fscale_d, a.err);
-              else fx_add(a.facc + (int64_t)d * N + vb + hh + 4 * k, (float)v, a.fscale, a.err);
+              for (int e = 1; e < 6; ++e) v = (a8 == e) ? v6[e] : v;
+              if (vj[k]) {
+                long long *dst = a.facc + (int64_t)d * N + vb + hh + 4 * k;
+                if (F64) fx_add(dst, (double)v, a.fscale_d, a.err);
+                else fx_add(dst, (float)v, a.fscale, a.err);
+              }
             }
           }
           if (COUNT) {
@@ -618,7 +707,7 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
           cnti[c] += __shfl_xor_sync(FULL, cnti[c], 16);
         }
         const int t = kClSize * c + a8;
-        if ((c & 3) == hh && c >= cb && c < ce && t < np) {
+        if ((c & 3) == hh && vi[c]) {
           const int64_t pi = p0 + t;
           if (F64) {
             fx_add(a.facc + pi, (double)fxi[c], a.fscale_d, a.err);
@@ -633,7 +722,12 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? 12 : 20)) cpair_kerne
         }
       }
       __syncwarp();
-      cb = ce;
+      if (asub < 0) {
+        cb = ce;
+      } else if (++asub >= min(kClSize, np - kClSize * cb)) {
+        asub = -1;
+        ++cb;
+      }
     }
   }
   // block partials of the energies and virials (each pair counted once)
@@ -721,6 +815,11 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
     const double band = frame_band(X, c.rc, c.box, false);
     a.pc.rc2_lo = (float)(c.rc * c.rc * (1.0 - band));
     a.pc.rc2_hi = (float)(c.rc * c.rc * (1.0 + band));
+    // band test |r^2 - mid| <= half: half reaches past both FP32 edges by a few ulps (the
+    // edges are rounded to FP32; the difference r^2 - mid is exact near mid)
+    a.rc2_mid = (float)(c.rc * c.rc);
+    const double mid = a.rc2_mid, ulp = std::nextafter((float)mid, 3e38f) - (float)mid;
+    a.rc2_half = (float)(std::max((double)a.pc.rc2_hi - mid, mid - (double)a.pc.rc2_lo) + 4.0 * ulp);
     // box test: squared gap of FP32 frame boxes (each bound within 2u L/2, the gap within
     // u L more), widened so that no pair within r_c is lost
     const double u = std::ldexp(1.0, -24);

@@ -332,6 +332,9 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
   c.alpha = p->alpha; c.rc = p->r_c; c.r_core = rbl ? p->r_core : 0.0;
   c.C = p->coulomb_C; c.dt = p->dt; c.kappa = p->kappa;
   c.P = p->P; c.p_rbl = rbl ? p->p_rbl : 0; c.precision = p->precision;
+  // the cluster kernel evaluates about a quarter more candidate pairs than the per-particle
+  // kernel: cheaper in FP32, where its per-pair overhead is saved, not in the FP64 form
+  c.pair_cluster = p->precision != RBE_FP64;
   c.nt = p->n_types; c.seed = p->seed; c.replica = p->replica; c.rbl = rbl;
   c.stream = (cudaStream_t)cuda_stream;
   c.sum_q2 = q2;
@@ -630,7 +633,7 @@ int rbe_forces(rbe_handle h, uint64_t step, float *F_out, int F_on_device, doubl
                double *virial) {
   if (!h) return RBE_ERR_INVALID;
   Ctx &c = *h;
-  int rc = forces_common(h, step, true);
+  int rc = forces_common(h, step, false);  // no neighbour counts or RBL partners
   if (rc != RBE_OK) return rc;
   if (F_out) {
     RBE_CUDA_TRY(launch_scatter_forces(c, false));
@@ -965,7 +968,7 @@ int rbe_autotune(rbe_handle h, int reps, int *chosen) {
   }
   c.pair_test16 = best16 != 0;
   int best_cl = 0;
-  if (!c.rbl && cl_saved) {
+  if (!c.rbl) {
     c.pair_cluster = true;
     if (cpair_usable(c)) {
       float ms = 0.f;

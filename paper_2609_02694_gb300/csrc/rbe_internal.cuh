@@ -79,7 +79,7 @@ struct Ctx {
   double alpha = 0, rc = 0, r_core = 0, C = 0, dt = 0, kappa = 0;
   int P = 0, p_rbl = 0, precision = RBE_FP32_COMP, nt = 1, sub = 2;
   bool pair_test16 = true;  // packed half-precision candidate pre-test in the pair kernel
-  bool pair_cluster = false; // cluster-pair kernel (each pair once) for the main pair pass
+  bool pair_cluster = true;  // cluster-pair kernel (each pair once) for the main pair pass
   bool rbl_eager = false;   // RBL: evaluate every shell pair in the classifying pass
   int rbl_span = 0;         // RBL: group extent in x cells (0: automatic)
   uint64_t seed = 0;

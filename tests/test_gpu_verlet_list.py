@@ -88,7 +88,10 @@ def test_list_and_cells_agree_over_steps(orc):
         F_cell, E_cell, _ = hc.forces_f64(12)
         nbr_cell, _ = hc.neighbor_counts()
     assert np.array_equal(nbr_list, nbr_cell)
-    assert rel_l2(F_list, F_cell) < 2e-6
+    # the list kernel converts exact integer displacements; the cell traversal's cluster kernel
+    # rounds frame coordinates of up to ~25 A (about 1e-6 A each); both are within 1e-5 of the
+    # oracle (below)
+    assert rel_l2(F_list, F_cell) < 5e-6
     ref = oracle_all(orc, sy2, m, S)
     assert rel_l2(F_list, ref["F"]) < TOL_F32
     assert np.array_equal(nbr_list, ref["nbr"])
