@@ -41,7 +41,7 @@ BIN_BYTES = 114.0
 INTEGRATE_BYTES = 104.0
 # DRAM bytes (read + write) per launch of the dominant kernel on this workload, from one ncu
 # capture of the kernel as it stands
-TRAFFIC_BYTES = {"cells": 12.94e6, "list_skin_1.0": 2.4174e9}
+TRAFFIC_BYTES = {"cluster": 42.71e6, "cells": 12.94e6, "list_skin_1.0": 2.4174e9}
 
 
 def hbm_peak_gbs():
@@ -73,6 +73,8 @@ def parse():
                     help="ion counts of --config ljelec")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 form, e2e, error and CPU legs (profiling runs)")
+    ap.add_argument("--no-rbl", action="store_true",
+                    help="skip the 2^27-particle random batch list leg")
     ap.add_argument("--config", default="main",
                     choices=["main", "batch96", "sweep16m", "rbl134m", "n3000", "ljelec", "peaks"],
                     help="main: the benchmark line; the others print per-config JSON lines")
@@ -207,43 +209,44 @@ def sampled_error(orc, sy, F, m, S, n=32, seed=0):
 
 
 def cpu_oracle_step(orc, sy, P, n_sample, seed=0):
-    """One oracle force evaluation of the workload, sampled: the structure factor and
-    the k-space forces in full, the O(N) real-space sums for n_sample particles; returns
-    (extrapolated seconds per full step, seconds spent)."""
+    """A bounded sample of one force evaluation of the workload by the oracle as it stands:
+    the structure factor and k-space forces of the whole system (Eq. F_long_RBE), and the
+    O(N) real-space sums (Eqs. F_i, G_short, LJ) of n_sample random particles, which then
+    hold their complete forces. Returns (seconds, particles with complete forces)."""
     from paper_2609_02694_gb300 import synth
     m, S = orc.sample_k(1, 0, 0, sy.box, synth.ALPHA, P)
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(sy.n, n_sample, replace=False))
     t0 = time.perf_counter()
     orc.rbe_kspace(sy.s, sy.q, sy.box, synth.ALPHA, synth.COULOMB_C, m, S)
-    t1 = time.perf_counter()
     orc.real_space(sy.s, sy.q, sy.types, sy.box, synth.ALPHA, synth.R_CUT, synth.COULOMB_C,
                    sy.eps, sy.sig, i_list=idx)
-    t2 = time.perf_counter()
-    return (t1 - t0) + (t2 - t1) * sy.n / n_sample, t2 - t0
+    return time.perf_counter() - t0, n_sample
 
 
-def cpu_baseline_record(orc, sy, P, n_sample=512, n_sample_1=64):
+def cpu_baseline_record(orc, sy, P, n_sample=8192, n_sample_1=512):
     """The oracle as it stands, timed on the host cores with all its OpenMP threads and on
-    one thread: one step-0 force evaluation each (cpu_oracle_step), real-space sums sampled
-    and extrapolated. The thread count is restored afterwards."""
+    one thread: one sampled step-0 force evaluation each (cpu_oracle_step); the value is the
+    particles given complete forces per second measured, nothing extrapolated. The thread
+    count is restored afterwards."""
     cores = orc.num_threads()
-    t_all, spent = cpu_oracle_step(orc, sy, P, n_sample)
+    t_all, n_all = cpu_oracle_step(orc, sy, P, n_sample)
     orc.set_num_threads(1)
     try:
-        t_one, spent1 = cpu_oracle_step(orc, sy, P, n_sample_1, seed=1)
+        t_one, n_one = cpu_oracle_step(orc, sy, P, n_sample_1, seed=1)
     finally:
         orc.set_num_threads(cores)
 
     def sample(n, s):
-        return ("one step 0 force evaluation: full structure factor and k-space forces, O(N) "
-                f"real-space sums of {n} sampled particles extrapolated to {sy.n} "
-                f"({s:.1f} s measured)")
+        return ("one step-0 force evaluation of the workload: structure factor and k-space "
+                f"forces of all {sy.n} particles and the real-space sums of {n} random "
+                f"particles, which then have complete forces ({s:.2f} s measured); value = "
+                f"{n} / that time")
 
-    return {"value": sy.n / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": sample(n_sample, spent),
-            "single_thread": {"value": sy.n / t_one, "unit": UNIT, "cores": 1,
-                              "sample": sample(n_sample_1, spent1)}}
+    return {"value": n_all / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample(n_all, t_all),
+            "single_thread": {"value": n_one / t_one, "unit": UNIT, "cores": 1,
+                              "sample": sample(n_one, t_one)}}
 
 
 def run_reference(args):
@@ -254,28 +257,126 @@ def run_reference(args):
     sy, desc = workload(args)
     orc = oracle
     orc.lib()
-    n_sample = 256
-    for _ in range(args.warmup):
-        cpu_oracle_step(orc, sy, args.P, 64)
-    tot = spent = 0.0
+    n_sample = 1024
+    for k in range(args.warmup):
+        cpu_oracle_step(orc, sy, args.P, 64, seed=1000 + k)
+    tot = 0.0
+    done = 0
     for k in range(args.steps):
-        t, s = cpu_oracle_step(orc, sy, args.P, n_sample, seed=k)
+        t, n = cpu_oracle_step(orc, sy, args.P, n_sample, seed=k)
         tot += t
-        spent += s
-    value = sy.n * args.steps / tot
-    sample = (f"per step: full structure factor and k-space forces, O(N) real-space sums of "
-              f"{n_sample} sampled particles, extrapolated to all {sy.n}")
+        done += n
+    value = done / tot
+    sample = (f"per step: structure factor and k-space forces of all {sy.n} particles and the "
+              f"real-space sums of {n_sample} random particles, which then have complete "
+              f"forces; value = particles with complete forces / measured time")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc + ", FP64 CPU oracle"},
+            "config": {"workload": desc + ", FP64 CPU oracle, sampled rows"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0},
-            "measured_seconds": spent}
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def subbox_errors(orc, binding, stream, Ps):
+    """Errors on the 65,536-particle box of the workload's composition and density, in both
+    forms, at P modes: forces against the oracle on the same modes and against the full Ewald
+    sum (the RBE sampling error of Eq. F_long_RBE against Eq. F_i; Fourier modes of weight
+    >= 1e-6, charged particles only, as neutral ones have no k-space force), and the total
+    energy and pressure against the oracle on the same modes and against full Ewald."""
+    from paper_2609_02694_gb300 import synth
+    sm = synth.sub_box()
+    A, RC, C = synth.ALPHA, synth.R_CUT, synth.COULOMB_C
+    rs = orc.real_space(sm.s, sm.q, sm.types, sm.box, A, RC, C, sm.eps, sm.sig)
+    ch = sm.q != 0
+    Fe = np.zeros((sm.n, 3))
+    Fe[ch], Ue, We = orc.ewald_kspace_tol(sm.s[ch], sm.q[ch], sm.box, A, C, 1e-6)
+    Us = orc.self_energy(sm.q, A, C)
+    V = float(np.prod(sm.box))
+    K2 = (sm.mass[:, None] * sm.v ** 2).sum() / synth.ACCEL_KAPPA  # 2 K
+    U_e = rs["U_real"] + rs["U_lj"] + Ue - Us
+    p_e = (K2 + rs["W_real"] + rs["W_lj"] + We) / (3 * V)
+    F_e = rs["F"] + Fe
+    res = {"N": sm.n, "full_ewald": "Fourier modes of weight >= 1e-6"}
+    for P in Ps:
+        res[f"P{P}"] = _subbox_forms(orc, binding, stream, sm, P, rs, Us, V, K2, F_e, U_e, p_e)
+    return res
+
+
+def _subbox_forms(orc, binding, stream, sm, P, rs, Us, V, K2, F_e, U_e, p_e):
+    from paper_2609_02694_gb300 import synth
+    A, RC, C = synth.ALPHA, synth.R_CUT, synth.COULOMB_C
+    m, S = orc.sample_k(1, 0, 0, sm.box, A, P)
+    Fk, Uk, Wk = orc.rbe_kspace(sm.s, sm.q, sm.box, A, C, m, S)
+    U_o = rs["U_real"] + rs["U_lj"] + Uk - Us
+    p_o = (K2 + rs["W_real"] + rs["W_lj"] + Wk) / (3 * V)
+    F_o = rs["F"] + Fk
+    out = {}
+    for form in ("fp32_comp", "fp64"):
+        with binding.from_system(sm, P=P, alpha=A, r_c=RC, coulomb_C=C, dt=1.0,
+                                 kappa=synth.ACCEL_KAPPA, precision=form,
+                                 stream=stream.cuda_stream) as h:
+            F, E, W = h.forces_f64(0)
+            mg, _ = h.sample_k(0)
+        p = (K2 + W["total"]) / (3 * V)
+        out[form] = {"modes_equal_oracle_draw": bool(np.array_equal(mg, m)),
+                     "force_rel_l2_vs_oracle_same_modes": rel(F, F_o),
+                     "force_rel_l2_vs_full_ewald": rel(F, F_e),
+                     "energy_rel_vs_oracle_same_modes": abs(E["total"] - U_o) / abs(U_o),
+                     "pressure_rel_vs_oracle_same_modes": abs(p - p_o) / abs(p_o),
+                     "energy_rel_vs_full_ewald": abs(E["total"] - U_e) / abs(U_e),
+                     "pressure_rel_vs_full_ewald": abs(p - p_e) / abs(p_e)}
+    return out
+
+
+def p1000_leg(binding, sy, mk, stream, flush, skin):
+    """The headline workload at P = 1,000 modes, FP32-compensated and FP64 forms: full
+    Verlet steps timed as the headline (L2 flushed between steps), each form autotuned."""
+    out = {}
+    for form, K in (("fp32_comp", 10), ("fp64", 3)):
+        kw = dict(mk)
+        kw["P"] = 1000
+        h = binding.from_system(sy, precision=form, **kw)
+        h.set_neighbor_list(skin)
+        tuned = h.autotune(1)
+        h.step(2)
+        ms, _ = time_steps(h, stream, flush, K)
+        out[form] = {"value": sy.n * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+                     "steps": K, "autotuned": tuned}
+        h.close()
+    return out
+
+
+def rbl_leg(binding, stream, K=2):
+    """2^27 particles (5% charged, density 0.1), random batch list r_core = 5 A, r_s = 10 A,
+    p = 10, P = 500, FP32-compensated: a few Verlet steps and the device bytes per particle."""
+    import torch
+    from paper_2609_02694_gb300 import synth
+    t0 = time.perf_counter()
+    sy = synth.make_system(1 << 27, density=0.1, frac_charged=0.05, seed=5)
+    h = binding.from_system(sy, P=500, alpha=synth.ALPHA, r_c=synth.R_CUT,
+                            coulomb_C=synth.COULOMB_C, dt=1.0, kappa=synth.ACCEL_KAPPA,
+                            r_core=5.0, p_rbl=10, stream=stream.cuda_stream)
+    n = sy.n
+    del sy
+    setup_s = time.perf_counter() - t0
+    h.step(1)
+    torch.cuda.synchronize()
+    ms = _timed(lambda: h.step(1), K, stream)
+    out = {"N": n, "value": n * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+           "steps": K, "device_bytes_per_particle": h.memory_bytes() / n,
+           "setup_s": setup_s,
+           "config": "5% +/-1e, density 0.1, RBL r_core 5 A, r_s 10 A, p 10, P 500, FP32-comp"}
+    h.close()
+    return out
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
 
 
 def pick_traversal(binding, sy, mk, args, stream):
@@ -391,11 +492,14 @@ def run_ours(args):
                                     "events in the graph; the headline ran without them"},
             "roofline": {"bound": "alu",
                          "kernel": ("list_pair_kernel (Verlet-list LJ)" if skin > 0
+                                    else "cpair_kernel (cluster pairs, LJ; with its "
+                                         "fixed-point finish)" if tuned.get("pair_cluster")
                                     else "pair_kernel (cell-list LJ)"),
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak if achieved else None,
-                         "traffic": (TRAFFIC_BYTES["cells"] if skin == 0 else
-                                     TRAFFIC_BYTES["list_skin_1.0"] if skin == 1.0 else None),
+                         "traffic": (TRAFFIC_BYTES["list_skin_1.0"] if skin == 1.0 else None
+                                     if skin > 0 else TRAFFIC_BYTES["cluster"]
+                                     if tuned.get("pair_cluster") else TRAFFIC_BYTES["cells"]),
                          "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch",
                          "pair_ms_per_launch": pair_ms,
                          "units": f"{pairs:.0f} unique pairs x {PAIR_FLOPS:.0f} flops",
@@ -465,6 +569,13 @@ def run_ours(args):
                        "h2d_bytes_per_step": sy.n * 3 * 8,
                        "d2h_bytes_per_step": sy.n * 3 * 4 + 8 * (6 + 4) + 4,
                        "call": "rbe_set_positions(host f64) + rbe_forces(host f32 F, energies)"}
+        # errors on the 65,536-particle box (same modes; full Ewald), headline P and 1,000
+        line["errors_65536_box"] = subbox_errors(orc, binding, stream, (args.P, 1000))
+        # the workload at P = 1,000 in both forms
+        line["p1000"] = p1000_leg(binding, sy, mk, stream, flush, skin)
+        # the largest single-GPU system: 2^27 particles with the random batch list
+        if not args.no_rbl:
+            line["rbl_134m"] = rbl_leg(binding, stream)
         # CPU baseline: the oracle on a bounded sample of the same workload
         line["cpu_baseline"] = cpu_baseline_record(orc, sy, args.P)
     h.close()

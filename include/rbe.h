@@ -191,7 +191,8 @@ enum {
   RBE_PH_BIN = 1,        /* list displacement check, linked-cell binning and reordering */
   RBE_PH_SAMPLE = 2,     /* Philox mode sampler */
   RBE_PH_SF = 3,         /* structure factor + FP64 combine */
-  RBE_PH_LIST = 4,       /* Verlet-list build (zero on steps without one, and in cell mode) */
+  RBE_PH_LIST = 4,       /* neighbour structures: the Verlet-list build (zero on steps without
+                            one), or the cluster-pair kernel's per-step cluster tables */
   RBE_PH_PAIR = 5,       /* main real-space kernel (cell list or Verlet list LJ[+Coulomb], or RBL) */
   RBE_PH_PAIR2 = 6,      /* charged-subset Coulomb pass, or the RBL mean-force correction */
   RBE_PH_GATHER = 7,     /* k-space force gather */

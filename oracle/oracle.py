@@ -38,6 +38,8 @@ def lib():
                                      ct.c_int, _i32p, ct.c_double, _f64p, _dp, _dp]
         L.orc_ewald_kspace.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, ct.c_double,
                                        ct.c_double, _f64p, _dp, _dp]
+        L.orc_ewald_kspace_tol.argtypes = [ct.c_int64, _u32p, _f64p, _f64p, ct.c_double,
+                                           ct.c_double, ct.c_double, _f64p, _dp, _dp]
         L.orc_self_energy.argtypes = [ct.c_int64, _f64p, ct.c_double, ct.c_double]
         L.orc_self_energy.restype = ct.c_double
         L.orc_min_image_r2.argtypes = [_u32p, _u32p, _f64p, _f64p]
@@ -67,7 +69,7 @@ def lib():
         L.orc_set_num_threads.argtypes = [ct.c_int]
         L.orc_set_num_threads.restype = None
         for name in ("orc_kdim_table", "orc_sample_k", "orc_rho", "orc_rbe_kspace",
-                     "orc_ewald_kspace", "orc_real_space", "orc_cells", "orc_rbl", "orc_rbl_rows",
+                     "orc_ewald_kspace", "orc_ewald_kspace_tol", "orc_real_space", "orc_cells", "orc_rbl", "orc_rbl_rows",
                      "orc_brute_coulomb", "orc_vv_drift", "orc_vv_kick", "orc_nh_half"):
             getattr(L, name).restype = ct.c_int
         _LIB = L
@@ -152,6 +154,18 @@ def ewald_kspace(s, q, box, alpha, C):
     U, W = ct.c_double(), ct.c_double()
     _check(lib().orc_ewald_kspace(len(s), s, _f(q), _f(box), float(alpha), float(C), F,
                                   ct.byref(U), ct.byref(W)), "ewald_kspace")
+    return F, U.value, W.value
+
+
+def ewald_kspace_tol(s, q, box, alpha, C, tol):
+    """Full Ewald k-space force, energy and virial over the modes whose weight
+    exp(-k^2/4 alpha) is at least tol (Eqs. U_Coul_Fourier, F_i at a stated accuracy)."""
+    s = _s(s)
+    F = np.zeros((len(s), 3), np.float64)
+    U, W = ct.c_double(), ct.c_double()
+    _check(lib().orc_ewald_kspace_tol(len(s), s, _f(q), _f(box), float(alpha), float(C),
+                                      float(tol), F, ct.byref(U), ct.byref(W)),
+           "ewald_kspace_tol")
     return F, U.value, W.value
 
 

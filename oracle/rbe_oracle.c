@@ -209,6 +209,11 @@ int orc_rbe_kspace(int64_t N, const uint32_t *s, const double *q, const double b
 
 /* Full Ewald k-space sum (Eqs. U_Coul_Fourier and F_i) over every m != 0 with
  * |m_d| <= M_d, where M_d is the half-width at which exp(-k^2/4 alpha) < 2^-53. */
+/* Eqs. U_Coul_Fourier and F_i summed over the P modes of mlist (frees mlist). */
+static int ewald_over_modes(int64_t N, const uint32_t *s, const double *q, const double box[3],
+                            double alpha, double C, int64_t P, int32_t *mlist, double *F,
+                            double *U, double *W);
+
 int orc_ewald_kspace(int64_t N, const uint32_t *s, const double *q, const double box[3],
                      double alpha, double C, double *F, double *U, double *W) {
   if (N < 0) return -1;
@@ -224,6 +229,39 @@ int orc_ewald_kspace(int64_t N, const uint32_t *s, const double *q, const double
         mlist[3 * P] = mx; mlist[3 * P + 1] = my; mlist[3 * P + 2] = mz;
         ++P;
       }
+  return ewald_over_modes(N, s, q, box, alpha, C, P, mlist, F, U, W);
+}
+
+/* The same sum truncated at a stated accuracy, the way Ewald and mesh solvers are run in
+ * practice (the paper's own reference runs use a mesh solver at a 1e-4 tolerance, Sec. 3.1):
+ * only the modes k != 0 whose weight exp(-k^2 / 4 alpha) is at least tol enter, a sphere
+ * |k|^2 <= 4 alpha ln(1/tol), in the same ascending (m_z, m_y, m_x) order. */
+int orc_ewald_kspace_tol(int64_t N, const uint32_t *s, const double *q, const double box[3],
+                         double alpha, double C, double tol, double *F, double *U, double *W) {
+  if (N < 0 || !(tol > 0.0) || !(tol < 1.0)) return -1;
+  const double k2max = 4.0 * alpha * log(1.0 / tol);
+  int M[3];
+  for (int d = 0; d < 3; ++d) M[d] = (int)ceil(box[d] * sqrt(k2max) / (2.0 * M_PI));
+  int64_t nm = (int64_t)(2 * M[0] + 1) * (2 * M[1] + 1) * (2 * M[2] + 1);
+  int32_t *mlist = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)nm);
+  int64_t P = 0;
+  for (int mz = -M[2]; mz <= M[2]; ++mz)
+    for (int my = -M[1]; my <= M[1]; ++my)
+      for (int mx = -M[0]; mx <= M[0]; ++mx) {
+        if (mx == 0 && my == 0 && mz == 0) continue;
+        const int32_t m[3] = {mx, my, mz};
+        double k[3];
+        kvec(m, box, k);
+        if (k[0] * k[0] + k[1] * k[1] + k[2] * k[2] > k2max) continue;
+        mlist[3 * P] = mx; mlist[3 * P + 1] = my; mlist[3 * P + 2] = mz;
+        ++P;
+      }
+  return ewald_over_modes(N, s, q, box, alpha, C, P, mlist, F, U, W);
+}
+
+static int ewald_over_modes(int64_t N, const uint32_t *s, const double *q, const double box[3],
+                            double alpha, double C, int64_t P, int32_t *mlist, double *F,
+                            double *U, double *W) {
   double V = box[0] * box[1] * box[2];
   double *rho = (double *)malloc(sizeof(double) * 2 * (size_t)P);
   double *g = (double *)malloc(sizeof(double) * (size_t)P); /* exp(-k^2/4a)/k^2 */

@@ -71,6 +71,9 @@ int orc_rbe_kspace(int64_t N, const uint32_t *s, const double *q, const double b
  * Pinned by the NaCl Madelung constant, brute-force image sums and alpha-invariance. */
 int orc_ewald_kspace(int64_t N, const uint32_t *s, const double *q, const double box[3],
                      double alpha, double C, double *F, double *U, double *W);
+/* Full Ewald truncated at weight tol: modes k != 0 with exp(-k^2 / 4 alpha) >= tol only. */
+int orc_ewald_kspace_tol(int64_t N, const uint32_t *s, const double *q, const double box[3],
+                         double alpha, double C, double tol, double *F, double *U, double *W);
 
 /* Self energy C sqrt(alpha/pi) sum q^2 (Eq. U_self). */
 double orc_self_energy(int64_t N, const double *q, double alpha, double C);

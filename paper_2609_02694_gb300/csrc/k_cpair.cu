@@ -777,16 +777,23 @@ bool cpair_usable(const Ctx &c) {
   return c.box[0] - 2.0 * c.rc > 2.0 * c.box[0] / c.grid.n[0];
 }
 
-cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts) {
+cudaError_t launch_cluster_tables(Ctx &c) {
   const int b = c.cur;
   const int nrows = c.grid.n[1] * c.grid.n[2];
-  const int nc = cpair_nc(c);
-  cluster_rows_kernel<<<1, 1024, 0, c.stream>>>(c.cell_start, c.grid.n[0], nrows, nc, c.cl_base,
-                                                c.sc_base);
+  cluster_rows_kernel<<<1, 1024, 0, c.stream>>>(c.cell_start, c.grid.n[0], nrows, cpair_nc(c),
+                                                c.cl_base, c.sc_base);
   const int64_t ccap = cpair_clusters_bound(c);
   cluster_bounds_kernel<<<(unsigned)((ccap + 255) / 256), 256, 0, c.stream>>>(
       c.s[b], c.s[b] + c.N, c.s[b] + 2 * c.N, c.cell_start, c.grid.n[0], nrows, c.cl_base, ccap,
       c.cl_lo, c.cl_hi);
+  return cudaGetLastError();
+}
+
+// The pair pass itself (the tables of launch_cluster_tables must be current), then the
+// fixed-point finish.
+cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts) {
+  const int b = c.cur;
+  const int nrows = c.grid.n[1] * c.grid.n[2];
   ClusterArgs a;
   a.set.sx = c.s[b]; a.set.sy = c.s[b] + c.N; a.set.sz = c.s[b] + 2 * c.N;
   a.set.qf = c.qf[b]; a.set.qd = c.qd[b]; a.set.type = c.type[b];

@@ -593,7 +593,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   }
   set_pretest_band(c, a, c.rc, wrap);
   const bool fp64 = c.precision == RBE_FP64;
-  if (!wrap && cpair_usable(c)) {
+  if (cpair_usable(c)) {
     // each pair once over clusters (k_cpair.cu); it writes F, the Coulomb pass adds to it
     const cudaError_t e = launch_cluster_pair(c, fused, multi, want_counts);
     if (e != cudaSuccess) return e;

@@ -151,6 +151,8 @@ int force_pipeline(Ctx &c, bool debug) {
   if (c.vl_on) {
     RBE_CUDA_TRY(launch_list_build(c));
     RBE_CUDA_TRY(launch_list_commit(c));
+  } else if (!c.rbl && cpair_usable(c)) {
+    RBE_CUDA_TRY(launch_cluster_tables(c));  // the cluster-pair kernel's per-step tables
   }
   mark(c, RBE_PH_PAIR);
   if (c.rbl) RBE_CUDA_TRY(launch_rbl(c, debug));

@@ -248,6 +248,7 @@ cudaError_t launch_pair(Ctx &c, bool want_counts);   // main pass, then mark, th
 bool cpair_usable(const Ctx &c);
 int64_t cpair_blocks_bound(const Ctx &c);
 int64_t cpair_clusters_bound(const Ctx &c);
+cudaError_t launch_cluster_tables(Ctx &c);  // per-row offsets and per-cluster bounds
 cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts);
 void mark(Ctx &c, int k);  // record the profiling event k (no-op when profiling is off)
 cudaError_t launch_rbl(Ctx &c, bool want_debug);

@@ -14,6 +14,6 @@ def test_cpu_baseline_record_fields():
     rec = bench.cpu_baseline_record(oracle, sy, 50, n_sample=32, n_sample_1=16)
     assert oracle.num_threads() == before
     assert rec["kind"] == "oracle" and rec["unit"] == bench.UNIT and rec["cores"] == before
-    assert rec["value"] > 0 and "32 sampled" in rec["sample"]
+    assert rec["value"] > 0 and "32 random particles" in rec["sample"]
     one = rec["single_thread"]
-    assert one["cores"] == 1 and one["value"] > 0 and "16 sampled" in one["sample"]
+    assert one["cores"] == 1 and one["value"] > 0 and "16 random particles" in one["sample"]

@@ -306,3 +306,43 @@ def test_rbe_variance_scales_as_one_over_p(orc):
                        for seed in range(n)])
         var[P] = Fs.var(axis=0).sum()
     assert var[4] / var[16] == pytest.approx(4.0, rel=0.2)
+
+
+def test_truncated_ewald_rock_salt(orc):
+    """Ewald sum truncated at mode weight 1e-10 still gives the rock-salt Madelung energy
+    (to the accuracy the truncation allows) and zero forces by symmetry."""
+    n, a, C = 4, 2.0, synth.COULOMB_C
+    L = n * a
+    idx = np.array([(x, y, z) for z in range(n) for y in range(n) for x in range(n)])
+    s = (idx * (TWO32 / n)).astype(np.uint64).astype(np.uint32)
+    q = np.where(idx.sum(axis=1) % 2 == 0, 1.0, -1.0)
+    box = np.array([L, L, L])
+    alpha, rc = 2.7, 0.4999 * L
+    rs = orc.real_space(s, q, np.zeros(len(q), np.int32), box, alpha, rc, C, [0.0], [1.0])
+    Fk, Uk, _ = orc.ewald_kspace_tol(s, q, box, alpha, C, 1e-10)
+    U = rs["U_real"] + Uk - orc.self_energy(q, alpha, C)
+    want = -len(q) * _madelung() * C / (2.0 * a)
+    assert U == pytest.approx(want, rel=1e-8)
+    assert np.abs(rs["F"] + Fk).max() < 1e-8 * abs(want)
+
+
+def test_truncated_ewald_converges_to_full(orc):
+    """The truncated sum is the full sum restricted to the sphere exp(-k^2/4 alpha) >= tol:
+    a tolerance below every mode weight the full sum keeps reproduces it, and the error of a
+    coarse tolerance falls with the tolerance and stays of its order."""
+    box = np.array([15.0, 16.0, 17.0])
+    s, q = _random_system(30, box, seed=21)
+    alpha, C = 0.3, 1.0
+    F0, U0, W0 = orc.ewald_kspace(s, q, box, alpha, C)
+    F1, U1, W1 = orc.ewald_kspace_tol(s, q, box, alpha, C, 1e-17)
+    assert np.abs(F1 - F0).max() < 1e-12 * np.abs(F0).max()
+    assert U1 == pytest.approx(U0, rel=1e-12) and W1 == pytest.approx(W0, rel=1e-11)
+    errs = []
+    for tol in (1e-3, 1e-5, 1e-7):
+        F, U, _ = orc.ewald_kspace_tol(s, q, box, alpha, C, tol)
+        errs.append(np.linalg.norm(F - F0) / np.linalg.norm(F0))
+        assert errs[-1] < 30 * tol
+    assert errs[0] > errs[1] > errs[2]
+    # invalid tolerances are refused
+    with pytest.raises(ValueError):
+        orc.ewald_kspace_tol(s, q, box, alpha, C, 0.0)
