@@ -270,6 +270,21 @@ int rbe_measure_peak(int kind, double *ops_per_s, double *ms);
 /* Bytes of device memory held by the handle. */
 int rbe_get_memory(rbe_handle h, int64_t *bytes);
 
+/* Checkpoint and resume (the paper does not describe one; the counter-based draws make it
+ * exact). rbe_save writes the handle's dynamic state to the file `path`: the step counter,
+ * the positions on the 2^-32 grid and the velocities (exact, id order) and the thermostat
+ * state, with a fingerprint of the system and parameters. rbe_load reads such a file into a
+ * handle created with the same N, box, charges' count, parameters and LJ table
+ * (RBE_ERR_STATE otherwise; RBE_ERR_INVALID for an unreadable or malformed file); the next
+ * rbe_step or rbe_forces evaluates the forces of the loaded state. Because every mode and
+ * random batch draw is a pure function of (seed, replica, step) and the cell order is a pure
+ * function of the positions, a run resumed with rbe_load continues bit for bit as the
+ * uninterrupted run, with the cell traversal or the random batch list; with a Verlet list the
+ * list is rebuilt when needed and forces agree up to FP32 summation order. Both calls
+ * synchronise the handle's stream. */
+int rbe_save(rbe_handle h, const char *path);
+int rbe_load(rbe_handle h, const char *path);
+
 /* Read and clear the device error flags; returns the first of RBE_ERR_SAMPLER,
  * RBE_ERR_NONFINITE, RBE_ERR_CAPACITY that is set, else RBE_OK. Synchronises. */
 int rbe_check_device(rbe_handle h);

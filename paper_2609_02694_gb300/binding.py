@@ -94,6 +94,8 @@ def lib(build_if_missing: bool = False):
     L.rbe_set_neighbor_list.argtypes = [ct.c_void_p, ct.c_double, ct.c_int]
     L.rbe_get_neighbor_list.argtypes = [ct.c_void_p, _vp]
     L.rbe_structure_factor_noalloc.argtypes = [_vp, _vp, ct.c_int64, _vp, ct.c_int, _vp, _vp]
+    L.rbe_save.argtypes = [h, ct.c_char_p]
+    L.rbe_load.argtypes = [h, ct.c_char_p]
     L.rbe_destroy.argtypes = [h]
     L.rbe_decision_band.argtypes = [_vp, ct.c_double, _vp, ct.c_int]
     L.rbe_decision_band.restype = ct.c_double
@@ -329,6 +331,14 @@ class RBE:
         return dict(builds=int(st[0]), evaluations=int(st[1]), max_len=int(st[2]),
                     max_len_charged=int(st[3]), capacity=int(st[4]),
                     capacity_charged=int(st[5]))
+
+    def save(self, path: str):
+        """Write the dynamic state (step, positions, velocities, thermostat) to a file."""
+        _check(lib().rbe_save(self._h, os.fsencode(path)), "rbe_save")
+
+    def load(self, path: str):
+        """Resume from a file written by save() on a handle with the same system."""
+        _check(lib().rbe_load(self._h, os.fsencode(path)), "rbe_load")
 
     def memory_bytes(self) -> int:
         b = ct.c_int64()

@@ -238,6 +238,21 @@ __global__ void set_positions_kernel(const double *__restrict__ pos, const int32
   }
 }
 
+// Checkpoint load: state given in id order (row-major per particle) into the sorted slots.
+template <typename V>
+__global__ void gather_state_kernel(const uint32_t *__restrict__ s_id, const double *__restrict__ v_id,
+                                    const int32_t *__restrict__ id, int64_t N,
+                                    uint32_t *__restrict__ s, V *__restrict__ v) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t o = (int64_t)id[k] * 3;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    s[d * N + k] = s_id[o + d];
+    v[d * N + k] = (V)v_id[o + d];
+  }
+}
+
 __global__ void scatter_int_kernel(const int32_t *__restrict__ src, const int32_t *__restrict__ id,
                                    int64_t N, int width, int32_t *__restrict__ dst) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -377,6 +392,16 @@ cudaError_t launch_set_positions(Ctx &c) {
   if (c.N == 0) return cudaSuccess;
   set_positions_kernel<<<nblk(c.N, 256), 256, 0, c.stream>>>(c.pos_stage, c.id[b], c.N, c.box[0],
                                                              c.box[1], c.box[2], c.s[b]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_state(Ctx &c, const uint32_t *s_id, const double *v_id) {
+  const int b = c.cur;
+  if (c.N == 0) return cudaSuccess;
+  if (c.precision == RBE_FP64)
+    gather_state_kernel<double><<<nblk(c.N, 256), 256, 0, c.stream>>>(s_id, v_id, c.id[b], c.N, c.s[b], c.vd[b]);
+  else
+    gather_state_kernel<float><<<nblk(c.N, 256), 256, 0, c.stream>>>(s_id, v_id, c.id[b], c.N, c.s[b], c.vf[b]);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 // operation runs in the kernels of k_*.cu, on the caller's stream.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1263,6 +1264,109 @@ int rbe_batch_destroy(rbe_batch b) {
   if (!b) return RBE_OK;
   cudaStreamSynchronize(b->stream);
   return batch_free(b);
+}
+
+// ---------------------------------------------------------------------------------------
+// Checkpoint / resume. File layout (little-endian, native sizes):
+//   "RBECKPT1"; the fingerprint (N, box, alpha, r_c, r_core, C, dt, kappa, P, p_rbl,
+//   precision, n_types, seed, replica, the LJ A/B table); the step counter; the thermostat
+//   (on, T, tau, kB, primed, its 7 device scalars); s (N x 3 uint32) and v (N x 3 double), id
+//   order.
+namespace {
+const char kCkptMagic[8] = {'R', 'B', 'E', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHead {
+  int64_t N;
+  double box[3], alpha, rc, r_core, C, dt, kappa;
+  int32_t P, p_rbl, precision, nt;
+  uint64_t seed;
+  uint32_t replica, pad;
+  double ljA[kMaxTypes * kMaxTypes], ljB[kMaxTypes * kMaxTypes];
+  uint64_t step;
+  int32_t nvt, primed;
+  double T0, tau, kB, thermo[7];
+};
+
+void ckpt_head(const Ctx &c, CkptHead &hd) {
+  std::memset(&hd, 0, sizeof(hd));
+  hd.N = c.N;
+  for (int d = 0; d < 3; ++d) hd.box[d] = c.box[d];
+  hd.alpha = c.alpha; hd.rc = c.rc; hd.r_core = c.r_core; hd.C = c.C; hd.dt = c.dt;
+  hd.kappa = c.kappa; hd.P = c.P; hd.p_rbl = c.p_rbl; hd.precision = c.precision; hd.nt = c.nt;
+  hd.seed = c.seed; hd.replica = c.replica;
+  for (int k = 0; k < c.nt * c.nt; ++k) { hd.ljA[k] = c.lj.Ad[k]; hd.ljB[k] = c.lj.Bd[k]; }
+}
+}  // namespace
+
+int rbe_save(rbe_handle h, const char *path) {
+  if (!h || !path) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  CkptHead hd;
+  ckpt_head(c, hd);
+  hd.step = c.step;
+  hd.nvt = c.nvt ? 1 : 0;
+  hd.primed = c.nvt_primed ? 1 : 0;
+  hd.T0 = c.T0; hd.tau = c.tau; hd.kB = c.kB;
+  if (c.thermo) {
+    RBE_CUDA_TRY(cudaMemcpyAsync(hd.thermo, c.thermo, sizeof(hd.thermo), cudaMemcpyDeviceToHost,
+                                 c.stream));
+  }
+  std::vector<uint32_t> s(3 * (size_t)c.N);
+  std::vector<double> v(3 * (size_t)c.N);
+  int rc = rbe_get_state(h, nullptr, v.data(), s.data());  // synchronises
+  if (rc != RBE_OK) return rc;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return RBE_ERR_INVALID;
+  bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+            std::fwrite(s.data(), sizeof(uint32_t), s.size(), f) == s.size() &&
+            std::fwrite(v.data(), sizeof(double), v.size(), f) == v.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? RBE_OK : RBE_ERR_INVALID;
+}
+
+int rbe_load(rbe_handle h, const char *path) {
+  if (!h || !path) return RBE_ERR_INVALID;
+  Ctx &c = *h;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return RBE_ERR_INVALID;
+  char magic[8];
+  CkptHead hd;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+            std::fread(&hd, sizeof(hd), 1, f) == 1;
+  if (!ok) { std::fclose(f); return RBE_ERR_INVALID; }
+  CkptHead mine;
+  ckpt_head(c, mine);
+  // the checkpoint must come from a handle with the same system and parameters
+  const size_t fp = offsetof(CkptHead, step);
+  if (std::memcmp(&hd, &mine, fp) != 0) { std::fclose(f); return RBE_ERR_STATE; }
+  std::vector<uint32_t> s(3 * (size_t)c.N);
+  std::vector<double> v(3 * (size_t)c.N);
+  ok = std::fread(s.data(), sizeof(uint32_t), s.size(), f) == s.size() &&
+       std::fread(v.data(), sizeof(double), v.size(), f) == v.size();
+  std::fclose(f);
+  if (!ok) return RBE_ERR_INVALID;
+  for (double x : v)
+    if (!std::isfinite(x)) return RBE_ERR_INVALID;
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  // staging: the positions in the 3N-float buffer, the velocities in the 3N-double one
+  RBE_CUDA_TRY(cudaMemcpy(c.outf, s.data(), sizeof(uint32_t) * s.size(), cudaMemcpyHostToDevice));
+  RBE_CUDA_TRY(cudaMemcpy(c.pos_stage, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+  RBE_CUDA_TRY(launch_gather_state(c, reinterpret_cast<const uint32_t *>(c.outf), c.pos_stage));
+  c.step = hd.step;
+  RBE_CUDA_TRY(launch_set_step(c, c.step));
+  if (hd.nvt) {
+    int rs = rbe_set_thermostat(h, hd.T0, hd.tau, hd.kB);
+    if (rs != RBE_OK) return rs;
+    RBE_CUDA_TRY(cudaMemcpy(c.thermo, hd.thermo, sizeof(hd.thermo), cudaMemcpyHostToDevice));
+    c.nvt_primed = hd.primed != 0;
+  } else if (c.nvt) {
+    int rs = rbe_set_thermostat(h, 0.0, 0.0, 0.0);
+    if (rs != RBE_OK) return rs;
+  }
+  drop_graphs(c);
+  c.have_forces = false;  // the next step evaluates the forces of the loaded state
+  RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  return RBE_OK;
 }
 
 int rbe_check_device(rbe_handle h) {

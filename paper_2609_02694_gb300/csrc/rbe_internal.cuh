@@ -270,6 +270,8 @@ cudaError_t launch_step_advance(Ctx &c);
 cudaError_t launch_scatter_forces(Ctx &c, bool to_double);
 cudaError_t launch_scatter_state(Ctx &c, int what);  // 0: positions, 1: velocities, 2: s
 cudaError_t launch_set_positions(Ctx &c);
+// Checkpoint load: positions (uint32) and velocities (double), id order, into the sorted slots.
+cudaError_t launch_gather_state(Ctx &c, const uint32_t *s_id, const double *v_id);
 cudaError_t launch_scatter_int(Ctx &c, const int32_t *src_sorted, int32_t *dst_id, int width);
 
 // Scalars in Ctx::scal (device doubles).
