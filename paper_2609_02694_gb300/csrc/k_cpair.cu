@@ -269,9 +269,12 @@ __device__ __forceinline__ real cp_terms(const ClusterArgs &a, bool in, real r2,
 // The kernel: one warp per super-cluster.
 
 template <typename real, bool COUL, bool MULTI, bool COUNT>
-// (occupancy: 20 warps per SM for the FP32 LJ pass, fewer for the register-heavy Coulomb and
+// (occupancy: 24 warps per SM for the FP32 LJ pass, fewer for the register-heavy Coulomb and
 // FP64 instances)
-__global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (COUL ? 12 : 20)))
+#ifndef RBE_CP_MINB
+#define RBE_CP_MINB 24
+#endif
+__global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (COUL ? 12 : RBE_CP_MINB)))
     cpair_kernel(const ClusterArgs a) {
   constexpr bool F64 = sizeof(real) == 8;
   constexpr int NC = F64 ? 4 : 8;          // clusters per super-cluster
@@ -280,6 +283,9 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
   __shared__ uint4 si[NP];                 // s_x, s_y, s_z, charge bits
   __shared__ int32_t sti[MULTI ? NP : 1];
   __shared__ float4 ibl[NC], ibh[NC];      // i-cluster boxes in frame coordinates
+  // FP32 forms: the group's i particles in frame coordinates (x, y, z, charge), read once
+  // per i-cluster and visit; slots outside the group hold a point no j can reach
+  __shared__ float4 sif[F64 ? 1 : NP];
   __shared__ int32_t seg_beg[kCpMaxSeg], seg_pre[kCpMaxSeg + 1];
   const int lane = threadIdx.x, a8 = lane & 7, hh = lane >> 3;
   const int w = blockIdx.x;
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
       const uint32_t rx = xlo + ((xhi - xlo) >> 1), ry = ylo + ((yhi - ylo) >> 1),
                      rz = zlo + ((zhi - zlo) >> 1);
       // i particles of this lane: particle a8 of each cluster of the group
-      real xi[NC], yi[NC], zi[NC], fxi[NC], fyi[NC], fzi[NC], qi[NC];
+      real fxi[NC], fyi[NC], fzi[NC], qi[NC];
       int oxi[NC], oyi[NC], ozi[NC], ti[NC], cnti[NC];
       bool vi[NC];
 #pragma unroll
@@ -349,18 +355,21 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
         vi[c] = v;
         const uint4 s = si[t];
         oxi[c] = (int)(s.x - rx); oyi[c] = (int)(s.y - ry); ozi[c] = (int)(s.z - rz);
-        if (!F64) {
-          xi[c] = v ? (real)((float)oxi[c] * pc.h[0]) : (real)3e18f;
-          yi[c] = v ? (real)((float)oyi[c] * pc.h[1]) : (real)3e18f;
-          zi[c] = v ? (real)((float)ozi[c] * pc.h[2]) : (real)3e18f;
-        } else {
-          xi[c] = yi[c] = zi[c] = (real)0;  // the FP64 form works on the integer offsets
-        }
         qi[c] = COUL ? (real)__uint_as_float(s.w) : (real)0;
         if (COUL && F64 && v) qi[c] = (real)a.set.qd[p0 + t];
         ti[c] = MULTI ? sti[t] : 0;
         fxi[c] = fyi[c] = fzi[c] = (real)0;
         cnti[c] = 0;
+      }
+      if (!F64) {
+        for (int t = lane; t < NP; t += 32) {
+          const int c = t / kClSize, a_ = t % kClSize;
+          const bool v = c >= cb && c < ce && t < np && (asub < 0 || a_ == asub);
+          const uint4 s = si[t];
+          sif[t] = v ? make_float4((float)(int)(s.x - rx) * pc.h[0], (float)(int)(s.y - ry) * pc.h[1],
+                                   (float)(int)(s.z - rz) * pc.h[2], __uint_as_float(s.w))
+                     : make_float4(3e18f, 3e18f, 3e18f, 0.f);
+        }
       }
       // i-cluster boxes in the frame (lanes cb..ce-1)
       if (lane < NC) {
@@ -616,11 +625,13 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             if ((Mh >> c) & 1u) {
+              const float4 pi4 = F64 ? make_float4(0.f, 0.f, 0.f, 0.f) : sif[kClSize * c + a8];
 #pragma unroll
               for (int k = 0; k < 2; ++k) {
                 real dx, dy, dz;
                 bool in;
-                const real g = pair_one(!F64 || vi[c], xi[c], yi[c], zi[c], oxi[c], oyi[c], ozi[c], qi[c],
+                const real g = pair_one(!F64 || vi[c], (real)pi4.x, (real)pi4.y, (real)pi4.z,
+                                        oxi[c], oyi[c], ozi[c], COUL && !F64 ? (real)pi4.w : qi[c],
                                         ti[c], k, dx, dy, dz, in);
                 fxi[c] += g * dx; fyi[c] += g * dy; fzi[c] += g * dz;
                 if (COUNT) cnti[c] += in ? 1 : 0;
