@@ -54,6 +54,7 @@ struct ClusterArgs {
   const int32_t *cl_base;      // nrows + 1: first global cluster of each row
   const int32_t *sc_base;      // nrows + 1: first super-cluster of each row
   const uint4 *cl_lo, *cl_hi;  // per cluster: (min s_x, s_y, s_z, first particle), (max..., count)
+  const uint4 *s4;             // FP32 forms: packed (s_x, s_y, s_z, q bits) of every particle
   int nrows;
   long long *facc;             // 3 x N fixed-point forces (x block, y, z)
   int64_t N;
@@ -530,10 +531,11 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
             oxj[k] = oyj[k] = ozj[k] = 0;
             qj[k] = (real)0;
             if (!F64) {
-              xj[k] = vj[k] ? (real)((float)(int)(a.set.sx[p] - rx) * pc.h[0]) : (real)-3e18f;
-              yj[k] = vj[k] ? (real)((float)(int)(a.set.sy[p] - ry) * pc.h[1]) : (real)-3e18f;
-              zj[k] = vj[k] ? (real)((float)(int)(a.set.sz[p] - rz) * pc.h[2]) : (real)-3e18f;
-              if (COUL) qj[k] = (real)a.set.qf[p];
+              const uint4 pj = __ldg(&a.s4[p]);
+              xj[k] = vj[k] ? (real)((float)(int)(pj.x - rx) * pc.h[0]) : (real)-3e18f;
+              yj[k] = vj[k] ? (real)((float)(int)(pj.y - ry) * pc.h[1]) : (real)-3e18f;
+              zj[k] = vj[k] ? (real)((float)(int)(pj.z - rz) * pc.h[2]) : (real)-3e18f;
+              if (COUL) qj[k] = (real)__uint_as_float(pj.w);
             } else {
               oxj[k] = (int)(a.set.sx[p] - rx);
               oyj[k] = (int)(a.set.sy[p] - ry);
@@ -815,6 +817,7 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
   a.ljAd = c.lj.Ad[0]; a.ljBd = c.lj.Bd[0]; a.ljA12d = c.lj.A12d[0]; a.ljB6d = c.lj.B6d[0];
   a.table = reinterpret_cast<const LJTable *>(c.lj_dev);
   a.cl_base = c.cl_base; a.sc_base = c.sc_base; a.cl_lo = c.cl_lo; a.cl_hi = c.cl_hi;
+  a.s4 = c.cp4;
   a.nrows = nrows;
   a.facc = c.facc;
   a.N = c.N;

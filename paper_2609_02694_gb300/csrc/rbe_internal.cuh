@@ -109,6 +109,8 @@ struct Ctx {
   long long *facc = nullptr;
   int32_t *cl_base = nullptr, *sc_base = nullptr;
   uint4 *cl_lo = nullptr, *cl_hi = nullptr;
+  uint4 *cp4 = nullptr;        // packed (s_x, s_y, s_z, q bits), sorted order, written by the
+                               // binning for the cluster kernel's j loads (FP32 forms)
   // charged subset
   uint32_t *cs = nullptr;
   float *cqf = nullptr;
