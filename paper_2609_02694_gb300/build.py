@@ -16,7 +16,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librbe_gb300.so")
 SOURCES = ["rbe_api.cu", "k_sample.cu", "k_bin.cu", "k_kspace.cu", "k_pair.cu", "k_rbl.cu",
-           "k_integrate.cu", "rbe_noalloc.cu", "k_probe.cu", "k_list.cu", "k_cpair.cu"]
+           "k_integrate.cu", "rbe_noalloc.cu", "k_probe.cu", "k_list.cu", "k_cpair.cu",
+           "k_coul.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I" + INCLUDE]

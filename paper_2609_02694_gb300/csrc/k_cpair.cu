@@ -851,7 +851,8 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
   }
   a.err = c.err;
   if (want_counts) cudaMemsetAsync(c.nbr, 0, sizeof(int32_t) * c.N, c.stream);
-  const int64_t blocks = cpair_blocks_bound(c);
+  // every slot of the pass's partial range (blocks past the last super-cluster write zeros)
+  const int64_t blocks = c.n_pair_blk;
   const dim3 g((unsigned)blocks), bl(32);
   const bool fp64 = c.precision == RBE_FP64;
 #define RBE_CP_LAUNCH(R, CO, MU)                                                             \

@@ -405,6 +405,12 @@ cudaError_t launch_gather_state(Ctx &c, const uint32_t *s_id, const double *v_id
   return cudaGetLastError();
 }
 
+void zero_partials_tail(Ctx &c, int64_t off, int64_t written, int64_t capacity) {
+  if (written >= capacity) return;
+  cudaMemsetAsync(c.epart + off + written * NQ_PAIR, 0,
+                  sizeof(double) * (size_t)(capacity - written) * NQ_PAIR, c.stream);
+}
+
 cudaError_t launch_scatter_int(Ctx &c, const int32_t *src_sorted, int32_t *dst_id, int width) {
   const int b = c.cur;
   if (c.N == 0) return cudaSuccess;

@@ -196,6 +196,7 @@ cudaError_t launch_list_pair(Ctx &c, bool want_counts) {
     if (fp64) list_launch<double, true, false>(la, c.N, multi, c.stream);
     else list_launch<float, true, false>(la, c.N, multi, c.stream);
   }
+  zero_partials_tail(c, c.off_pair, nblk(c.N, kPairWarps * 32), c.n_pair_blk);
   mark(c, RBE_PH_PAIR2);
   if (!fused && c.Nq > 0) {
     ListArgs lq = la;
@@ -210,6 +211,7 @@ cudaError_t launch_list_pair(Ctx &c, bool want_counts) {
     lq.s4 = c.cs4;
     if (fp64) list_launch<double, false, true>(lq, c.Nq, false, c.stream);
     else list_launch<float, false, true>(lq, c.Nq, false, c.stream);
+    zero_partials_tail(c, c.off_coul, nblk(c.Nq, kPairWarps * 32), c.n_coul_blk);
   }
   return cudaGetLastError();
 }

@@ -597,32 +597,19 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
     // each pair once over clusters (k_cpair.cu); it writes F, the Coulomb pass adds to it
     const cudaError_t e = launch_cluster_pair(c, fused, multi, want_counts);
     if (e != cudaSuccess) return e;
-  } else if (fused) {
-    if (fp64) launch_one<double, true, true>(a, c.N, multi, wrap, c.stream);
-    else launch_one<float, true, true>(a, c.N, multi, wrap, c.stream);
   } else {
-    if (fp64) launch_one<double, true, false>(a, c.N, multi, wrap, c.stream);
-    else launch_one<float, true, false>(a, c.N, multi, wrap, c.stream);
+    if (fused) {
+      if (fp64) launch_one<double, true, true>(a, c.N, multi, wrap, c.stream);
+      else launch_one<float, true, true>(a, c.N, multi, wrap, c.stream);
+    } else {
+      if (fp64) launch_one<double, true, false>(a, c.N, multi, wrap, c.stream);
+      else launch_one<float, true, false>(a, c.N, multi, wrap, c.stream);
+    }
+    zero_partials_tail(c, c.off_pair, pair_blocks(c.N), c.n_pair_blk);
   }
   mark(c, RBE_PH_PAIR2);
-  if (!fused) {
-    if (c.Nq > 0) {
-      PairArgs b2 = a;
-      b2.set.sx = c.cs; b2.set.sy = c.cs + c.Nq; b2.set.sz = c.cs + 2 * c.Nq;
-      b2.set.qf = c.cqf; b2.set.qd = c.cqd; b2.set.type = nullptr;
-      b2.set.cell_start = c.ccell_start; b2.set.map = c.cmap; b2.set.n = c.Nq;
-      b2.accumulate = 1;
-      // FP32 pre-test: the dilute charged subset's groups then span more cells (the half-
-      // precision test bounds a group's extent), so fewer groups walk their stencils
-      b2.smax16 = 0;
-      set_pretest_band(c, b2, c.rc, wrap);
-      b2.trim = 0;  // rows of the dilute subset are short: trimming costs more than it saves
-      b2.epart = c.epart + c.off_coul;
-      b2.nbr = nullptr;
-      if (fp64) launch_one<double, false, true>(b2, c.Nq, false, wrap, c.stream);
-      else launch_one<float, false, true>(b2, c.Nq, false, wrap, c.stream);
-    }
-  }
+  // the charged subset's Coulomb pass (k_coul.cu), added to the forces the main pass wrote
+  if (!fused && c.Nq > 0) return launch_coulomb_subset(c, c.cq4);
   return cudaGetLastError();
 }
 

@@ -111,6 +111,7 @@ struct Ctx {
   uint4 *cl_lo = nullptr, *cl_hi = nullptr;
   uint4 *cp4 = nullptr;        // packed (s_x, s_y, s_z, q bits), sorted order, written by the
                                // binning for the cluster kernel's j loads (FP32 forms)
+  uint4 *cq4 = nullptr;        // the same for the charged subset (its Coulomb pass)
   // charged subset
   uint32_t *cs = nullptr;
   float *cqf = nullptr;
@@ -252,6 +253,10 @@ int64_t cpair_blocks_bound(const Ctx &c);
 int64_t cpair_clusters_bound(const Ctx &c);
 cudaError_t launch_cluster_tables(Ctx &c);  // per-row offsets and per-cluster bounds
 cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts);
+// Coulomb pass over the charged subset (k_coul.cu): one warp per charged particle; its grid
+// (the partial slots of the pass) for nq charged particles.
+int64_t coul_blocks(int64_t nq);
+cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4);
 void mark(Ctx &c, int k);  // record the profiling event k (no-op when profiling is off)
 cudaError_t launch_rbl(Ctx &c, bool want_debug);
 cudaError_t launch_list_check(Ctx &c);    // rebuild flag from the displacements
@@ -264,6 +269,9 @@ cudaError_t launch_kinetic(Ctx &c);
 cudaError_t launch_thermostat(Ctx &c, int mode);  // 0: end + next start half, 1: start half only
 cudaError_t launch_totals(Ctx &c);
 int64_t partials_compact_count(int64_t nblk);
+// The totals sum every slot of a pass's partial range: a pass whose grid writes fewer slots
+// than the range holds clears the rest (another kernel may have filled them before).
+void zero_partials_tail(Ctx &c, int64_t off, int64_t written, int64_t capacity);
 // Relative half-width of the band around r^2 inside which the exact FP64 decision is taken,
 // for an FP32 r^2 formed from FP32 frame coordinates with |x_d| <= X[d] (at least 1e-5).
 double frame_band(const double X[3], double r, const double box[3], bool wrap);

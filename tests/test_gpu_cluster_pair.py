@@ -152,3 +152,37 @@ def test_cluster_pair_wide_groups_split(orc):
     ref = orc.total_forces(sy.s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig, m, S)
     assert np.array_equal(nbr, ref["nbr"])
     assert rel_l2(F, ref["F"]) < 1e-5
+
+
+def test_switching_passes_keeps_energies(orc):
+    """The energy totals sum every per-block partial slot of a pass. Switching one handle
+    between the per-particle kernel, the cluster kernel and the Verlet list (whose grids write
+    different numbers of slots) leaves the same energies as a fresh handle, and the oracle's."""
+    sy = synth.make_system(20000, density=0.1, frac_charged=0.1, seed=8)
+    P = 64
+
+    def fresh(cl):
+        with binding.from_system(sy, P=P, alpha=ALPHA, r_c=RC, coulomb_C=C) as h:
+            h.set_tuning("pair_cluster", cl)
+            return h.forces_f64(2)[1:]
+
+    E_cl, W_cl = fresh(1)
+    E_pp, W_pp = fresh(0)
+    with binding.from_system(sy, P=P, alpha=ALPHA, r_c=RC, coulomb_C=C) as h:
+        h.set_tuning("pair_cluster", 0)
+        h.forces_f64(2)
+        h.set_tuning("pair_cluster", 1)
+        _, E1, W1 = h.forces_f64(2)
+        h.set_neighbor_list(1.0)
+        h.forces_f64(2)
+        h.set_neighbor_list(0.0)
+        _, E2, W2 = h.forces_f64(2)
+        h.set_tuning("pair_cluster", 0)
+        _, E3, W3 = h.forces_f64(2)
+        m, S = sampled.oracle_modes(orc, h, sy, P, 2)
+    assert E1 == E_cl and W1 == W_cl
+    assert E2 == E_cl and W2 == W_cl
+    assert E3 == E_pp and W3 == W_pp
+    ref = orc.total_forces(sy.s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig, m, S)
+    assert E1["lj"] == pytest.approx(ref["U_lj"], rel=2e-6)
+    assert E1["real"] == pytest.approx(ref["U_real"], rel=1e-5)
