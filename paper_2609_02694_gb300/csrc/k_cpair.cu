@@ -159,23 +159,20 @@ __global__ void __launch_bounds__(256) cluster_bounds_kernel(
 
 // F = fixed-point sums / scale (overwriting), and the sums cleared for the next pass. The
 // 64-bit sum converts as its two 32-bit halves (a 64-bit integer conversion is slow here):
-// v = hi 2^32 + lo with hi signed and lo unsigned.
+// v = hi 2^32 + lo with hi signed and lo unsigned; FP32 forms take the FP32 factors
+// sh = 2^32 / scale and sl = 1 / scale (no FP64 work per element), the FP64 form the FP64 ones.
 template <typename real>
 __global__ void __launch_bounds__(256) cpair_finalize_kernel(long long *__restrict__ facc,
                                                              real *__restrict__ F, int64_t n3,
-                                                             double inv_scale) {
+                                                             float sh, float sl, double inv_scale) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n3) return;
   const long long v = facc[k];
   facc[k] = 0;
   const int hi = (int)(v >> 32);
   const unsigned lo = (unsigned)(v & 0xffffffffll);
-  if (sizeof(real) == 8) {
-    F[k] = (real)(((double)hi * 4294967296.0 + (double)lo) * inv_scale);
-  } else {
-    const float s = (float)inv_scale;
-    F[k] = (real)fmaf((float)hi, (float)(4294967296.0 * inv_scale), (float)lo * s);
-  }
+  if (sizeof(real) == 8) F[k] = (real)(((double)hi * 4294967296.0 + (double)lo) * inv_scale);
+  else F[k] = (real)fmaf((float)hi, sh, (float)lo * sl);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -870,8 +867,12 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
 #undef RBE_CP_LAUNCH
   const int64_t n3 = 3 * c.N;
   const unsigned fb = (unsigned)((n3 + 255) / 256);
-  if (fp64) cpair_finalize_kernel<double><<<fb, 256, 0, c.stream>>>(c.facc, c.Fd, n3, 1.0 / kFixScale64);
-  else cpair_finalize_kernel<float><<<fb, 256, 0, c.stream>>>(c.facc, c.F, n3, 1.0 / kFixScale32);
+  if (fp64)
+    cpair_finalize_kernel<double><<<fb, 256, 0, c.stream>>>(c.facc, c.Fd, n3, 0.f, 0.f,
+                                                            1.0 / kFixScale64);
+  else
+    cpair_finalize_kernel<float><<<fb, 256, 0, c.stream>>>(
+        c.facc, c.F, n3, (float)(4294967296.0 / kFixScale32), (float)(1.0 / kFixScale32), 0.0);
   return cudaGetLastError();
 }
 
