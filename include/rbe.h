@@ -292,17 +292,27 @@ int rbe_check_device(rbe_handle h);
 /* Free every device buffer and the handle. NULL is accepted. */
 int rbe_destroy(rbe_handle h);
 
-/* Batched replicas: independent systems (each its own rbe_init handle, typically with its
- * own `replica` key) advanced together. One CUDA graph holds one Verlet step of every
- * replica as parallel branches, so one graph launch per step advances the whole batch
- * and small replicas run concurrently.
+/* Batched replicas: independent systems of any sizes (each its own rbe_init handle,
+ * typically with its own `replica` key) advanced together by one CUDA graph launch per step.
+ * Replicas whose Verlet steps launch the same kernels in the same block shapes form a class
+ * (same precision, cell traversal, Coulomb arrangement, tuning); every kernel of the step
+ * then runs once for the whole class, over the concatenated grids of its replicas, each
+ * block reading its replica's own arguments (modes, structure factor, particle arrays) from
+ * a table. Results are bit-identical to stepping each replica alone. Classes run as
+ * parallel branches of the graph; a replica in no class of two or more (a random batch list
+ * or Verlet-list traversal, or a configuration of its own) runs its own step as a branch.
  *  handles  n handles created on the same device; the batch does not own them
  *  cuda_stream  stream the graph is launched on (NULL = legacy default stream)
+ * The classes and tables are planned at the first rbe_batch_step (or rbe_batch_info) from
+ * the handles' configuration then; change no handle's tuning, traversal or thermostat after.
  * rbe_batch_step is asynchronous; each handle's own getters read its state afterwards
  * (they synchronise the handle's stream, so synchronise cuda_stream first). */
 typedef struct rbe_batch_s *rbe_batch;
 int rbe_batch_create(rbe_batch *b, int n, const rbe_handle *handles, void *cuda_stream);
 int rbe_batch_step(rbe_batch b, int nsteps);
+/* The batch plan: number of classes, replicas run by class launches, and kernel launches
+ * per batch step (any output may be NULL). Plans the batch if rbe_batch_step has not. */
+int rbe_batch_info(rbe_batch b, int32_t *n_classes, int32_t *n_batched, int64_t *kernels);
 int rbe_batch_destroy(rbe_batch b);
 
 /* Structure factor rho_l = sum_j q_j exp(2 pi i sum_d m_ld s_jd / 2^32) of N particles for P

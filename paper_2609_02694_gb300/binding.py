@@ -85,6 +85,7 @@ def lib(build_if_missing: bool = False):
     L.rbe_batch_create.argtypes = [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(ct.c_void_p), _vp]
     L.rbe_batch_step.argtypes = [ct.c_void_p, ct.c_int]
     L.rbe_batch_destroy.argtypes = [ct.c_void_p]
+    L.rbe_batch_info.argtypes = [ct.c_void_p, _vp, _vp, _vp]
     L.rbe_measure_peak.argtypes = [ct.c_int, _vp, _vp]
     L.rbe_set_thermostat.argtypes = [ct.c_void_p, ct.c_double, ct.c_double, ct.c_double]
     L.rbe_get_thermostat.argtypes = [ct.c_void_p, _vp]
@@ -363,6 +364,13 @@ class Batch:
 
     def step(self, n: int = 1):
         _check(lib().rbe_batch_step(self._b, n), "rbe_batch_step")
+
+    def info(self):
+        """(classes, replicas run by the batched launches, kernel launches per step)."""
+        k, nb, kern = ct.c_int32(), ct.c_int32(), ct.c_int64()
+        _check(lib().rbe_batch_info(self._b, ct.addressof(k), ct.addressof(nb),
+                                    ct.addressof(kern)), "rbe_batch_info")
+        return k.value, nb.value, kern.value
 
     def close(self):
         if getattr(self, "_b", None) is not None and self._b.value:

@@ -19,7 +19,10 @@ SOURCES = ["rbe_api.cu", "k_sample.cu", "k_bin.cu", "k_kspace.cu", "k_pair.cu", 
            "k_integrate.cu", "rbe_noalloc.cu", "k_probe.cu", "k_list.cu", "k_cpair.cu",
            "k_coul.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
+# -fmad=false: no implicit multiply-add contraction; the kernels write every fused
+# multiply-add out (fmaf / fma), so any two compilations of a kernel body (a replica's own
+# launch and the batched launch over many replicas) round alike and agree bit for bit.
+NVCC_FLAGS = ["-O3", "-lineinfo", "-fmad=false", "-std=c++17", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I" + INCLUDE]
 
 

@@ -27,31 +27,51 @@ constexpr int kScanBlock = kScanThreads * kScanItems;
 // true when a gated kernel has nothing to do this step
 __device__ __forceinline__ bool gated_off(const int32_t *gate) { return gate && *gate == 0; }
 
-__global__ void bin_count_kernel(int64_t N, const uint32_t *__restrict__ s,
-                                 const float *__restrict__ q, int n0, int n1, int n2,
-                                 int32_t *__restrict__ count, int32_t *__restrict__ ccount,
-                                 int32_t *__restrict__ key, int32_t *__restrict__ off,
-                                 const int32_t *__restrict__ gate) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N || gated_off(gate)) return;
-  const int cx = cell_of(s[i], n0), cy = cell_of(s[N + i], n1), cz = cell_of(s[2 * N + i], n2);
-  const int c = cx + n0 * (cy + n1 * cz);
-  key[i] = c;
-  off[i] = atomicAdd(&count[c], 1);
-  if (q[i] != 0.0f) atomicAdd(&ccount[c], 1);
+struct CountArgs {
+  int64_t N;
+  const uint32_t *s;
+  const float *q;
+  int n0, n1, n2;
+  int32_t *count, *ccount, *key, *off;
+  const int32_t *gate;
+};
+
+__device__ __forceinline__ void bin_count_body(const CountArgs &a, int bx, int) {
+  const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
+  const int64_t N = a.N;
+  if (i >= N || gated_off(a.gate)) return;
+  const int cx = cell_of(a.s[i], a.n0), cy = cell_of(a.s[N + i], a.n1),
+            cz = cell_of(a.s[2 * N + i], a.n2);
+  const int c = cx + a.n0 * (cy + a.n1 * cz);
+  a.key[i] = c;
+  a.off[i] = atomicAdd(&a.count[c], 1);
+  if (a.q[i] != 0.0f) atomicAdd(&a.ccount[c], 1);
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(256), bin_count_kernel, CountArgs, bin_count_body)
+
+// Arguments of the three scan passes and the provisional scatter.
+struct ScanArgs {
+  const int32_t *cnt;
+  int32_t *start, *blk;
+  int64_t ncell, nblk;
+  const int32_t *gate;
+};
+struct ScatterArgs {
+  int64_t N;
+  const int32_t *key, *off, *start;
+  int32_t *tmp;
+  const int32_t *gate;
+};
 
 // Exclusive scan, three passes. Arrays hold two independent sequences (blockIdx.y).
-__global__ void __launch_bounds__(kScanThreads)
-    scan_block_kernel(const int32_t *__restrict__ cnt, int32_t *__restrict__ start,
-                      int32_t *__restrict__ blk, int64_t ncell, int64_t nblk,
-                      const int32_t *__restrict__ gate) {
+__device__ __forceinline__ void scan_block_body(const ScanArgs &a, int bx, int) {
   __shared__ int32_t warp_tot[kScanThreads / 32];
-  if (gated_off(gate)) return;
+  if (gated_off(a.gate)) return;
+  const int64_t ncell = a.ncell, nblk = a.nblk;
   const int which = blockIdx.y;
-  const int32_t *in = cnt + which * ncell;
-  int32_t *out = start + which * (ncell + 1);
-  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+  const int32_t *in = a.cnt + which * ncell;
+  int32_t *out = a.start + which * (ncell + 1);
+  const int64_t base = (int64_t)bx * kScanBlock + (int64_t)threadIdx.x * kScanItems;
   int32_t v[kScanItems];
   int32_t tsum = 0;
 #pragma unroll
@@ -87,17 +107,18 @@ __global__ void __launch_bounds__(kScanThreads)
     if (idx < ncell) out[idx] = run;
     run += v[k];
   }
-  if (threadIdx.x == kScanThreads - 1) blk[which * nblk + blockIdx.x] = run;  // block total
+  if (threadIdx.x == kScanThreads - 1) a.blk[which * nblk + bx] = run;  // block total
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(kScanThreads), scan_block_kernel, ScanArgs, scan_block_body)
 
-__global__ void __launch_bounds__(1024)
-    scan_top_kernel(int32_t *__restrict__ blk, int64_t nblk, int32_t *__restrict__ start,
-                    int64_t ncell, const int32_t *__restrict__ gate) {
+// One block per sequence.
+__device__ __forceinline__ void scan_top_body(const ScanArgs &a, int bx, int) {
   __shared__ int32_t warp_tot[32];
   __shared__ int32_t carry_s;
-  if (gated_off(gate)) return;
-  const int which = blockIdx.x;
-  int32_t *b = blk + which * nblk;
+  if (gated_off(a.gate)) return;
+  const int64_t ncell = a.ncell, nblk = a.nblk;
+  const int which = bx;
+  int32_t *b = a.blk + which * nblk;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry_s = 0;
   __syncthreads();
@@ -130,31 +151,30 @@ __global__ void __launch_bounds__(1024)
     if (threadIdx.x == 1023) carry_s = excl + v;
     __syncthreads();
   }
-  if (threadIdx.x == 0) start[which * (ncell + 1) + ncell] = carry_s;
+  if (threadIdx.x == 0) a.start[which * (ncell + 1) + ncell] = carry_s;
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(1024), scan_top_kernel, ScanArgs, scan_top_body)
 
-__global__ void __launch_bounds__(kScanThreads)
-    scan_add_kernel(int32_t *__restrict__ start, const int32_t *__restrict__ blk,
-                    int64_t ncell, int64_t nblk, const int32_t *__restrict__ gate) {
-  if (gated_off(gate)) return;
+__device__ __forceinline__ void scan_add_body(const ScanArgs &a, int bx, int) {
+  if (gated_off(a.gate)) return;
+  const int64_t ncell = a.ncell;
   const int which = blockIdx.y;
-  int32_t *out = start + which * (ncell + 1);
-  const int32_t add = blk[which * nblk + blockIdx.x];
-  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  int32_t *out = a.start + which * (ncell + 1);
+  const int32_t add = a.blk[which * a.nblk + bx];
+  const int64_t base = (int64_t)bx * kScanBlock;
   for (int k = threadIdx.x; k < kScanBlock; k += kScanThreads) {
     const int64_t idx = base + k;
     if (idx < ncell) out[idx] += add;
   }
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(kScanThreads), scan_add_kernel, ScanArgs, scan_add_body)
 
-__global__ void bin_scatter_kernel(int64_t N, const int32_t *__restrict__ key,
-                                   const int32_t *__restrict__ off,
-                                   const int32_t *__restrict__ start, int32_t *__restrict__ tmp,
-                                   const int32_t *__restrict__ gate) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N || gated_off(gate)) return;
-  tmp[start[key[i]] + off[i]] = (int32_t)i;
+__device__ __forceinline__ void bin_scatter_body(const ScatterArgs &a, int bx, int) {
+  const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
+  if (i >= a.N || gated_off(a.gate)) return;
+  a.tmp[a.start[a.key[i]] + a.off[i]] = (int32_t)i;
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(256), bin_scatter_kernel, ScatterArgs, bin_scatter_body)
 
 struct PermuteArgs {
   int64_t N, Nq, ncell;
@@ -209,10 +229,10 @@ constexpr int kCellsPerWarp = 4;
 // members among themselves), then move every field to the final slot. When no cell of the four
 // holds more than 8 particles (dilute systems), each cell gets 8 lanes; otherwise the warp
 // takes the cells one after another, 32 members at a time.
-__global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
+__device__ __forceinline__ void bin_rank_permute_body(const PermuteArgs &a, int bx, int) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t c0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kCellsPerWarp;
+  const int64_t c0 = (((int64_t)bx * blockDim.x + threadIdx.x) >> 5) * kCellsPerWarp;
   if (c0 >= a.ncell || gated_off(a.gate)) return;
   int cnt4 = 0;
   if (lane < kCellsPerWarp && c0 + lane < a.ncell)
@@ -268,13 +288,15 @@ __global__ void __launch_bounds__(256) bin_rank_permute_kernel(PermuteArgs a) {
     }
   }
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(256), bin_rank_permute_kernel, PermuteArgs,
+                   bin_rank_permute_body)
 
 // Order kept (no list build this step): copy every field to the same slot of the other
 // buffer and refresh the charged subset's coordinates through cmap. Threads [0, N) copy
 // particles, threads [N, N + Nq) charged slots.
-__global__ void __launch_bounds__(256) bin_identity_kernel(PermuteArgs a) {
+__device__ __forceinline__ void bin_identity_body(const PermuteArgs &a, int bx, int) {
   if (a.gate && *a.gate != 0) return;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t k = (int64_t)bx * blockDim.x + threadIdx.x;
   const int64_t N = a.N, Nq = a.Nq;
   if (k < N) {
     const uint32_t sx = a.s0[k], sy = a.s0[N + k], sz = a.s0[2 * N + k];
@@ -296,27 +318,36 @@ __global__ void __launch_bounds__(256) bin_identity_kernel(PermuteArgs a) {
     if (a.cs4) a.cs4[pc] = make_uint4(sx, sy, sz, __float_as_uint(a.cqf[pc]));
   }
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(256), bin_identity_kernel, PermuteArgs, bin_identity_body)
 
 cudaError_t launch_bin_sort(Ctx &c) {
   const int64_t N = c.N, nc = c.grid.ncell;
   const int b0 = c.cur, b1 = 1 - c.cur;
   const int32_t *gate = c.vl_on ? c.vl_flags : nullptr;  // list mode: sort only on a build
-  cudaError_t e = cudaMemsetAsync(c.cell_count, 0, sizeof(int32_t) * 2 * nc, c.stream);
+  cudaError_t e = fill_zero(c, c.cell_count, 2 * nc);
   if (e != cudaSuccess) return e;
   if (N > 0) {
-    bin_count_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(
-        N, c.s[b0], c.qf[b0], c.grid.n[0], c.grid.n[1], c.grid.n[2], c.cell_count,
-        c.ccell_count, c.key, c.off, gate);
+    const CountArgs a{N, c.s[b0], c.qf[b0], c.grid.n[0], c.grid.n[1], c.grid.n[2],
+                      c.cell_count, c.ccell_count, c.key, c.off, gate};
+    e = dispatch(c, bin_count_kernel, bin_count_kernel_b, dim3((unsigned)((N + 255) / 256)),
+                 dim3(256), 0, a);
+    if (e != cudaSuccess) return e;
   }
   const int64_t nblk = c.scan_nblk;
-  scan_block_kernel<<<dim3((unsigned)nblk, 2), kScanThreads, 0, c.stream>>>(
-      c.cell_count, c.cell_start, c.scan_blk, nc, nblk, gate);
-  scan_top_kernel<<<2, 1024, 0, c.stream>>>(c.scan_blk, nblk, c.cell_start, nc, gate);
-  scan_add_kernel<<<dim3((unsigned)nblk, 2), kScanThreads, 0, c.stream>>>(c.cell_start,
-                                                                         c.scan_blk, nc, nblk, gate);
+  const ScanArgs sa{c.cell_count, c.cell_start, c.scan_blk, nc, nblk, gate};
+  e = dispatch(c, scan_block_kernel, scan_block_kernel_b, dim3((unsigned)nblk, 2),
+               dim3(kScanThreads), 0, sa);
+  if (e != cudaSuccess) return e;
+  e = dispatch(c, scan_top_kernel, scan_top_kernel_b, dim3(2), dim3(1024), 0, sa);
+  if (e != cudaSuccess) return e;
+  e = dispatch(c, scan_add_kernel, scan_add_kernel_b, dim3((unsigned)nblk, 2),
+               dim3(kScanThreads), 0, sa);
+  if (e != cudaSuccess) return e;
   if (N > 0) {
-    bin_scatter_kernel<<<(unsigned)((N + 255) / 256), 256, 0, c.stream>>>(
-        N, c.key, c.off, c.cell_start, c.tmp, gate);
+    const ScatterArgs xa{N, c.key, c.off, c.cell_start, c.tmp, gate};
+    e = dispatch(c, bin_scatter_kernel, bin_scatter_kernel_b, dim3((unsigned)((N + 255) / 256)),
+                 dim3(256), 0, xa);
+    if (e != cudaSuccess) return e;
     PermuteArgs a;
     a.N = N; a.Nq = c.Nq; a.ncell = nc;
     a.cell_start = c.cell_start; a.ccell_start = c.ccell_start; a.tmp = c.tmp;
@@ -333,9 +364,12 @@ cudaError_t launch_bin_sort(Ctx &c) {
     a.cs4 = c.vl_on ? c.cs4 : c.cq4;  // list gathers, or the Coulomb pass
     a.gate = gate;
     const int64_t threads = (nc + kCellsPerWarp - 1) / kCellsPerWarp * 32;
-    bin_rank_permute_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, c.stream>>>(a);
-    if (gate)
-      bin_identity_kernel<<<(unsigned)((N + c.Nq + 255) / 256), 256, 0, c.stream>>>(a);
+    e = dispatch(c, bin_rank_permute_kernel, bin_rank_permute_kernel_b, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, a);
+    if (e != cudaSuccess) return e;
+    if (gate) {
+      e = dispatch(c, bin_identity_kernel, bin_identity_kernel_b, dim3((unsigned)((N + c.Nq + 255) / 256)), dim3(256), 0, a);
+      if (e != cudaSuccess) return e;
+    }
   }
   c.cur = b1;
   return cudaGetLastError();

@@ -49,11 +49,7 @@ struct CoulArgs {
 int64_t coul_blocks(int64_t nq) { return (nq + kCoulWarps - 1) / kCoulWarps; }
 
 template <typename real>
-// (16 blocks of 4 warps in the FP32 forms: the whole SM's 64 warps; the pass is bound by the
-// latency of each warp's dependent loads, so occupancy is what hides it; 8 in the FP64 form,
-// whose registers would spill)
-__global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
-    coul_kernel(const CoulArgs a) {
+__device__ __forceinline__ void coul_body(const CoulArgs a, int bx, int) {
   constexpr bool F64 = sizeof(real) == 8;
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ int4 buf[kCoulWarps][kCoulBuf];  // hits: integer displacement, charge bits or index
@@ -62,7 +58,7 @@ __global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
   __shared__ double wred[kCoulWarps][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const PairConst &pc = a.pc;
-  const int64_t i = (int64_t)blockIdx.x * kCoulWarps + wid;
+  const int64_t i = (int64_t)bx * kCoulWarps + wid;
   real fx = (real)0, fy = (real)0, fz = (real)0;
   real uc = (real)0, wc = (real)0, cuc = (real)0, cwc = (real)0;
   if (i < a.nq) {
@@ -87,7 +83,7 @@ __global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
         const float ey = fmaxf(0.f, fmaxf((float)(cy + dy) - fyc, fyc - (float)(cy + dy + 1)) - 1e-3f);
         const float ez = fmaxf(0.f, fmaxf((float)(cz + dz) - fzc, fzc - (float)(cz + dz + 1)) - 1e-3f);
         const float dyl = ey * wy, dzl = ez * wz;
-        const float rx2 = a.reach2 - dyl * dyl - dzl * dzl;
+        const float rx2 = mad(-dzl, dzl, mad(-dyl, dyl, a.reach2));
         if (rx2 > 0.f) {
           const int ryw = ((cy + dy) % n1 + n1) % n1, rzw = ((cz + dz) % n2 + n2) % n2;
           const int64_t rowbase = (int64_t)n0 * (ryw + (int64_t)n1 * rzw);
@@ -144,7 +140,7 @@ __global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
           dx = (real)((float)e.x * pc.h[0]);
           dy = (real)((float)e.y * pc.h[1]);
           dz = (real)((float)e.z * pc.h[2]);
-          r2 = dx * dx + dy * dy + dz * dz;
+          r2 = mad(dx, dx, mad(dy, dy, dz * dz));
           qj = (real)__int_as_float(e.w);
         }
         real r, rinv, erfcv, expv;
@@ -163,14 +159,14 @@ __global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
         const real tsp = F64 ? (real)pc.two_sqrt_alpha_over_sqrt_pi_d
                              : (real)pc.two_sqrt_alpha_over_sqrt_pi;
         const real rinv2 = rinv * rinv;
-        const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
-        fx += gc * dx; fy += gc * dy; fz += gc * dz;
+        const real gc = Cqq * mad(erfcv * rinv, rinv2, tsp * expv * rinv2);
+        fx = mad(gc, dx, fx); fy = mad(gc, dy, fy); fz = mad(gc, dz, fz);
         if (a.comp) {
           kahan_add(uc, cuc, Cqq * erfcv * rinv);
           kahan_add(wc, cwc, gc * r2);
         } else {
-          uc += Cqq * erfcv * rinv;
-          wc += gc * r2;
+          uc = mad(Cqq * erfcv, rinv, uc);
+          wc = mad(gc, r2, wc);
         }
       }
     };
@@ -192,7 +188,7 @@ __global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
           } else {
             const float ex = (float)dsx * pc.h[0], ey = (float)dsy * pc.h[1],
                         ez = (float)dsz * pc.h[2];
-            const float r2 = ex * ex + ey * ey + ez * ez;
+            const float r2 = mad(ex, ex, mad(ey, ey, ez * ez));
             hit = r2 < pc.rc2_lo;
             if (r2 >= pc.rc2_lo && r2 <= pc.rc2_hi) hit = exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d;
           }
@@ -230,9 +226,19 @@ __global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
     double s = 0.0;
     if (threadIdx.x == Q_UREAL || threadIdx.x == Q_WREAL)
       for (int k = 0; k < kCoulWarps; ++k) s += wred[k][threadIdx.x == Q_UREAL ? 0 : 1];
-    a.epart[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = 0.5 * s;
+    a.epart[(int64_t)bx * NQ_PAIR + threadIdx.x] = 0.5 * s;
   }
 }
+
+// (16 blocks of 4 warps in the FP32 forms: the whole SM's 64 warps; the pass is bound by the
+// latency of each warp's dependent loads, so occupancy is what hides it; 8 in the FP64 form,
+// whose registers would spill)
+template <typename real>
+__global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
+    coul_kernel(const CoulArgs a) {
+  coul_body<real>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
 
 cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4) {
   CoulArgs a;
@@ -248,11 +254,11 @@ cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4) {
   a.comp = c.precision == RBE_FP32_COMP;
   const double rr = c.rc * (1.0 + 1e-5) + 8.0 * std::ldexp(1.0, -24) * std::max(c.box[0], std::max(c.box[1], c.box[2]));
   a.reach2 = (float)(rr * rr);
-  const unsigned blocks = (unsigned)c.n_coul_blk;  // every slot of the pass's partial range
-  if (blocks == 0) return cudaSuccess;
-  if (c.precision == RBE_FP64) coul_kernel<double><<<blocks, kCoulWarps * 32, 0, c.stream>>>(a);
-  else coul_kernel<float><<<blocks, kCoulWarps * 32, 0, c.stream>>>(a);
-  return cudaGetLastError();
+  const dim3 g((unsigned)c.n_coul_blk), b(kCoulWarps * 32);  // every slot of the partial range
+  // (per replica in a batch, like the other pair kernels)
+  if (c.precision == RBE_FP64)
+    return dispatch(c, coul_kernel<double>, nullptr, g, b, 0, a, true);
+  return dispatch(c, coul_kernel<float>, nullptr, g, b, 0, a, true);
 }
 
 }  // namespace rbe

@@ -72,12 +72,34 @@ struct ClusterArgs {
 // ---------------------------------------------------------------------------------------
 // Per-step cluster tables
 
+struct RowsArgs {
+  const int32_t *cell_start;
+  int n0, nrows, nc_sc;
+  int32_t *cl_base, *sc_base;
+};
+struct BoundsArgs {
+  const uint32_t *sx, *sy, *sz;
+  const int32_t *cell_start;
+  int n0, nrows;
+  const int32_t *cl_base;
+  int64_t cap;
+  uint4 *lo, *hi;
+};
+struct FinishArgs {
+  long long *facc;
+  void *F;                 // float or double forces, by the kernel's type
+  int64_t n3;
+  float sh, sl;
+  double inv_scale;
+};
+
 // One block: clusters and super-clusters of every row, as exclusive prefix sums.
-__global__ void __launch_bounds__(1024) cluster_rows_kernel(const int32_t *__restrict__ cell_start,
-                                                            int n0, int nrows, int nc_sc,
-                                                            int32_t *__restrict__ cl_base,
-                                                            int32_t *__restrict__ sc_base) {
+__device__ __forceinline__ void cluster_rows_body(const RowsArgs &a, int, int) {
   __shared__ int2 ws[32];
+  const int32_t *__restrict__ cell_start = a.cell_start;
+  const int n0 = a.n0, nrows = a.nrows, nc_sc = a.nc_sc;
+  int32_t *__restrict__ cl_base = a.cl_base;
+  int32_t *__restrict__ sc_base = a.sc_base;
   const unsigned FULL = 0xffffffffu;
   const int t = threadIdx.x, ln = t & 31;
   const int per = (nrows + 1023) / 1024;
@@ -122,6 +144,7 @@ __global__ void __launch_bounds__(1024) cluster_rows_kernel(const int32_t *__res
     sc_base[nrows] = bs;
   }
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(1024), cluster_rows_kernel, RowsArgs, cluster_rows_body)
 
 // Largest r in [0, nrows) with base[r] <= g (base is non-decreasing; g < base[nrows]).
 __device__ __forceinline__ int row_of(const int32_t *__restrict__ base, int nrows, int g) {
@@ -135,12 +158,15 @@ __device__ __forceinline__ int row_of(const int32_t *__restrict__ base, int nrow
 }
 
 // Bounding box (integer fractional coordinates), first particle and count of every cluster.
-__global__ void __launch_bounds__(256) cluster_bounds_kernel(
-    const uint32_t *__restrict__ sx, const uint32_t *__restrict__ sy,
-    const uint32_t *__restrict__ sz, const int32_t *__restrict__ cell_start, int n0, int nrows,
-    const int32_t *__restrict__ cl_base, int64_t cap, uint4 *__restrict__ lo,
-    uint4 *__restrict__ hi) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cluster_bounds_body(const BoundsArgs &a, int bx, int) {
+  const uint32_t *__restrict__ sx = a.sx;
+  const uint32_t *__restrict__ sy = a.sy;
+  const uint32_t *__restrict__ sz = a.sz;
+  const int32_t *__restrict__ cell_start = a.cell_start;
+  const int32_t *__restrict__ cl_base = a.cl_base;
+  const int n0 = a.n0, nrows = a.nrows;
+  const int64_t cap = a.cap;
+  const int64_t g = (int64_t)bx * blockDim.x + threadIdx.x;
   if (g >= cap || g >= cl_base[nrows]) return;
   const int r = row_of(cl_base, nrows, (int)g);
   const int ps = cell_start[(int64_t)r * n0], pe = cell_start[(int64_t)(r + 1) * n0];
@@ -153,26 +179,63 @@ __global__ void __launch_bounds__(256) cluster_bounds_kernel(
     y0 = min(y0, y); y1 = max(y1, y);
     z0 = min(z0, z); z1 = max(z1, z);
   }
-  lo[g] = make_uint4(x0, y0, z0, (uint32_t)b);
-  hi[g] = make_uint4(x1, y1, z1, (uint32_t)n);
+  a.lo[g] = make_uint4(x0, y0, z0, (uint32_t)b);
+  a.hi[g] = make_uint4(x1, y1, z1, (uint32_t)n);
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(256), cluster_bounds_kernel, BoundsArgs, cluster_bounds_body)
 
 // F = fixed-point sums / scale (overwriting), and the sums cleared for the next pass. The
 // 64-bit sum converts as its two 32-bit halves (a 64-bit integer conversion is slow here):
 // v = hi 2^32 + lo with hi signed and lo unsigned; FP32 forms take the FP32 factors
 // sh = 2^32 / scale and sl = 1 / scale (no FP64 work per element), the FP64 form the FP64 ones.
+// Four sums a thread in 16-byte accesses (one 8-byte sum a thread left most of the pass
+// waiting on memory latency).
 template <typename real>
-__global__ void __launch_bounds__(256) cpair_finalize_kernel(long long *__restrict__ facc,
-                                                             real *__restrict__ F, int64_t n3,
-                                                             float sh, float sl, double inv_scale) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n3) return;
-  const long long v = facc[k];
-  facc[k] = 0;
+__device__ __forceinline__ real fx_value(long long v, const FinishArgs &a) {
   const int hi = (int)(v >> 32);
   const unsigned lo = (unsigned)(v & 0xffffffffll);
-  if (sizeof(real) == 8) F[k] = (real)(((double)hi * 4294967296.0 + (double)lo) * inv_scale);
-  else F[k] = (real)fmaf((float)hi, sh, (float)lo * sl);
+  if (sizeof(real) == 8) return (real)(((double)hi * 4294967296.0 + (double)lo) * a.inv_scale);
+  return (real)fmaf((float)hi, a.sh, (float)lo * a.sl);
+}
+
+template <typename real>
+__device__ __forceinline__ void cpair_finalize_body(const FinishArgs &a, int bx, int) {
+  const int64_t k0 = 4 * ((int64_t)bx * blockDim.x + threadIdx.x);
+  const int64_t n3 = a.n3;
+  if (k0 >= n3) return;
+  long long *__restrict__ facc = a.facc;
+  real *__restrict__ F = static_cast<real *>(a.F);
+  if (k0 + 4 <= n3) {  // facc and F start 256-byte aligned, k0 is a multiple of 4
+    const longlong2 u = *reinterpret_cast<const longlong2 *>(facc + k0);
+    const longlong2 w = *reinterpret_cast<const longlong2 *>(facc + k0 + 2);
+    *reinterpret_cast<longlong2 *>(facc + k0) = make_longlong2(0, 0);
+    *reinterpret_cast<longlong2 *>(facc + k0 + 2) = make_longlong2(0, 0);
+    const real f0 = fx_value<real>(u.x, a), f1 = fx_value<real>(u.y, a);
+    const real f2 = fx_value<real>(w.x, a), f3 = fx_value<real>(w.y, a);
+    if (sizeof(real) == 4) {
+      *reinterpret_cast<float4 *>(F + k0) = make_float4((float)f0, (float)f1, (float)f2, (float)f3);
+    } else {
+      *reinterpret_cast<double2 *>(F + k0) = make_double2((double)f0, (double)f1);
+      *reinterpret_cast<double2 *>(F + k0 + 2) = make_double2((double)f2, (double)f3);
+    }
+  } else {
+    for (int64_t k = k0; k < n3; ++k) {
+      const long long v = facc[k];
+      facc[k] = 0;
+      F[k] = fx_value<real>(v, a);
+    }
+  }
+}
+template <typename real>
+__global__ void __launch_bounds__(256) cpair_finalize_kernel(const FinishArgs a) {
+  cpair_finalize_body<real>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+template <typename real>
+__global__ void __launch_bounds__(256)
+    cpair_finalize_kernel_b(const FinishArgs *__restrict__ t, const int32_t *__restrict__ pre,
+                            int nrep) {
+  const BatchIdx q = batch_locate(pre, nrep);
+  cpair_finalize_body<real>(t[q.r], q.bx, q.nbx);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -218,15 +281,15 @@ __device__ __forceinline__ real cp_terms(const ClusterArgs &a, bool in, real r2,
     real A, B, A12, B6;
     if (sizeof(real) == 8) { A = (real)tab->Ad[pt]; B = (real)tab->Bd[pt]; A12 = (real)tab->A12d[pt]; B6 = (real)tab->B6d[pt]; }
     else { A = (real)tab->A[pt]; B = (real)tab->B[pt]; A12 = (real)tab->A12[pt]; B6 = (real)tab->B6[pt]; }
-    const real w = ir6 * (A12 * ir6 - B6);
+    const real w = ir6 * mad(A12, ir6, -B6);
     g = w * ir2;
-    acc.u0 += ir6 * (A * ir6 - B);
+    acc.u0 = mad(ir6, mad(A, ir6, -B), acc.u0);
     acc.u1 += w;
   } else {
     const real A12 = sizeof(real) == 8 ? (real)a.ljA12d : (real)a.ljA12;
     const real B6 = sizeof(real) == 8 ? (real)a.ljB6d : (real)a.ljB6;
-    g = ir6 * ir2 * (A12 * ir6 - B6);
-    acc.u0 += ir6 * ir6;
+    g = ir6 * ir2 * mad(A12, ir6, -B6);
+    acc.u0 = mad(ir6, ir6, acc.u0);
     acc.u1 += ir6;
   }
   if (COUL) {
@@ -249,14 +312,14 @@ __device__ __forceinline__ real cp_terms(const ClusterArgs &a, bool in, real r2,
       const real tsp = sizeof(real) == 8 ? (real)pc.two_sqrt_alpha_over_sqrt_pi_d
                                          : (real)pc.two_sqrt_alpha_over_sqrt_pi;
       const real rinv2 = rinv * rinv;
-      const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
+      const real gc = Cqq * mad(erfcv * rinv, rinv2, tsp * expv * rinv2);
       g += gc;
       if (a.comp) {
         kahan_add(acc.uc, acc.cuc, Cqq * erfcv * rinv);
         kahan_add(acc.wc, acc.cwc, gc * r2);
       } else {
-        acc.uc += Cqq * erfcv * rinv;
-        acc.wc += gc * r2;
+        acc.uc = mad(Cqq * erfcv, rinv, acc.uc);
+        acc.wc = mad(gc, r2, acc.wc);
       }
     }
   }
@@ -267,13 +330,7 @@ __device__ __forceinline__ real cp_terms(const ClusterArgs &a, bool in, real r2,
 // The kernel: one warp per super-cluster.
 
 template <typename real, bool COUL, bool MULTI, bool COUNT>
-// (occupancy: 24 warps per SM for the FP32 LJ pass, fewer for the register-heavy Coulomb and
-// FP64 instances)
-#ifndef RBE_CP_MINB
-#define RBE_CP_MINB 24
-#endif
-__global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (COUL ? 12 : RBE_CP_MINB)))
-    cpair_kernel(const ClusterArgs a) {
+__device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
   constexpr bool F64 = sizeof(real) == 8;
   constexpr int NC = F64 ? 4 : 8;          // clusters per super-cluster
   constexpr int NP = NC * kClSize;         // particles per super-cluster
@@ -286,7 +343,7 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
   __shared__ float4 sif[F64 ? 1 : NP];
   __shared__ int32_t seg_beg[kCpMaxSeg], seg_pre[kCpMaxSeg + 1];
   const int lane = threadIdx.x, a8 = lane & 7, hh = lane >> 3;
-  const int w = blockIdx.x;
+  const int w = bx;
   const PairConst &pc = a.pc;
   const int64_t N = a.N;
   CpAcc<real> acc;
@@ -574,7 +631,7 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
               ir2 = in ? (real)rcp_approx((float)r2) : (real)0;
             }
             const real g = cp_terms<real, COUL, MULTI>(a, in, r2, ir2, qi_, qj[k], ti_, tj[k], acc);
-            fxj[k] -= g * dx; fyj[k] -= g * dy; fzj[k] -= g * dz;
+            fxj[k] = mad(-g, dx, fxj[k]); fyj[k] = mad(-g, dy, fyj[k]); fzj[k] = mad(-g, dz, fzj[k]);
             if (COUNT) cntj[k] += in ? 1 : 0;
             return g;
           };
@@ -603,7 +660,7 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
               bool in;
               const real g = pair_one(vd && a8 < hh + 4 * k, xd, yd, zd, ox, oy, oz, qd, td, k,
                                       dx, dy, dz, in);
-              fdx += g * dx; fdy += g * dy; fdz += g * dz;
+              fdx = mad(g, dx, fdx); fdy = mad(g, dy, fdy); fdz = mad(g, dz, fdz);
               if (COUNT) cd += in ? 1 : 0;
             }
             fdx += __shfl_xor_sync(FULL, fdx, 8); fdx += __shfl_xor_sync(FULL, fdx, 16);
@@ -632,7 +689,7 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
                 const real g = pair_one(!F64 || vi[c], (real)pi4.x, (real)pi4.y, (real)pi4.z,
                                         oxi[c], oyi[c], ozi[c], COUL && !F64 ? (real)pi4.w : qi[c],
                                         ti[c], k, dx, dy, dz, in);
-                fxi[c] += g * dx; fyi[c] += g * dy; fzi[c] += g * dz;
+                fxi[c] = mad(g, dx, fxi[c]); fyi[c] = mad(g, dy, fyi[c]); fzi[c] = mad(g, dz, fzi[c]);
                 if (COUNT) cnti[c] += in ? 1 : 0;
               }
             }
@@ -754,9 +811,22 @@ __global__ void __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (CO
 #pragma unroll
   for (int k = 0; k < NQ_PAIR; ++k) {
     const double s = warp_sum(v[k]);
-    if (lane == 0) a.epart[(int64_t)blockIdx.x * NQ_PAIR + k] = s;
+    if (lane == 0) a.epart[(int64_t)bx * NQ_PAIR + k] = s;
   }
 }
+
+// (occupancy: 24 warps per SM for the FP32 LJ pass, fewer for the register-heavy Coulomb and
+// FP64 instances)
+#ifndef RBE_CP_MINB
+#define RBE_CP_MINB 24
+#endif
+#define RBE_CP_BOUNDS                                                                          \
+  __launch_bounds__(32, (sizeof(real) == 8 ? (COUL ? 8 : 12) : (COUL ? 12 : RBE_CP_MINB)))
+template <typename real, bool COUL, bool MULTI, bool COUNT>
+__global__ void RBE_CP_BOUNDS cpair_kernel(const ClusterArgs a) {
+  cpair_body<real, COUL, MULTI, COUNT>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+#undef RBE_CP_BOUNDS
 
 // ---------------------------------------------------------------------------------------
 // Host side
@@ -790,13 +860,14 @@ bool cpair_usable(const Ctx &c) {
 cudaError_t launch_cluster_tables(Ctx &c) {
   const int b = c.cur;
   const int nrows = c.grid.n[1] * c.grid.n[2];
-  cluster_rows_kernel<<<1, 1024, 0, c.stream>>>(c.cell_start, c.grid.n[0], nrows, cpair_nc(c),
-                                                c.cl_base, c.sc_base);
+  const RowsArgs ra{c.cell_start, c.grid.n[0], nrows, cpair_nc(c), c.cl_base, c.sc_base};
+  cudaError_t e = dispatch(c, cluster_rows_kernel, cluster_rows_kernel_b, dim3(1), dim3(1024), 0,
+                           ra);
+  if (e != cudaSuccess) return e;
   const int64_t ccap = cpair_clusters_bound(c);
-  cluster_bounds_kernel<<<(unsigned)((ccap + 255) / 256), 256, 0, c.stream>>>(
-      c.s[b], c.s[b] + c.N, c.s[b] + 2 * c.N, c.cell_start, c.grid.n[0], nrows, c.cl_base, ccap,
-      c.cl_lo, c.cl_hi);
-  return cudaGetLastError();
+  const BoundsArgs ba{c.s[b], c.s[b] + c.N, c.s[b] + 2 * c.N, c.cell_start, c.grid.n[0], nrows,
+                      c.cl_base, ccap, c.cl_lo, c.cl_hi};
+  return dispatch(c, cluster_bounds_kernel, cluster_bounds_kernel_b, dim3((unsigned)((ccap + 255) / 256)), dim3(256), 0, ba);
 }
 
 // The pair pass itself (the tables of launch_cluster_tables must be current), then the
@@ -847,16 +918,18 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
     a.bb2 = (float)(rr * rr);
   }
   a.err = c.err;
-  if (want_counts) cudaMemsetAsync(c.nbr, 0, sizeof(int32_t) * c.N, c.stream);
+  if (want_counts) {
+    const cudaError_t e = fill_zero(c, c.nbr, c.N);
+    if (e != cudaSuccess) return e;
+  }
   // every slot of the pass's partial range (blocks past the last super-cluster write zeros)
-  const int64_t blocks = c.n_pair_blk;
-  const dim3 g((unsigned)blocks), bl(32);
+  const dim3 g((unsigned)c.n_pair_blk), bl(32);
   const bool fp64 = c.precision == RBE_FP64;
+  cudaError_t e;
+  // (per replica in a batch)
 #define RBE_CP_LAUNCH(R, CO, MU)                                                             \
-  do {                                                                                       \
-    if (want_counts) cpair_kernel<R, CO, MU, true><<<g, bl, 0, c.stream>>>(a);               \
-    else cpair_kernel<R, CO, MU, false><<<g, bl, 0, c.stream>>>(a);                          \
-  } while (0)
+  e = want_counts ? dispatch(c, cpair_kernel<R, CO, MU, true>, nullptr, g, bl, 0, a, true)   \
+                  : dispatch(c, cpair_kernel<R, CO, MU, false>, nullptr, g, bl, 0, a, true)
   if (fp64) {
     if (coul) { if (multi) RBE_CP_LAUNCH(double, true, true); else RBE_CP_LAUNCH(double, true, false); }
     else { if (multi) RBE_CP_LAUNCH(double, false, true); else RBE_CP_LAUNCH(double, false, false); }
@@ -865,15 +938,16 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
     else { if (multi) RBE_CP_LAUNCH(float, false, true); else RBE_CP_LAUNCH(float, false, false); }
   }
 #undef RBE_CP_LAUNCH
+  if (e != cudaSuccess) return e;
   const int64_t n3 = 3 * c.N;
-  const unsigned fb = (unsigned)((n3 + 255) / 256);
-  if (fp64)
-    cpair_finalize_kernel<double><<<fb, 256, 0, c.stream>>>(c.facc, c.Fd, n3, 0.f, 0.f,
-                                                            1.0 / kFixScale64);
-  else
-    cpair_finalize_kernel<float><<<fb, 256, 0, c.stream>>>(
-        c.facc, c.F, n3, (float)(4294967296.0 / kFixScale32), (float)(1.0 / kFixScale32), 0.0);
-  return cudaGetLastError();
+  const dim3 fg((unsigned)(((n3 + 3) / 4 + 255) / 256)), fb(256);
+  if (fp64) {
+    const FinishArgs f{c.facc, c.Fd, n3, 0.f, 0.f, 1.0 / kFixScale64};
+    return dispatch(c, cpair_finalize_kernel<double>, cpair_finalize_kernel_b<double>, fg, fb, 0, f);
+  }
+  const FinishArgs f{c.facc, c.F, n3, (float)(4294967296.0 / kFixScale32),
+                     (float)(1.0 / kFixScale32), 0.0};
+  return dispatch(c, cpair_finalize_kernel<float>, cpair_finalize_kernel_b<float>, fg, fb, 0, f);
 }
 
 }  // namespace rbe

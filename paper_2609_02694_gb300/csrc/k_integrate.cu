@@ -17,13 +17,44 @@ int64_t rbl_compact_count(int64_t nblk);
 // of L / 2^32 where the FP64 rounding would differ); FP64 runs at 1/64 of the FP32 rate on
 // this GPU, and this pass would otherwise be bound by it instead of by memory.
 template <typename V, typename FT>
-__global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
-                                  const float *__restrict__ invm, uint32_t *__restrict__ s,
-                                  int64_t N, double hdk, double gx, double gy, double gz,
-                                  int *__restrict__ err, const double *__restrict__ scale) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+struct KickDriftArgs {
+  V *v;
+  const FT *F;
+  const float *invm;
+  uint32_t *s;
+  int64_t N;
+  double hdk, gx, gy, gz;
+  int *err;
+  const double *scale;
+  uint64_t *step;  // the step counter, advanced by the first thread (the sampler reads it next)
+};
+
+// Solo and batched kernels of a body templated on the velocity and force types.
+#define RBE_VF_KERNELS(LB, NAME, ARGS, BODY)                                                   \
+  template <typename V, typename FT>                                                         \
+  __global__ void LB NAME(const ARGS<V, FT> a) {                                              \
+    BODY<V, FT>(a, (int)blockIdx.x, (int)gridDim.x);                                          \
+  }                                                                                          \
+  template <typename V, typename FT>                                                         \
+  __global__ void LB NAME##_b(const ARGS<V, FT> *__restrict__ t,                              \
+                              const int32_t *__restrict__ pre, int nrep) {                    \
+    const BatchIdx q = batch_locate(pre, nrep);                                               \
+    BODY<V, FT>(t[q.r], q.bx, q.nbx);                                                         \
+  }
+
+template <typename V, typename FT>
+__device__ __forceinline__ void kick_drift_body(const KickDriftArgs<V, FT> &a, int bx, int) {
+  const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
+  const int64_t N = a.N;
+  if (i == 0) *a.step += 1;
   if (i >= N) return;
-  const double g[3] = {gx, gy, gz};
+  V *__restrict__ v = a.v;
+  const FT *__restrict__ F = a.F;
+  uint32_t *__restrict__ s = a.s;
+  const double *scale = a.scale;
+  const double hdk = a.hdk;
+  const double g[3] = {a.gx, a.gy, a.gz};
+  const float *__restrict__ invm = a.invm;
   const V im = (V)invm[i];
   const V sc = scale ? (V)*scale : (V)1;  // Nose-Hoover start-of-step scaling
   bool bad = false;
@@ -43,16 +74,31 @@ __global__ void kick_drift_kernel(V *__restrict__ v, const FT *__restrict__ F,
     }
     s[d * N + i] += (uint32_t)st;
   }
-  if (bad) atomicOr(err, ERRBIT_NONFINITE);
+  if (bad) atomicOr(a.err, ERRBIT_NONFINITE);
 }
+RBE_VF_KERNELS(__launch_bounds__(256), kick_drift_kernel, KickDriftArgs, kick_drift_body)
 
 template <typename V, typename FT>
-__global__ void __launch_bounds__(256)
-    kick_kernel(V *__restrict__ v, const FT *__restrict__ F, const float *__restrict__ invm,
-                int64_t N, double hdk, double inv_kappa, int do_kick,
-                double *__restrict__ ke_part) {
+struct KickArgs {
+  V *v;
+  const FT *F;
+  const float *invm;
+  int64_t N;
+  double hdk, inv_kappa;
+  int do_kick;
+  double *ke_part;
+};
+
+template <typename V, typename FT>
+__device__ __forceinline__ void kick_body(const KickArgs<V, FT> &a, int bx, int) {
   __shared__ double sh[256];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  V *__restrict__ v = a.v;
+  const FT *__restrict__ F = a.F;
+  const float *__restrict__ invm = a.invm;
+  const int64_t N = a.N;
+  const double hdk = a.hdk, inv_kappa = a.inv_kappa;
+  const int do_kick = a.do_kick;
+  const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
   double ke = 0.0;
   if (i < N) {
     const V im = (V)invm[i];
@@ -77,16 +123,28 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) ke_part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) a.ke_part[bx] = sh[0];
 }
+RBE_VF_KERNELS(__launch_bounds__(256), kick_kernel, KickArgs, kick_body)
 
 // Nose-Hoover half steps (chain of one): from 2K = 2 sum(kinetic partials) the end-of-step
 // half (mode 0) gives the velocity scale s_end and the start-of-next-step half gives
 // s_start, applied by the next kick-drift; mode 1 only does the start half (first step).
-__global__ void __launch_bounds__(256)
-    thermostat_kernel(const double *__restrict__ ke_part, int64_t n, double Nf, double kT,
-                      double Q, double dt, double *__restrict__ th, int mode) {
+struct ThermoArgs {
+  const double *ke_part;
+  int64_t n;
+  double Nf, kT, Q, dt;
+  double *th;
+  int mode;
+};
+
+__device__ __forceinline__ void thermostat_body(const ThermoArgs &a, int, int) {
   __shared__ double sh[256];
+  const double *__restrict__ ke_part = a.ke_part;
+  const int64_t n = a.n;
+  const double Nf = a.Nf, kT = a.kT, Q = a.Q, dt = a.dt;
+  double *__restrict__ th = a.th;
+  const int mode = a.mode;
   double acc = 0.0;
   for (int64_t b = threadIdx.x; b < n; b += blockDim.x) acc += ke_part[b];
   sh[threadIdx.x] = acc;
@@ -118,13 +176,21 @@ __global__ void __launch_bounds__(256)
   th[1] = eta;
   th[2] = s_start;
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(256), thermostat_kernel, ThermoArgs, thermostat_body)
 
-template <typename V>
-__global__ void scale_v_kernel(V *__restrict__ v, int64_t N, const double *__restrict__ scale) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= 3 * N) return;
-  v[k] *= (V)*scale;
+template <typename V, typename FT>
+struct ScaleArgs {
+  V *v;
+  int64_t N;
+  const double *scale;
+};
+template <typename V, typename FT>
+__device__ __forceinline__ void scale_v_body(const ScaleArgs<V, FT> &a, int bx, int) {
+  const int64_t k = (int64_t)bx * blockDim.x + threadIdx.x;
+  if (k >= 3 * a.N) return;
+  a.v[k] *= (V)*a.scale;
 }
+RBE_VF_KERNELS(__launch_bounds__(256), scale_v_kernel, ScaleArgs, scale_v_body)
 
 struct TotalsArgs {
   const double *ke_override;
@@ -141,7 +207,7 @@ struct TotalsArgs {
 constexpr int kTotalsThreads = 1024;
 
 template <typename ACC>
-__global__ void __launch_bounds__(kTotalsThreads) totals_kernel(TotalsArgs a) {
+__device__ __forceinline__ void totals_body(const TotalsArgs &a, int, int) {
   constexpr int NV = 7;  // ureal ulj wreal wlj uk wk ke
   constexpr int NW = kTotalsThreads / 32;
   __shared__ ACC sh[NV][NW];
@@ -187,6 +253,16 @@ __global__ void __launch_bounds__(kTotalsThreads) totals_kernel(TotalsArgs a) {
     a.scal[S_WK] = wk;
     a.scal[S_WTOT] = wr + wl + wk;
   }
+}
+template <typename ACC>
+__global__ void __launch_bounds__(kTotalsThreads) totals_kernel(const TotalsArgs a) {
+  totals_body<ACC>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+template <typename ACC>
+__global__ void __launch_bounds__(kTotalsThreads)
+    totals_kernel_b(const TotalsArgs *__restrict__ t, const int32_t *__restrict__ pre, int nrep) {
+  const BatchIdx q = batch_locate(pre, nrep);
+  totals_body<ACC>(t[q.r], q.bx, q.nbx);
 }
 
 template <typename FT, typename OT>
@@ -263,46 +339,56 @@ __global__ void scatter_int_kernel(const int32_t *__restrict__ src, const int32_
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// First half-kick and drift, with the step counter's advance (alone when there are no
+// particles).
 cudaError_t launch_kick_drift(Ctx &c) {
   const int b = c.cur;
   const double hdk = 0.5 * c.dt * c.kappa;
-  if (c.N == 0) return cudaSuccess;
+  if (c.N == 0) return launch_step_advance(c);
   const double *scale = c.nvt ? c.thermo + 2 : nullptr;
   const double gx = c.dt * kTwo32 / c.box[0], gy = c.dt * kTwo32 / c.box[1],
                gz = c.dt * kTwo32 / c.box[2];
-  if (c.precision == RBE_FP64)
-    kick_drift_kernel<double, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vd[b], c.Fd, c.invm[b], c.s[b], c.N, hdk, gx, gy, gz, c.err, scale);
-  else
-    kick_drift_kernel<float, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vf[b], c.F, c.invm[b], c.s[b], c.N, hdk, gx, gy, gz, c.err, scale);
-  return cudaGetLastError();
+  const dim3 g(nblk(c.N, 256)), t(256);
+  if (c.precision == RBE_FP64) {
+    const KickDriftArgs<double, double> a{c.vd[b], c.Fd, c.invm[b], c.s[b], c.N, hdk, gx, gy, gz,
+                                          c.err, scale, c.step_dev};
+    return dispatch(c, kick_drift_kernel<double, double>, kick_drift_kernel_b<double, double>, g,
+                    t, 0, a);
+  }
+  const KickDriftArgs<float, float> a{c.vf[b], c.F, c.invm[b], c.s[b], c.N, hdk, gx, gy, gz,
+                                      c.err, scale, c.step_dev};
+  return dispatch(c, kick_drift_kernel<float, float>, kick_drift_kernel_b<float, float>, g, t, 0,
+                  a);
 }
 
 cudaError_t launch_thermostat(Ctx &c, int mode) {
   const int b = c.cur;
-  thermostat_kernel<<<1, 256, 0, c.stream>>>(c.epart + c.off_ke, c.n_ke_blk, c.Nf, c.kB * c.T0,
-                                             c.Qnh, c.dt, c.thermo, mode);
-  if (mode == 0) {
-    if (c.precision == RBE_FP64)
-      scale_v_kernel<double><<<nblk(3 * c.N, 256), 256, 0, c.stream>>>(c.vd[b], c.N, c.thermo + 4);
-    else
-      scale_v_kernel<float><<<nblk(3 * c.N, 256), 256, 0, c.stream>>>(c.vf[b], c.N, c.thermo + 4);
+  const ThermoArgs ta{c.epart + c.off_ke, c.n_ke_blk, c.Nf, c.kB * c.T0, c.Qnh, c.dt, c.thermo,
+                      mode};
+  cudaError_t e = dispatch(c, thermostat_kernel, thermostat_kernel_b, dim3(1), dim3(256), 0, ta);
+  if (e != cudaSuccess || mode != 0) return e;
+  const dim3 g(nblk(3 * c.N, 256)), t(256);
+  if (c.precision == RBE_FP64) {
+    const ScaleArgs<double, double> a{c.vd[b], c.N, c.thermo + 4};
+    return dispatch(c, scale_v_kernel<double, double>, scale_v_kernel_b<double, double>, g, t, 0, a);
   }
-  return cudaGetLastError();
+  const ScaleArgs<float, float> a{c.vf[b], c.N, c.thermo + 4};
+  return dispatch(c, scale_v_kernel<float, float>, scale_v_kernel_b<float, float>, g, t, 0, a);
 }
 
 static cudaError_t kick_impl(Ctx &c, int do_kick) {
   const int b = c.cur;
   const double hdk = 0.5 * c.dt * c.kappa;
   if (c.N == 0) return cudaSuccess;
-  if (c.precision == RBE_FP64)
-    kick_kernel<double, double><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vd[b], c.Fd, c.invm[b], c.N, hdk, 1.0 / c.kappa, do_kick, c.epart + c.off_ke);
-  else
-    kick_kernel<float, float><<<nblk(c.N, 256), 256, 0, c.stream>>>(
-        c.vf[b], c.F, c.invm[b], c.N, hdk, 1.0 / c.kappa, do_kick, c.epart + c.off_ke);
-  return cudaGetLastError();
+  const dim3 g(nblk(c.N, 256)), t(256);
+  if (c.precision == RBE_FP64) {
+    const KickArgs<double, double> a{c.vd[b], c.Fd, c.invm[b], c.N, hdk, 1.0 / c.kappa, do_kick,
+                                     c.epart + c.off_ke};
+    return dispatch(c, kick_kernel<double, double>, kick_kernel_b<double, double>, g, t, 0, a);
+  }
+  const KickArgs<float, float> a{c.vf[b], c.F, c.invm[b], c.N, hdk, 1.0 / c.kappa, do_kick,
+                                 c.epart + c.off_ke};
+  return dispatch(c, kick_kernel<float, float>, kick_kernel_b<float, float>, g, t, 0, a);
 }
 
 cudaError_t launch_kick(Ctx &c) { return kick_impl(c, 1); }
@@ -311,11 +397,17 @@ cudaError_t launch_kinetic(Ctx &c) { return kick_impl(c, 0); }
 // Block partials of a pair pass ([nblk][NQ_PAIR]) summed over fixed contiguous ranges in a
 // fixed order into [gridDim.x][NQ_PAIR]: the FP64 adds are spread over many SMs (one SM's
 // FP64 rate is low) before the one-block totals.
-__global__ void __launch_bounds__(256) partials_compact_kernel(const double *__restrict__ in,
-                                                               int64_t nblk, int64_t per,
-                                                               double *__restrict__ out) {
+struct CompactArgs {
+  const double *in;
+  int64_t nblk, per;
+  double *out;
+};
+
+__device__ __forceinline__ void partials_compact_body(const CompactArgs &a, int bx, int) {
   __shared__ double sh[NQ_PAIR][256];
-  const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(nblk, b0 + per);
+  const double *__restrict__ in = a.in;
+  const int64_t nblk = a.nblk, per = a.per;
+  const int64_t b0 = (int64_t)bx * per, b1 = min(nblk, b0 + per);
   double acc[NQ_PAIR];
 #pragma unroll
   for (int k = 0; k < NQ_PAIR; ++k) acc[k] = 0.0;
@@ -331,8 +423,10 @@ __global__ void __launch_bounds__(256) partials_compact_kernel(const double *__r
       for (int k = 0; k < NQ_PAIR; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x < NQ_PAIR) out[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < NQ_PAIR) a.out[(int64_t)bx * NQ_PAIR + threadIdx.x] = sh[threadIdx.x][0];
 }
+RBE_BATCHED_KERNEL(__launch_bounds__(256), partials_compact_kernel, CompactArgs,
+                   partials_compact_body)
 
 int64_t partials_compact_count(int64_t nblk) { return std::min<int64_t>(nblk, kCompactMax); }
 
@@ -340,13 +434,21 @@ cudaError_t launch_totals(Ctx &c) {
   TotalsArgs a;
   // pair and Coulomb-pass partials, compacted first (at most kCompactMax per pass)
   const int64_t ncp = partials_compact_count(c.n_pair_blk), ncc = partials_compact_count(c.n_coul_blk);
-  if (ncp > 0)
-    partials_compact_kernel<<<(unsigned)ncp, 256, 0, c.stream>>>(
-        c.epart + c.off_pair, c.n_pair_blk, (c.n_pair_blk + ncp - 1) / ncp, c.ecomp);
-  if (ncc > 0)
-    partials_compact_kernel<<<(unsigned)ncc, 256, 0, c.stream>>>(
-        c.epart + c.off_coul, c.n_coul_blk, (c.n_coul_blk + ncc - 1) / ncc,
-        c.ecomp + kCompactMax * NQ_PAIR);
+  cudaError_t e;
+  if (ncp > 0) {
+    const CompactArgs ca{c.epart + c.off_pair, c.n_pair_blk, (c.n_pair_blk + ncp - 1) / ncp,
+                         c.ecomp};
+    e = dispatch(c, partials_compact_kernel, partials_compact_kernel_b, dim3((unsigned)ncp),
+                 dim3(256), 0, ca);
+    if (e != cudaSuccess) return e;
+  }
+  if (ncc > 0) {
+    const CompactArgs ca{c.epart + c.off_coul, c.n_coul_blk, (c.n_coul_blk + ncc - 1) / ncc,
+                         c.ecomp + kCompactMax * NQ_PAIR};
+    e = dispatch(c, partials_compact_kernel, partials_compact_kernel_b, dim3((unsigned)ncc),
+                 dim3(256), 0, ca);
+    if (e != cudaSuccess) return e;
+  }
   a.pair = c.ecomp; a.n_pair = ncp;
   a.coul = c.ecomp + kCompactMax * NQ_PAIR; a.n_coul = ncc;
   // RBL partials: the compacted ones (rbl_compact_kernel runs after the RBL kernel)
@@ -357,9 +459,11 @@ cudaError_t launch_totals(Ctx &c) {
   a.U_self = c.U_self;
   a.scal = c.scal;
   a.ke_override = c.nvt ? c.thermo + 3 : nullptr;
-  if (c.precision == RBE_FP32) totals_kernel<float><<<1, kTotalsThreads, 0, c.stream>>>(a);
-  else totals_kernel<double><<<1, kTotalsThreads, 0, c.stream>>>(a);
-  return cudaGetLastError();
+  if (c.precision == RBE_FP32)
+    return dispatch(c, totals_kernel<float>, totals_kernel_b<float>, dim3(1), dim3(kTotalsThreads),
+                    0, a);
+  return dispatch(c, totals_kernel<double>, totals_kernel_b<double>, dim3(1),
+                  dim3(kTotalsThreads), 0, a);
 }
 
 cudaError_t launch_scatter_forces(Ctx &c, bool to_double) {
@@ -407,8 +511,7 @@ cudaError_t launch_gather_state(Ctx &c, const uint32_t *s_id, const double *v_id
 
 void zero_partials_tail(Ctx &c, int64_t off, int64_t written, int64_t capacity) {
   if (written >= capacity) return;
-  cudaMemsetAsync(c.epart + off + written * NQ_PAIR, 0,
-                  sizeof(double) * (size_t)(capacity - written) * NQ_PAIR, c.stream);
+  fill_zero(c, c.epart + off + written * NQ_PAIR, 2 * (capacity - written) * NQ_PAIR);
 }
 
 cudaError_t launch_scatter_int(Ctx &c, const int32_t *src_sorted, int32_t *dst_id, int width) {

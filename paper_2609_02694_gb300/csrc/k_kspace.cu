@@ -20,14 +20,63 @@
 
 namespace rbe {
 
+struct SfArgs {
+  const uint32_t *cs;
+  const float *cqf;
+  const double *cqd;
+  int64_t Nq;
+  const int4 *m;
+  int P, tile;
+  double *part;
+};
+struct CombineArgs {
+  const double *part;
+  int nblk, P;
+  const double4_16a *kcd;
+  double alpha;
+  double2 *rho;
+  float2 *abf;
+  double2 *abd;
+  double *emode;
+};
+struct GatherArgs {
+  const uint32_t *cs;
+  const float *cqf;
+  const double *cqd;
+  int64_t Nq;
+  const int4 *m;
+  const float4 *kcf;
+  const double4_16a *kcd;
+  const float2 *abf;
+  const double2 *abd;
+  int P;
+  const int32_t *cmap;
+  float *F;
+  double *Fd;
+  int64_t N;
+};
+
+// Solo and batched kernels of a body templated on MODE.
+#define RBE_MODE_KERNELS(LB, NAME, ARGS, BODY)                                                 \
+  template <int MODE>                                                                        \
+  __global__ void LB NAME(const ARGS a) { BODY<MODE>(a, (int)blockIdx.x, (int)gridDim.x); }   \
+  template <int MODE>                                                                        \
+  __global__ void LB NAME##_b(const ARGS *__restrict__ t, const int32_t *__restrict__ pre,   \
+                              int nrep) {                                                     \
+    const BatchIdx q = batch_locate(pre, nrep);                                               \
+    BODY<MODE>(t[q.r], q.bx, q.nbx);                                                          \
+  }
+
 // MODE: 0 = FP32 with Kahan-compensated per-thread sums, 1 = plain FP32, 2 = FP64.
 template <int MODE>
-__global__ void __launch_bounds__(256)
-    sf_kernel(const uint32_t *__restrict__ cs, const float *__restrict__ cqf,
-              const double *__restrict__ cqd, int64_t Nq, const int4 *__restrict__ m, int P,
-              int tile, double *__restrict__ part) {
+__device__ __forceinline__ void sf_body(const SfArgs &a, int bx, int) {
   extern __shared__ uint4 sh[];
-  const int64_t p0 = (int64_t)blockIdx.x * tile;
+  const uint32_t *__restrict__ cs = a.cs;
+  const float *__restrict__ cqf = a.cqf;
+  const double *__restrict__ cqd = a.cqd;
+  const int64_t Nq = a.Nq;
+  const int P = a.P, tile = a.tile;
+  const int64_t p0 = (int64_t)bx * tile;
   const int np = (int)min((int64_t)tile, Nq - p0);
   double *shq = reinterpret_cast<double *>(sh + tile);
   for (int k = threadIdx.x; k < np; k += blockDim.x) {
@@ -38,16 +87,16 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const int l = blockIdx.y * blockDim.x + threadIdx.x;
   if (l >= P) return;
-  const int4 mm = m[l];
-  double *out = part + ((int64_t)blockIdx.x * P + l) * 2;
+  const int4 mm = a.m[l];
+  double *out = a.part + ((int64_t)bx * P + l) * 2;
   if (MODE == 2) {
     double re = 0.0, im = 0.0;
     for (int k = 0; k < np; ++k) {
       const uint4 e = sh[k];
       double sn, co;
       sincos(phase_to_radians_d(phase_u32(mm, e.x, e.y, e.z)), &sn, &co);
-      re += shq[k] * co;
-      im += shq[k] * sn;
+      re = mad(shq[k], co, re);
+      im = mad(shq[k], sn, im);
     }
     out[0] = re;
     out[1] = im;
@@ -76,18 +125,17 @@ __global__ void __launch_bounds__(256)
     out[1] = (double)im - (double)cim;
   }
 }
+RBE_MODE_KERNELS(__launch_bounds__(256), sf_kernel, SfArgs, sf_body)
 
 // One block per mode: sum the block partials in a fixed order, then derive the per-mode
 // energy, virial and the gather coefficients (c Im rho, c Re rho).
 template <int MODE>
-__global__ void __launch_bounds__(128)
-    sf_combine_kernel(const double *__restrict__ part, int nblk, int P,
-                      const double4_16a *__restrict__ kcd, double alpha, double2 *__restrict__ rho,
-                      float2 *__restrict__ abf, double2 *__restrict__ abd,
-                      double *__restrict__ emode) {
+__device__ __forceinline__ void sf_combine_body(const CombineArgs &a, int bx, int) {
   __shared__ double sre[128], sim[128];
   __shared__ float fre[128], fim[128];
-  const int l = blockIdx.x;
+  const double *__restrict__ part = a.part;
+  const int nblk = a.nblk, P = a.P;
+  const int l = bx;
   if (MODE == 1) {
     float re = 0.f, im = 0.f;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
@@ -124,34 +172,37 @@ __global__ void __launch_bounds__(128)
   }
   if (threadIdx.x == 0) {
     const double re = sre[0], im = sim[0];
-    const double4_16a kc = kcd[l];
+    const double4_16a kc = a.kcd[l];
     const double k2 = kc.x * kc.x + kc.y * kc.y + kc.z * kc.z;
     const double E = 0.5 * kc.w * (re * re + im * im);
-    rho[l] = make_double2(re, im);
-    emode[2 * l] = E;
-    emode[2 * l + 1] = E * (1.0 - k2 / (2.0 * alpha));
-    abf[l] = make_float2((float)(kc.w * im), (float)(kc.w * re));
-    abd[l] = make_double2(kc.w * im, kc.w * re);
+    a.rho[l] = make_double2(re, im);
+    a.emode[2 * l] = E;
+    a.emode[2 * l + 1] = E * (1.0 - k2 / (2.0 * a.alpha));
+    a.abf[l] = make_float2((float)(kc.w * im), (float)(kc.w * re));
+    a.abd[l] = make_double2(kc.w * im, kc.w * re);
   }
 }
+RBE_MODE_KERNELS(__launch_bounds__(128), sf_combine_kernel, CombineArgs, sf_combine_body)
 
 constexpr int kGatherThreads = 256;
 constexpr int kGatherChunk = 256;
 
 template <int MODE>
-__global__ void __launch_bounds__(kGatherThreads)
-    gather_kernel(const uint32_t *__restrict__ cs, const float *__restrict__ cqf,
-                  const double *__restrict__ cqd, int64_t Nq, const int4 *__restrict__ m,
-                  const float4 *__restrict__ kcf, const double4_16a *__restrict__ kcd,
-                  const float2 *__restrict__ abf, const double2 *__restrict__ abd, int P,
-                  const int32_t *__restrict__ cmap, float *__restrict__ F,
-                  double *__restrict__ Fd, int64_t N) {
+__device__ __forceinline__ void gather_body(const GatherArgs &a, int bx, int) {
+  const uint32_t *__restrict__ cs = a.cs;
+  const int64_t Nq = a.Nq, N = a.N;
+  const int P = a.P;
+  const int4 *__restrict__ m = a.m;
+  const float4 *__restrict__ kcf = a.kcf;
+  const double4_16a *__restrict__ kcd = a.kcd;
+  const float2 *__restrict__ abf = a.abf;
+  const double2 *__restrict__ abd = a.abd;
   __shared__ int4 sm[kGatherChunk];
   __shared__ float4 skf[kGatherChunk];
   __shared__ float2 sabf[kGatherChunk];
   __shared__ double4_16a skd[MODE == 2 ? kGatherChunk : 1];
   __shared__ double2 sabd[MODE == 2 ? kGatherChunk : 1];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)bx * blockDim.x + threadIdx.x;
   const bool valid = i < Nq;
   const uint32_t sx = valid ? cs[i] : 0u, sy = valid ? cs[Nq + i] : 0u,
                  sz = valid ? cs[2 * Nq + i] : 0u;
@@ -175,16 +226,16 @@ __global__ void __launch_bounds__(kGatherThreads)
       for (int t = 0; t < nl; ++t) {
         double sn, co;
         sincos(phase_to_radians_d(phase_u32(sm[t], sx, sy, sz)), &sn, &co);
-        const double g = sabd[t].x * co - sabd[t].y * sn;
-        dx += g * skd[t].x;
-        dy += g * skd[t].y;
-        dz += g * skd[t].z;
+        const double g = mad(sabd[t].x, co, -(sabd[t].y * sn));
+        dx = mad(g, skd[t].x, dx);
+        dy = mad(g, skd[t].y, dy);
+        dz = mad(g, skd[t].z, dz);
       }
     } else {
       for (int t = 0; t < nl; ++t) {
         float sn, co;
         __sincosf(phase_to_radians(phase_u32(sm[t], sx, sy, sz)), &sn, &co);
-        const float g = sabf[t].x * co - sabf[t].y * sn;
+        const float g = mad(sabf[t].x, co, -(sabf[t].y * sn));
         fx = fmaf(g, skf[t].x, fx);
         fy = fmaf(g, skf[t].y, fy);
         fz = fmaf(g, skf[t].z, fz);
@@ -192,18 +243,31 @@ __global__ void __launch_bounds__(kGatherThreads)
     }
   }
   if (!valid) return;
-  const int64_t p = cmap[i];
+  const int64_t p = a.cmap[i];
   if (MODE == 2) {
-    const double q = cqd[i];
-    Fd[p] -= q * dx;
-    Fd[N + p] -= q * dy;
-    Fd[2 * N + p] -= q * dz;
+    double *__restrict__ Fd = a.Fd;
+    const double q = a.cqd[i];
+    Fd[p] = mad(-q, dx, Fd[p]);
+    Fd[N + p] = mad(-q, dy, Fd[N + p]);
+    Fd[2 * N + p] = mad(-q, dz, Fd[2 * N + p]);
   } else {
-    const float q = cqf[i];
-    F[p] -= q * fx;
-    F[N + p] -= q * fy;
-    F[2 * N + p] -= q * fz;
+    float *__restrict__ F = a.F;
+    const float q = a.cqf[i];
+    F[p] = mad(-q, fx, F[p]);
+    F[N + p] = mad(-q, fy, F[N + p]);
+    F[2 * N + p] = mad(-q, fz, F[2 * N + p]);
   }
+}
+RBE_MODE_KERNELS(__launch_bounds__(kGatherThreads), gather_kernel, GatherArgs, gather_body)
+
+template <int MODE>
+static cudaError_t sf_launch(Ctx &c, dim3 grid, size_t shm) {
+  const SfArgs a{c.cs, c.cqf, c.cqd, c.Nq, c.m, c.P, c.sf_tile, c.sf_part};
+  cudaError_t e = dispatch(c, sf_kernel<MODE>, sf_kernel_b<MODE>, grid, dim3(c.sf_mb), shm, a);
+  if (e != cudaSuccess) return e;
+  const CombineArgs b{c.sf_part, c.sf_nblk_p, c.P, c.kcd, c.alpha, c.rho, c.abf, c.abd, c.emode};
+  return dispatch(c, sf_combine_kernel<MODE>, sf_combine_kernel_b<MODE>, dim3(c.P), dim3(128),
+                  0, b);
 }
 
 cudaError_t launch_structure_factor(Ctx &c) {
@@ -211,38 +275,22 @@ cudaError_t launch_structure_factor(Ctx &c) {
   const dim3 grid((unsigned)c.sf_nblk_p, (unsigned)c.sf_nblk_m);
   const size_t shm = (size_t)c.sf_tile * (sizeof(uint4) + (c.precision == RBE_FP64 ? 8 : 0));
   switch (c.precision) {
-    case RBE_FP32_COMP:
-      sf_kernel<0><<<grid, c.sf_mb, shm, c.stream>>>(c.cs, c.cqf, c.cqd, c.Nq, c.m, c.P,
-                                                     c.sf_tile, c.sf_part);
-      sf_combine_kernel<0><<<c.P, 128, 0, c.stream>>>(c.sf_part, c.sf_nblk_p, c.P, c.kcd,
-                                                      c.alpha, c.rho, c.abf, c.abd, c.emode);
-      break;
-    case RBE_FP32:
-      sf_kernel<1><<<grid, c.sf_mb, shm, c.stream>>>(c.cs, c.cqf, c.cqd, c.Nq, c.m, c.P,
-                                                     c.sf_tile, c.sf_part);
-      sf_combine_kernel<1><<<c.P, 128, 0, c.stream>>>(c.sf_part, c.sf_nblk_p, c.P, c.kcd,
-                                                      c.alpha, c.rho, c.abf, c.abd, c.emode);
-      break;
-    default:
-      sf_kernel<2><<<grid, c.sf_mb, shm, c.stream>>>(c.cs, c.cqf, c.cqd, c.Nq, c.m, c.P,
-                                                     c.sf_tile, c.sf_part);
-      sf_combine_kernel<2><<<c.P, 128, 0, c.stream>>>(c.sf_part, c.sf_nblk_p, c.P, c.kcd,
-                                                      c.alpha, c.rho, c.abf, c.abd, c.emode);
-      break;
+    case RBE_FP32_COMP: return sf_launch<0>(c, grid, shm);
+    case RBE_FP32: return sf_launch<1>(c, grid, shm);
+    default: return sf_launch<2>(c, grid, shm);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_kspace_gather(Ctx &c) {
   if (c.Nq == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((c.Nq + kGatherThreads - 1) / kGatherThreads);
+  const GatherArgs a{c.cs, c.cqf, c.cqd, c.Nq, c.m, c.kcf, c.kcd, c.abf, c.abd, c.P, c.cmap,
+                     c.F, c.Fd, c.N};
   if (c.precision == RBE_FP64)
-    gather_kernel<2><<<blocks, kGatherThreads, 0, c.stream>>>(
-        c.cs, c.cqf, c.cqd, c.Nq, c.m, c.kcf, c.kcd, c.abf, c.abd, c.P, c.cmap, c.F, c.Fd, c.N);
-  else
-    gather_kernel<0><<<blocks, kGatherThreads, 0, c.stream>>>(
-        c.cs, c.cqf, c.cqd, c.Nq, c.m, c.kcf, c.kcd, c.abf, c.abd, c.P, c.cmap, c.F, c.Fd, c.N);
-  return cudaGetLastError();
+    return dispatch(c, gather_kernel<2>, gather_kernel_b<2>, dim3(blocks), dim3(kGatherThreads),
+                    0, a);
+  return dispatch(c, gather_kernel<0>, gather_kernel_b<0>, dim3(blocks), dim3(kGatherThreads), 0,
+                  a);
 }
 
 }  // namespace rbe

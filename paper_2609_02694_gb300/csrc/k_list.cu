@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256)
     const float dx = (float)(int)(s[i] - ref[i]) * hx;
     const float dy = (float)(int)(s[N + i] - ref[N + i]) * hy;
     const float dz = (float)(int)(s[2 * N + i] - ref[2 * N + i]) * hz;
-    moved = dx * dx + dy * dy + dz * dz >= lim2;
+    moved = mad(dx, dx, mad(dy, dy, dz * dz)) >= lim2;
   }
   if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) atomicOr(&flags[0], 1);
   if (i == 0) {

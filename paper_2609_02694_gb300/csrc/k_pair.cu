@@ -45,7 +45,7 @@ constexpr int kHitQ = 4;                // hit-mask queue entries per lane (at m
 // issue-bound loop (32 warps spill and run slower). One-warp blocks: a warp that finishes
 // early frees its slot instead of waiting at a block barrier for the slowest warp.
 template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
-__global__ void __launch_bounds__(kPairWarps * 32, 28 / kPairWarps) pair_kernel(const PairArgs a) {
+__device__ __forceinline__ void pair_body(const PairArgs &a, int bx, int) {
   __shared__ float4 stage[kPairWarps][kWin][T16 ? 1 : 32];     // FP32 test coordinates
   __shared__ uint4 stage16[kPairWarps][kWin][T16 ? 16 : 1];    // packed half test coordinates
   __shared__ int4 stage_d[kPairWarps][kWin][32];               // exact integer frame coords, type
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 28 / kPairWarps) pair_kernel(
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t n = a.set.n;
-  const int64_t i0 = ((int64_t)blockIdx.x * kPairWarps + wid) * 32;
+  const int64_t i0 = ((int64_t)bx * kPairWarps + wid) * 32;
   const int64_t i = i0 + lane;
   const bool valid = i < n;
   const LJTable *tab = a.table;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kPairWarps * 32, 28 / kPairWarps) pair_kernel(
             const float ex = (float)dsx * a.pc.h[0];
             const float ey = (float)dsy * a.pc.h[1];
             const float ez = (float)dsz * a.pc.h[2];
-            const bool hit = act && j != (int32_t)i && ex * ex + ey * ey + ez * ez <= a.pc.rc2_hi;
+            const bool hit = act && j != (int32_t)i && mad(ex, ex, mad(ey, ey, ez * ez)) <= a.pc.rc2_hi;
             if (hit && cnt < a.K) lst[(int64_t)cnt * 32] = j;
             cnt += hit ? 1 : 0;
           } else {
@@ -482,25 +482,28 @@ __global__ void __launch_bounds__(kPairWarps * 32, 28 / kPairWarps) pair_kernel(
   if (threadIdx.x < NQ_PAIR) {
     double s = 0.0;
     for (int w = 0; w < kPairWarps; ++w) s += wred[w][threadIdx.x];
-    a.epart[(int64_t)blockIdx.x * NQ_PAIR + threadIdx.x] = 0.5 * s;
+    a.epart[(int64_t)bx * NQ_PAIR + threadIdx.x] = 0.5 * s;
   }
 }
 
+template <typename real, bool LJ, bool COUL, bool MULTI, bool WRAP, bool T16, bool BUILD>
+__global__ void __launch_bounds__(kPairWarps * 32, 28 / kPairWarps) pair_kernel(const PairArgs a) {
+  pair_body<real, LJ, COUL, MULTI, WRAP, T16, BUILD>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
 template <typename real, bool LJ, bool COUL, bool BUILD = false>
-static void launch_one(const PairArgs &a, int64_t n, bool multi, bool wrap, cudaStream_t st) {
+static cudaError_t launch_one(Ctx &c, const PairArgs &a, int64_t n, bool multi, bool wrap) {
   const unsigned blocks = (unsigned)((n + 32 * kPairWarps - 1) / (32 * kPairWarps));
-  if (blocks == 0) return;
+  if (blocks == 0) return cudaSuccess;
   const dim3 g(blocks), b(kPairWarps * 32);
-  if (wrap) {
-    if (multi) pair_kernel<real, LJ, COUL, true, true, false, BUILD><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, true, false, BUILD><<<g, b, 0, st>>>(a);
-  } else if (a.smax16 > 0) {
-    if (multi) pair_kernel<real, LJ, COUL, true, false, true, BUILD><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, false, true, BUILD><<<g, b, 0, st>>>(a);
-  } else {
-    if (multi) pair_kernel<real, LJ, COUL, true, false, false, BUILD><<<g, b, 0, st>>>(a);
-    else pair_kernel<real, LJ, COUL, false, false, false, BUILD><<<g, b, 0, st>>>(a);
-  }
+  // (per replica in a batch; the list build is not used batched)
+#define RBE_PK(MU, WR, T)                                                                     \
+  dispatch(c, pair_kernel<real, LJ, COUL, MU, WR, T, BUILD>,                                  \
+           nullptr, g, b, 0, a, !BUILD)
+  if (wrap) return multi ? RBE_PK(true, true, false) : RBE_PK(false, true, false);
+  if (a.smax16 > 0) return multi ? RBE_PK(true, false, true) : RBE_PK(false, false, true);
+  return multi ? RBE_PK(true, false, false) : RBE_PK(false, false, false);
+#undef RBE_PK
 }
 
 // Group x-extent (cells) for the half-precision test at cutoff rc with stencil R: every
@@ -599,11 +602,13 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
     if (e != cudaSuccess) return e;
   } else {
     if (fused) {
-      if (fp64) launch_one<double, true, true>(a, c.N, multi, wrap, c.stream);
-      else launch_one<float, true, true>(a, c.N, multi, wrap, c.stream);
+      const cudaError_t e = fp64 ? launch_one<double, true, true>(c, a, c.N, multi, wrap)
+                                 : launch_one<float, true, true>(c, a, c.N, multi, wrap);
+      if (e != cudaSuccess) return e;
     } else {
-      if (fp64) launch_one<double, true, false>(a, c.N, multi, wrap, c.stream);
-      else launch_one<float, true, false>(a, c.N, multi, wrap, c.stream);
+      const cudaError_t e = fp64 ? launch_one<double, true, false>(c, a, c.N, multi, wrap)
+                                 : launch_one<float, true, false>(c, a, c.N, multi, wrap);
+      if (e != cudaSuccess) return e;
     }
     zero_partials_tail(c, c.off_pair, pair_blocks(c.N), c.n_pair_blk);
   }
@@ -640,14 +645,16 @@ cudaError_t launch_list_build(Ctx &c) {
   set_pretest_band(c, a, rl, wrap);
   a.list = c.vl_list; a.len = c.vl_len; a.K = c.vl_K;
   a.gate = c.vl_flags; a.maxlen = c.vl_flags + 2; a.err = c.err;
-  launch_one<float, false, false, true>(a, c.N, false, wrap, c.stream);
+  cudaError_t e = launch_one<float, false, false, true>(c, a, c.N, false, wrap);
+  if (e != cudaSuccess) return e;
   if (!fused && c.Nq > 0) {
     PairArgs q = a;
     q.set.sx = c.cs; q.set.sy = c.cs + c.Nq; q.set.sz = c.cs + 2 * c.Nq;
     q.set.qf = c.cqf; q.set.qd = c.cqd; q.set.type = nullptr;
     q.set.cell_start = c.ccell_start; q.set.map = c.cmap; q.set.n = c.Nq;
     q.list = c.vl_listq; q.len = c.vl_lenq; q.K = c.vl_Kq; q.maxlen = c.vl_flags + 3;
-    launch_one<float, false, false, true>(q, c.Nq, false, wrap, c.stream);
+    e = launch_one<float, false, false, true>(c, q, c.Nq, false, wrap);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

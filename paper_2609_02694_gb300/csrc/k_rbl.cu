@@ -104,7 +104,7 @@ __device__ __forceinline__ void rbl_pair_ds(const RblArgs &a, const LJTable *tab
   } else {
     dx = (real)((float)dsx * pc.h[0]); dy = (real)((float)dsy * pc.h[1]); dz = (real)((float)dsz * pc.h[2]);
   }
-  const real r2 = dx * dx + dy * dy + dz * dz;
+  const real r2 = mad(dx, dx, mad(dy, dy, dz * dz));
   pair_force_v<real, true, COUL, MULTI>(a.pa, tab, dx, dy, dz, r2, qi, ti, qj, tj, acc);
 }
 
@@ -120,7 +120,7 @@ __device__ __forceinline__ PairAcc<real> rbl_pair_eval(const RblArgs &a, const L
   } else {
     dx = (real)((float)dsx * pc.h[0]); dy = (real)((float)dsy * pc.h[1]); dz = (real)((float)dsz * pc.h[2]);
   }
-  const real r2 = dx * dx + dy * dy + dz * dz;
+  const real r2 = mad(dx, dx, mad(dy, dy, dz * dz));
   const real on = act ? (real)1 : (real)0;
   const real r2s = act ? r2 : (real)1;
   PairAcc<real> t;
@@ -136,8 +136,8 @@ template <typename real>
 __device__ __forceinline__ void rbl_acc_add(const RblArgs &a, bool on_, const PairAcc<real> &t,
                                             PairAcc<real> &acc) {
   const real on = on_ ? (real)1 : (real)0;
-  acc.fx += on * t.fx; acc.fy += on * t.fy; acc.fz += on * t.fz;
-  acc.ulj += on * t.ulj; acc.wlj += on * t.wlj;
+  acc.fx = mad(on, t.fx, acc.fx); acc.fy = mad(on, t.fy, acc.fy); acc.fz = mad(on, t.fz, acc.fz);
+  acc.ulj = mad(on, t.ulj, acc.ulj); acc.wlj = mad(on, t.wlj, acc.wlj);
   if (a.pa.comp) {
     real s = acc.uc, cs = acc.cuc, w = acc.wc, cw = acc.cwc;
     kahan_add(s, cs, t.uc);
@@ -145,8 +145,8 @@ __device__ __forceinline__ void rbl_acc_add(const RblArgs &a, bool on_, const Pa
     acc.uc = on_ ? s : acc.uc; acc.cuc = on_ ? cs : acc.cuc;
     acc.wc = on_ ? w : acc.wc; acc.cwc = on_ ? cw : acc.cwc;
   } else {
-    acc.uc += on * t.uc;
-    acc.wc += on * t.wc;
+    acc.uc = mad(on, t.uc, acc.uc);
+    acc.wc = mad(on, t.wc, acc.wc);
   }
 }
 
@@ -524,9 +524,9 @@ __global__ void __launch_bounds__(kRblWarps * 32, 16) rbl_kernel(const RblArgs a
     }
     if (valid) {
       const real w = nsh > a.p ? (real)nsh / (real)a.p : (real)1;
-      fx = core.fx + w * shell.fx;
-      fy = core.fy + w * shell.fy;
-      fz = core.fz + w * shell.fz;
+      fx = mad(w, shell.fx, core.fx);
+      fy = mad(w, shell.fy, core.fy);
+      fz = mad(w, shell.fz, core.fz);
       en[Q_UREAL] = ((double)core.uc - (double)core.cuc) +
                     (double)w * ((double)shell.uc - (double)shell.cuc);
       en[Q_ULJ] = (double)(core.ulj + w * shell.ulj);

@@ -50,7 +50,7 @@ struct PairArgs {
 
 // Fold a coordinate difference into [-L/2, L/2) (only the small-box variants use it).
 __device__ __forceinline__ float fold(float d, float L, float invL) {
-  return d - L * rintf(d * invL);
+  return mad(-L, rintf(d * invL), d);
 }
 
 template <typename real>
@@ -93,9 +93,9 @@ __device__ __forceinline__ void lj_terms(const PairArgs &a, const LJTable *tab, 
     else { A = (real)a.ljA; B = (real)a.ljB; A12 = (real)a.ljA12; B6 = (real)a.ljB6; }
   }
   const real ir6 = ir2 * ir2 * ir2;
-  w = ir6 * (A12 * ir6 - B6);
+  w = ir6 * mad(A12, ir6, -B6);
   gl = w * ir2;
-  u = ir6 * (A * ir6 - B);
+  u = ir6 * mad(A, ir6, -B);
 }
 
 // Pair force, energies and virial of one pair that is inside the cutoff (Eqs. F_i,
@@ -135,21 +135,21 @@ __device__ __forceinline__ void pair_force_v(const PairArgs &a, const LJTable *t
       const real tsp = sizeof(real) == 8 ? (real)pc.two_sqrt_alpha_over_sqrt_pi_d
                                          : (real)pc.two_sqrt_alpha_over_sqrt_pi;
       const real rinv2 = rinv * rinv;
-      const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
+      const real gc = Cqq * mad(erfcv * rinv, rinv2, tsp * expv * rinv2);
       g += gc;
       // erfc-Coulomb pair energies of both signs cancel heavily: compensate the sums
       if (a.comp) {
         kahan_add(acc.uc, acc.cuc, Cqq * erfcv * rinv);
         kahan_add(acc.wc, acc.cwc, gc * r2);
       } else {
-        acc.uc += Cqq * erfcv * rinv;
-        acc.wc += gc * r2;
+        acc.uc = mad(Cqq * erfcv, rinv, acc.uc);
+        acc.wc = mad(gc, r2, acc.wc);
       }
     }
   }
-  acc.fx += g * dx;
-  acc.fy += g * dy;
-  acc.fz += g * dz;
+  acc.fx = mad(g, dx, acc.fx);
+  acc.fy = mad(g, dy, acc.fy);
+  acc.fz = mad(g, dz, acc.fz);
 }
 
 // Same, with the charge and type of j read from the set.
@@ -190,7 +190,7 @@ __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTabl
     dx = (real)((float)dsx * pc.h[0]);
     dy = (real)((float)dsy * pc.h[1]);
     dz = (real)((float)dsz * pc.h[2]);
-    r2 = dx * dx + dy * dy + dz * dz;
+    r2 = mad(dx, dx, mad(dy, dy, dz * dz));
     inside = act && (float)r2 < pc.rc2_lo && (float)r2 > 0.f;
     const bool band = act && (float)r2 >= pc.rc2_lo && (float)r2 <= pc.rc2_hi;
     if (band) inside = exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d;
@@ -230,20 +230,20 @@ __device__ __forceinline__ void pair_eval_masked(const PairArgs &a, const LJTabl
       const real tsp = sizeof(real) == 8 ? (real)pc.two_sqrt_alpha_over_sqrt_pi_d
                                          : (real)pc.two_sqrt_alpha_over_sqrt_pi;
       const real rinv2 = rinv * rinv;
-      const real gc = Cqq * (erfcv * rinv * rinv2 + tsp * expv * rinv2);
+      const real gc = Cqq * mad(erfcv * rinv, rinv2, tsp * expv * rinv2);
       g += gc;
       if (a.comp) {
         kahan_add(acc.uc, acc.cuc, Cqq * erfcv * rinv);
         kahan_add(acc.wc, acc.cwc, gc * r2);
       } else {
-        acc.uc += Cqq * erfcv * rinv;
-        acc.wc += gc * r2;
+        acc.uc = mad(Cqq * erfcv, rinv, acc.uc);
+        acc.wc = mad(gc, r2, acc.wc);
       }
     }
   }
-  acc.fx += g * dx;
-  acc.fy += g * dy;
-  acc.fz += g * dz;
+  acc.fx = mad(g, dx, acc.fx);
+  acc.fy = mad(g, dy, acc.fy);
+  acc.fz = mad(g, dz, acc.fz);
 }
 
 // Exact cutoff decision from the integer displacement ds = s_i - s_j (mod 2^32, the
@@ -267,7 +267,7 @@ __device__ __forceinline__ void pair_body_ds(const PairArgs &a, const LJTable *t
     dx = (real)((float)dsx * pc.h[0]);
     dy = (real)((float)dsy * pc.h[1]);
     dz = (real)((float)dsz * pc.h[2]);
-    r2 = dx * dx + dy * dy + dz * dz;
+    r2 = mad(dx, dx, mad(dy, dy, dz * dz));
     if ((float)r2 > pc.rc2_hi) return;
     if ((float)r2 >= pc.rc2_lo && !(exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d)) return;
   }
@@ -298,7 +298,7 @@ __device__ __forceinline__ void pair_body(const PairArgs &a, const LJTable *tab,
     dx = (real)((float)dsx * pc.h[0]);
     dy = (real)((float)dsy * pc.h[1]);
     dz = (real)((float)dsz * pc.h[2]);
-    r2 = dx * dx + dy * dy + dz * dz;
+    r2 = mad(dx, dx, mad(dy, dy, dz * dz));
     if ((float)r2 > pc.rc2_hi) return;
     if ((float)r2 >= pc.rc2_lo) {  // exact decision inside the band
       if (!(exact_r2(pc, dsx, dsy, dsz) <= pc.rc2d)) return;

@@ -5,6 +5,7 @@
 // density of Eq. F_long_RBE, and the cell grid follows the cutoff. Every per-step
 // operation runs in the kernels of k_*.cu, on the caller's stream.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -93,7 +94,7 @@ uint32_t quantise(double r, double L) {
 
 namespace rbe {
 void mark(Ctx &c, int k) {
-  if (!c.timing || !c.ev[k]) return;
+  if (c.rec || !c.timing || !c.ev[k]) return;
   // during graph capture only an external record becomes an event node of the graph
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(c.stream, &st);
@@ -167,7 +168,7 @@ int force_pipeline(Ctx &c, bool debug) {
 
 // Kernels one Verlet step launches (memsets excluded).
 int64_t kernels_per_step(const Ctx &c) {
-  int64_t k = 2;                         // kick-drift, step counter
+  int64_t k = 1;                         // kick-drift (with the step counter)
   k += 6;                                // count, 3 scan passes, scatter, rank+permute
   k += 1;                                // sampler
   k += c.Nq > 0 ? 2 : 0;                 // structure factor + combine
@@ -238,8 +239,7 @@ int capture_step_graph(Ctx &c, int parity, cudaGraphExec_t *out) {
   int rc = RBE_OK;
   do {
     mark(c, RBE_PH_KICK_DRIFT);
-    if (launch_kick_drift(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
-    if (launch_step_advance(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+    if (launch_kick_drift(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }  // + step counter
     rc = force_pipeline(c, false);
     if (rc != RBE_OK) break;
     if (launch_kick(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
@@ -1133,58 +1133,325 @@ int rbe_get_memory(rbe_handle h, int64_t *bytes) {
   return RBE_OK;
 }
 
+// A class: replicas whose Verlet steps launch the same kernels in the same shapes. Each of
+// its launches runs once per step over the concatenated grids of all its replicas.
+// A class: replicas whose Verlet steps launch the same kernels in the same shapes. Each of
+// its kernels runs once per step over the concatenated grids of all its replicas.
+struct BatchClass {
+  std::vector<int> reps;
+};
+
 struct rbe_batch_s {
   std::vector<rbe_handle> h;
   std::vector<cudaStream_t> br;   // capture branches
   std::vector<cudaEvent_t> ev;    // join events
+  std::vector<cudaStream_t> sub;  // per-replica launches of a class: replica r's branch
+  std::vector<cudaEvent_t> sub_ev;
+  std::vector<cudaEvent_t> run_ev;  // per class: fork of its per-replica launches
   cudaEvent_t fork = nullptr;
   cudaStream_t stream = nullptr;  // launch stream
   cudaStream_t cap = nullptr;     // capture origin
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  void *dev[2] = {nullptr, nullptr};  // argument tables and block prefixes of each graph
   int phase = 0;
+  std::vector<int> exp_cur;       // each handle's buffer parity the graphs expect now
+  bool planned = false;
+  std::vector<BatchClass> cls;    // batched classes
+  std::vector<int> solo;          // replicas stepped on a branch of their own
+  int64_t kernels = 0;            // kernel launches per batch step
 };
+
+static void batch_drop_graphs(rbe_batch b) {
+  for (int k = 0; k < 2; ++k) {
+    if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    if (b->dev[k]) cudaFree(b->dev[k]);
+    b->graph[k] = nullptr;
+    b->dev[k] = nullptr;
+  }
+  b->phase = 0;
+}
 
 static int batch_free(rbe_batch b) {
   for (auto s : b->br) if (s) cudaStreamDestroy(s);
   for (auto e : b->ev) if (e) cudaEventDestroy(e);
+  for (auto s : b->sub) if (s) cudaStreamDestroy(s);
+  for (auto e : b->sub_ev) if (e) cudaEventDestroy(e);
+  for (auto e : b->run_ev) if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->cap) cudaStreamDestroy(b->cap);
-  for (int k = 0; k < 2; ++k) if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+  batch_drop_graphs(b);
   delete b;
   return RBE_OK;
 }
 
-// One graph: fork from the origin stream, each replica's Verlet step on its own branch,
-// join. `flip` selects the buffer parity after an odd number of steps.
-static int batch_capture(rbe_batch b, int flip, cudaGraphExec_t *out) {
+// One Verlet step of replica c on c.stream (the sequence rbe_step captures).
+static int step_sequence(Ctx &c) {
+  if (launch_kick_drift(c) != cudaSuccess) return RBE_ERR_CUDA;  // + step counter
+  int rc = force_pipeline(c, false);
+  if (rc != RBE_OK) return rc;
+  if (launch_kick(c) != cudaSuccess) return RBE_ERR_CUDA;
+  if (c.nvt && launch_thermostat(c, 0) != cudaSuccess) return RBE_ERR_CUDA;
+  if (launch_totals(c) != cudaSuccess) return RBE_ERR_CUDA;
+  return RBE_OK;
+}
+
+// Record the launches of one step of replica c at buffer parity flip. Returns false when
+// the step cannot run batched: a traversal without batched kernels (random batch list,
+// Verlet list), a kernel without a batched form, or any other stream work, which the
+// recording catches in a throwaway capture of a scratch stream.
+static bool record_step(Ctx &c, int flip, Recorder &rec) {
+  if (c.rbl || c.vl_on) return false;
+  cudaStream_t scratch = nullptr;
+  if (cudaStreamCreateWithFlags(&scratch, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int saved_cur = c.cur;
+  cudaStream_t saved_stream = c.stream;
+  c.cur = flip ? 1 - saved_cur : saved_cur;
+  c.stream = scratch;
+  c.rec = &rec;
+  bool ok = cudaStreamBeginCapture(scratch, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    ok = step_sequence(c) == RBE_OK && rec.ok;
+    cudaGraph_t g = nullptr;
+    size_t nodes = 0;
+    if (cudaStreamEndCapture(scratch, &g) != cudaSuccess) ok = false;
+    if (g) {
+      if (cudaGraphGetNodes(g, nullptr, &nodes) != cudaSuccess || nodes != 0) ok = false;
+      cudaGraphDestroy(g);
+    }
+  }
+  c.rec = nullptr;
+  c.cur = saved_cur;
+  c.stream = saved_stream;
+  cudaStreamDestroy(scratch);
+  cudaGetLastError();
+  return ok;
+}
+
+// Same kernel (batched and solo: a kernel launched per replica has no batched form, so its
+// solo instance decides) and the same block shape.
+static bool same_shape(const RecItem &x, const RecItem &y) {
+  return x.fn == y.fn && x.solo_fn == y.solo_fn && x.per_replica == y.per_replica &&
+         x.grid.y == y.grid.y && x.grid.z == y.grid.z &&
+         x.block.x == y.block.x && x.block.y == y.block.y && x.block.z == y.block.z &&
+         x.smem == y.smem && x.args.size() == y.args.size();
+}
+static bool same_sequence(const Recorder &x, const Recorder &y) {
+  if (x.items.size() != y.items.size()) return false;
+  for (size_t i = 0; i < x.items.size(); ++i)
+    if (!same_shape(x.items[i], y.items[i])) return false;
+  return true;
+}
+
+// Group the replicas into classes by the kernels and shapes of their steps (at both
+// buffer parities); a class of one gains nothing and steps on its own branch.
+static int batch_plan(rbe_batch b) {
   const int n = (int)b->h.size();
+  std::vector<Recorder> rec(n);
+  std::vector<bool> ok(n);
+  for (int r = 0; r < n; ++r) {
+    Recorder other;
+    ok[r] = record_step(*b->h[r], 0, rec[r]) && record_step(*b->h[r], 1, other) &&
+            same_sequence(rec[r], other);
+  }
+  b->cls.clear();
+  b->solo.clear();
+  for (int r = 0; r < n; ++r) {
+    if (!ok[r]) {
+      b->solo.push_back(r);
+      continue;
+    }
+    bool placed = false;
+    for (auto &k : b->cls)
+      if (same_sequence(rec[k.reps[0]], rec[r])) {
+        k.reps.push_back(r);
+        placed = true;
+        break;
+      }
+    if (!placed) b->cls.push_back(BatchClass{{r}});
+  }
+  for (size_t k = 0; k < b->cls.size();) {
+    if (b->cls[k].reps.size() < 2) {
+      b->solo.push_back(b->cls[k].reps[0]);
+      b->cls.erase(b->cls.begin() + k);
+    } else {
+      ++k;
+    }
+  }
+  std::sort(b->solo.begin(), b->solo.end());
+  b->kernels = 0;
+  for (auto &k : b->cls)
+    for (size_t i = 0; i < rec[k.reps[0]].items.size(); ++i) {
+      int64_t blocks = 0, launches = 0;
+      for (int r : k.reps) {
+        blocks += rec[r].items[i].grid.x;
+        launches += rec[r].items[i].grid.x > 0 ? 1 : 0;
+      }
+      if (rec[k.reps[0]].items[i].per_replica) b->kernels += launches;
+      else if (blocks > 0) b->kernels += 1;
+    }
+  for (int r : b->solo) b->kernels += kernels_per_step(*b->h[r]);
+  b->planned = true;
+  return RBE_OK;
+}
+
+// One launch of a class: the batched kernel, the concatenated grid, and its tables; or,
+// for a kernel launched per replica, the solo kernel with each replica's grid and arguments.
+struct ClassLaunch {
+  const void *fn;
+  dim3 grid, block;
+  size_t smem, tab_off, pre_off;
+  bool per_replica;
+  std::vector<dim3> grids;
+  std::vector<std::vector<unsigned char>> args;
+};
+
+// Record every class's step at buffer parity flip, lay the argument tables and block
+// prefixes out in one device buffer (uploaded here) and return the launches.
+static int batch_tables(rbe_batch b, int flip, void **dev, std::vector<std::vector<ClassLaunch>> &out) {
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  std::vector<std::vector<Recorder>> rec(b->cls.size());
+  size_t bytes = 0;
+  out.assign(b->cls.size(), {});
+  for (size_t k = 0; k < b->cls.size(); ++k) {
+    const auto &reps = b->cls[k].reps;
+    rec[k].resize(reps.size());
+    for (size_t j = 0; j < reps.size(); ++j)
+      if (!record_step(*b->h[reps[j]], flip, rec[k][j]) || !same_sequence(rec[k][0], rec[k][j]))
+        return RBE_ERR_STATE;  // a handle's configuration changed since the plan
+    for (size_t i = 0; i < rec[k][0].items.size(); ++i) {
+      const RecItem &it = rec[k][0].items[i];
+      ClassLaunch L;
+      L.block = it.block;
+      L.smem = it.smem;
+      L.per_replica = it.per_replica;
+      L.tab_off = L.pre_off = 0;
+      if (it.per_replica) {
+        L.fn = it.solo_fn;
+        L.grid = it.grid;
+        for (size_t j = 0; j < reps.size(); ++j) {
+          L.grids.push_back(rec[k][j].items[i].grid);
+          L.args.push_back(rec[k][j].items[i].args);
+        }
+      } else {
+        L.fn = it.fn;
+        L.grid = dim3(0, it.grid.y, it.grid.z);
+        L.tab_off = bytes;
+        bytes = align(bytes + it.args.size() * reps.size());
+        L.pre_off = bytes;
+        bytes = align(bytes + sizeof(int32_t) * (reps.size() + 1));
+      }
+      out[k].push_back(std::move(L));
+    }
+  }
+  std::vector<unsigned char> host(bytes, 0);
+  for (size_t k = 0; k < b->cls.size(); ++k)
+    for (size_t i = 0; i < out[k].size(); ++i) {
+      ClassLaunch &L = out[k][i];
+      if (L.per_replica) continue;
+      const size_t sz = rec[k][0].items[i].args.size();
+      int32_t *pp = reinterpret_cast<int32_t *>(host.data() + L.pre_off);
+      int64_t pre = 0;
+      for (size_t j = 0; j < rec[k].size(); ++j) {
+        const RecItem &it = rec[k][j].items[i];
+        std::memcpy(host.data() + L.tab_off + j * sz, it.args.data(), sz);
+        pp[j] = (int32_t)pre;
+        pre += it.grid.x;
+        if (pre > INT32_MAX) return RBE_ERR_INVALID;
+      }
+      pp[rec[k].size()] = (int32_t)pre;
+      L.grid.x = (unsigned)pre;
+    }
+  *dev = nullptr;
+  if (bytes == 0) return RBE_OK;
+  if (cudaMalloc(dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *dev = nullptr;
+    return RBE_ERR_OOM;
+  }
+  RBE_CUDA_TRY(cudaMemcpy(*dev, host.data(), bytes, cudaMemcpyHostToDevice));
+  return RBE_OK;
+}
+
+// Graph k: fork from the origin stream; each class's launches in order on a branch of its
+// own, and each remaining replica's Verlet step on a branch of its own; join. `flip`
+// selects the buffer parity relative to the handles' current one.
+static int batch_capture(rbe_batch b, int k, int flip) {
+  const int n = (int)b->h.size();
+  std::vector<std::vector<ClassLaunch>> launches;
+  int rc = batch_tables(b, flip, &b->dev[k], launches);
+  if (rc != RBE_OK) return rc;
   std::vector<int> saved_cur(n);
   std::vector<cudaStream_t> saved_stream(n);
   for (int r = 0; r < n; ++r) {
     saved_cur[r] = b->h[r]->cur;
     saved_stream[r] = b->h[r]->stream;
-    b->h[r]->cur = flip ? 1 - saved_cur[r] : saved_cur[r];
-    b->h[r]->stream = b->br[r];
   }
-  int rc = RBE_OK;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaEventRecord(b->fork, b->cap);
-    for (int r = 0; r < n && rc == RBE_OK; ++r) {
-      Ctx &c = *b->h[r];
-      if (cudaStreamWaitEvent(b->br[r], b->fork, 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
-      if (launch_kick_drift(c) != cudaSuccess || launch_step_advance(c) != cudaSuccess) {
-        rc = RBE_ERR_CUDA;
-        break;
+    int nb = 0;  // branches used
+    for (size_t kc = 0; kc < b->cls.size() && rc == RBE_OK; ++kc) {
+      cudaStream_t st = b->br[nb];
+      if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      const auto &reps = b->cls[kc].reps;
+      int nrep = (int)reps.size();
+      const auto &Ls = launches[kc];
+      for (size_t i = 0; i < Ls.size() && rc == RBE_OK;) {
+        if (Ls[i].per_replica) {
+          // a run of per-replica launches: fork one branch per replica, then join
+          size_t i1 = i;
+          while (i1 < Ls.size() && Ls[i1].per_replica) ++i1;
+          if (cudaEventRecord(b->run_ev[kc], st) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+          for (int j = 0; j < nrep && rc == RBE_OK; ++j) {
+            cudaStream_t ss = b->sub[reps[j]];
+            if (cudaStreamWaitEvent(ss, b->run_ev[kc], 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+            for (size_t q = i; q < i1; ++q) {
+              const ClassLaunch &L = Ls[q];
+              const dim3 g = L.grids[j];
+              if (g.x == 0) continue;
+              void *params[] = {const_cast<unsigned char *>(L.args[j].data())};
+              if (cudaLaunchKernel(L.fn, g, L.block, params, L.smem, ss) != cudaSuccess) {
+                rc = RBE_ERR_CUDA;
+                break;
+              }
+            }
+            if (rc != RBE_OK) break;
+            cudaEventRecord(b->sub_ev[reps[j]], ss);
+            cudaStreamWaitEvent(st, b->sub_ev[reps[j]], 0);
+          }
+          i = i1;
+          continue;
+        }
+        const ClassLaunch &L = Ls[i++];
+        if (L.grid.x == 0) continue;
+        const void *tab = static_cast<char *>(b->dev[k]) + L.tab_off;
+        const void *pre = static_cast<char *>(b->dev[k]) + L.pre_off;
+        void *params[] = {&tab, &pre, &nrep};
+        if (cudaLaunchKernel(L.fn, L.grid, L.block, params, L.smem, st) != cudaSuccess) {
+          rc = RBE_ERR_CUDA;
+          break;
+        }
       }
-      rc = force_pipeline(c, false);
       if (rc != RBE_OK) break;
-      if (launch_kick(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
-      if (c.nvt && launch_thermostat(c, 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
-      if (launch_totals(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
-      cudaEventRecord(b->ev[r], b->br[r]);
-      cudaStreamWaitEvent(b->cap, b->ev[r], 0);
+      cudaEventRecord(b->ev[nb], st);
+      cudaStreamWaitEvent(b->cap, b->ev[nb], 0);
+      ++nb;
+    }
+    for (size_t j = 0; j < b->solo.size() && rc == RBE_OK; ++j) {
+      Ctx &c = *b->h[b->solo[j]];
+      cudaStream_t st = b->br[nb];
+      c.cur = flip ? 1 - c.cur : c.cur;
+      c.stream = st;
+      if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      rc = step_sequence(c);
+      if (rc != RBE_OK) break;
+      cudaEventRecord(b->ev[nb], st);
+      cudaStreamWaitEvent(b->cap, b->ev[nb], 0);
+      ++nb;
     }
     e = cudaStreamEndCapture(b->cap, &g);
   }
@@ -1197,7 +1464,7 @@ static int batch_capture(rbe_batch b, int flip, cudaGraphExec_t *out) {
     return rc;
   }
   RBE_CUDA_TRY(e);
-  e = cudaGraphInstantiate(out, g, 0);
+  e = cudaGraphInstantiate(&b->graph[k], g, 0);
   cudaGraphDestroy(g);
   RBE_CUDA_TRY(e);
   return RBE_OK;
@@ -1214,11 +1481,17 @@ int rbe_batch_create(rbe_batch *out, int n, const rbe_handle *handles, void *cud
   b->stream = (cudaStream_t)cuda_stream;
   b->br.assign(n, nullptr);
   b->ev.assign(n, nullptr);
+  b->sub.assign(n, nullptr);
+  b->sub_ev.assign(n, nullptr);
+  b->run_ev.assign(n, nullptr);
   bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
   for (int r = 0; r < n && ok; ++r)
     ok = cudaStreamCreateWithFlags(&b->br[r], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&b->ev[r], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&b->ev[r], cudaEventDisableTiming) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&b->sub[r], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->sub_ev[r], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->run_ev[r], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     batch_free(b);
@@ -1245,20 +1518,54 @@ int rbe_batch_step(rbe_batch b, int nsteps) {
     }
     RBE_CUDA_TRY(cudaStreamSynchronize(h->stream));
   }
+  if (!b->planned) {
+    const int rc = batch_plan(b);
+    if (rc != RBE_OK) return rc;
+  }
+  // the graphs hold buffer pointers by parity: capture them again when a handle's parity is
+  // not the one they expect (the handle stepped on its own in between)
+  bool moved = b->exp_cur.size() != b->h.size();
+  for (size_t r = 0; r < b->exp_cur.size() && !moved; ++r) moved = b->exp_cur[r] != b->h[r]->cur;
+  if (moved) {
+    batch_drop_graphs(b);
+    b->exp_cur.resize(b->h.size());
+    for (size_t r = 0; r < b->h.size(); ++r) b->exp_cur[r] = b->h[r]->cur;
+  }
   for (int k = 0; k < 2; ++k)
     if (!b->graph[k]) {
-      int rc = batch_capture(b, (b->phase + k) & 1, &b->graph[k]);
-      if (rc != RBE_OK) return rc;
+      // graph k serves the steps at phase k: parity (phase + k) relative to now
+      const int rc = batch_capture(b, k, (b->phase + k) & 1);
+      if (rc != RBE_OK) {
+        batch_drop_graphs(b);
+        b->exp_cur.clear();
+        return rc;
+      }
     }
   for (int s = 0; s < nsteps; ++s) {
     RBE_CUDA_TRY(cudaGraphLaunch(b->graph[b->phase], b->stream));
     b->phase ^= 1;
-    for (auto h : b->h) {
+    for (size_t r = 0; r < b->h.size(); ++r) {
+      rbe_handle h = b->h[r];
       h->cur = 1 - h->cur;
       h->step += 1;
       h->have_forces = true;
+      b->exp_cur[r] = h->cur;
     }
   }
+  return RBE_OK;
+}
+
+int rbe_batch_info(rbe_batch b, int32_t *n_classes, int32_t *n_batched, int64_t *kernels) {
+  if (!b) return RBE_ERR_INVALID;
+  if (!b->planned) {
+    const int rc = batch_plan(b);
+    if (rc != RBE_OK) return rc;
+  }
+  int32_t nb = 0;
+  for (auto &k : b->cls) nb += (int32_t)k.reps.size();
+  if (n_classes) *n_classes = (int32_t)b->cls.size();
+  if (n_batched) *n_batched = nb;
+  if (kernels) *kernels = b->kernels;
   return RBE_OK;
 }
 

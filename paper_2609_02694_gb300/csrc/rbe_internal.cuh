@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/rbe.h"
 
 namespace rbe {
@@ -178,6 +180,8 @@ struct Ctx {
   int32_t *vl_flags = nullptr;       // 8 ints
   unsigned long long *vl_count = nullptr;  // builds, force evaluations
   int64_t vl_bytes = 0;
+  // batched replicas: while set, launches are recorded here instead of issued
+  struct Recorder *rec = nullptr;
   // graph
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per starting buffer parity
   cudaStream_t cap_stream = nullptr;  // internal non-blocking stream used only for capture
@@ -227,6 +231,11 @@ __device__ __forceinline__ double phase_to_radians_d(uint32_t ph) {
   return (double)(int)ph * (2.0 * kPi / kTwo32);
 }
 
+// Fused multiply-add a * b + c (one rounding) in either precision. The library is compiled
+// without implicit contraction: every fused multiply-add of a kernel is written with these.
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -237,6 +246,104 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+
+// ---------------------------------------------------------------------------------------
+// Launches for one replica or for a batch of replicas.
+//
+// A kernel's work is a body taking its arguments (one struct) and the block's index bx in
+// a grid of nbx blocks. The solo kernel runs the body on its own arguments with
+// (blockIdx.x, gridDim.x). The batched kernel (suffix _b) runs one launch over the
+// concatenated grids of many replicas: replica r owns blocks [pre[r], pre[r+1]) and its own
+// argument struct tab[r], so every block does exactly the work of the replica's own launch.
+// The library is compiled without implicit multiply-add contraction (every fused
+// multiply-add is written out), so the two kernels round every operation alike and give the
+// same results bit for bit.
+
+struct BatchIdx {
+  int r, bx, nbx;
+};
+
+// Replica of this block: the largest r with pre[r] <= blockIdx.x (empty ranges skipped).
+__device__ __forceinline__ BatchIdx batch_locate(const int32_t *__restrict__ pre, int nrep) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = nrep;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(pre + mid) <= b) lo = mid; else hi = mid;
+  }
+  BatchIdx q;
+  const int p0 = __ldg(pre + lo);
+  q.r = lo;
+  q.bx = b - p0;
+  q.nbx = __ldg(pre + lo + 1) - p0;
+  return q;
+}
+
+// One recorded launch: the batched and the solo kernel, whether a batch launches it per
+// replica, the replica's grid and block, dynamic shared memory and the bytes of its
+// argument struct.
+struct RecItem {
+  const void *fn, *solo_fn;
+  bool per_replica;
+  dim3 grid, block;
+  size_t smem;
+  std::vector<unsigned char> args;
+};
+struct Recorder {
+  std::vector<RecItem> items;
+  bool ok = true;  // false: a launch without a batched form was met
+};
+
+// Issue the solo kernel on c.stream, or record the launch while c.rec is set. `per_replica`:
+// a batch runs this kernel as one solo launch per replica, on parallel branches (the pair
+// kernels: their arguments as constant-bank operands save the registers a table costs; a
+// batched form of the cluster-pair kernel spilled and ran half as fast again). Otherwise a
+// kernel without a batched form (batched == nullptr) makes the recording unusable.
+template <class T>
+struct NoDeduce {
+  using type = T;
+};
+template <class A>
+cudaError_t dispatch(Ctx &c, void (*solo)(A),
+                     typename NoDeduce<void (*)(const A *, const int32_t *, int)>::type batched,
+                     dim3 grid, dim3 block, size_t smem, const A &a, bool per_replica = false) {
+  if (c.rec) {
+    if (!batched && !per_replica) {
+      c.rec->ok = false;
+      return cudaSuccess;
+    }
+    RecItem it;
+    it.fn = reinterpret_cast<const void *>(batched);
+    it.solo_fn = reinterpret_cast<const void *>(solo);
+    it.per_replica = per_replica;
+    it.grid = grid;
+    it.block = block;
+    it.smem = smem;
+    it.args.assign(reinterpret_cast<const unsigned char *>(&a),
+                   reinterpret_cast<const unsigned char *>(&a) + sizeof(A));
+    c.rec->items.push_back(std::move(it));
+    return cudaSuccess;
+  }
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+  A copy = a;
+  void *params[] = {&copy};
+  return cudaLaunchKernel(reinterpret_cast<const void *>(solo), grid, block, params, smem, c.stream);
+}
+
+// Zero `words` 32-bit words on c.stream (a memset, or a recorded zeroing kernel).
+cudaError_t fill_zero(Ctx &c, void *p, int64_t words);
+
+// Solo and batched kernels of a body; LB is the launch-bounds clause, the variadic tail the
+// argument type (which may hold template arguments).
+#define RBE_KERNELS(LB, NAME, BODY, ...)                                                        \
+  __global__ void LB NAME(const __VA_ARGS__ a) { BODY(a, (int)blockIdx.x, (int)gridDim.x); }  \
+  __global__ void LB NAME##_b(const __VA_ARGS__ *__restrict__ t,                              \
+                              const int32_t *__restrict__ pre, int nrep) {                    \
+    const BatchIdx q = batch_locate(pre, nrep);                                               \
+    BODY(t[q.r], q.bx, q.nbx);                                                                \
+  }
+#define RBE_BATCHED_KERNEL(LB, NAME, ARGS, BODY) RBE_KERNELS(LB, NAME, BODY, ARGS)
 
 // ---------------------------------------------------------------------------------------
 // Launchers (each in its own translation unit). All return cudaGetLastError().
@@ -263,7 +370,7 @@ cudaError_t launch_list_check(Ctx &c);    // rebuild flag from the displacements
 cudaError_t launch_list_build(Ctx &c);    // gated list build(s) at r_c + skin
 cudaError_t launch_list_commit(Ctx &c);   // gated: reference positions, counters
 cudaError_t launch_list_pair(Ctx &c, bool want_counts);  // pair forces from the lists
-cudaError_t launch_kick_drift(Ctx &c);
+cudaError_t launch_kick_drift(Ctx &c);  // also advances the device step counter
 cudaError_t launch_kick(Ctx &c);
 cudaError_t launch_kinetic(Ctx &c);
 cudaError_t launch_thermostat(Ctx &c, int mode);  // 0: end + next start half, 1: start half only

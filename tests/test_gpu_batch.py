@@ -28,10 +28,12 @@ def _handle(r, sy, precision="fp32_comp"):
                                replica=r, precision=precision)
 
 
-@pytest.mark.parametrize("precision", ["fp32_comp", "fp64"])
-def test_batch_equals_individual_steps(precision):
+@pytest.mark.parametrize("precision,order", [("fp32_comp", 1), ("fp64", 1), ("fp64", -1)])
+def test_batch_equals_individual_steps(precision, order):
+    """Uneven sizes, in either order: boxes whose pair kernels differ (half-precision
+    pre-test or not, cluster pairs or per-particle) fall into different classes."""
     import torch
-    reps = _replicas([2000, 5100, 3000, 9000, 2400])
+    reps = _replicas([2000, 5100, 3000, 9000, 2400][::order])
     hb = [_handle(r, sy, precision) for r, sy in reps]
     hi = [_handle(r, sy, precision) for r, sy in reps]
     with binding.Batch(hb) as b:
@@ -48,6 +50,44 @@ def test_batch_equals_individual_steps(precision):
             ec, _ = c.energies()
             assert ea["total"] == ec["total"]
             assert a.step_count() == c.step_count() == 5
+    for h in hb + hi:
+        h.close()
+
+
+@pytest.mark.parametrize("precision,nvt", [("fp32_comp", False), ("fp32", True),
+                                           ("fp64", False)])
+def test_batch_classes_equal_individual_steps(precision, nvt):
+    """Replicas of one configuration (uneven sizes) form one class: every kernel of the step
+    runs once over all of them, and the result is bit for bit what each replica's own steps
+    give (with the Nose-Hoover thermostat in one case)."""
+    import torch
+    reps = _replicas([20000, 31000, 26000, 40000])
+    hb = [_handle(r, sy, precision) for r, sy in reps]
+    hi = [_handle(r, sy, precision) for r, sy in reps]
+    if nvt:
+        for h in hb + hi:
+            h.set_thermostat(300.0, 50.0)
+    with binding.Batch(hb) as b:
+        ncls, nbat, kern = b.info()
+        # the FP32 forms share every kernel; the FP64 form's per-particle pair kernel has a
+        # half-precision pre-test variant that depends on the box
+        assert nbat == 4 and ncls == 1 if precision != "fp64" else nbat == 4 and ncls <= 2, \
+            (ncls, nbat, kern)
+        # one launch per kernel of the step and class, the pair kernels one per replica
+        assert 0 < kern < 30 * ncls + 3 * nbat
+        b.step(3)
+        torch.cuda.synchronize()
+        for h in hi:
+            h.step(3)
+        for a, c in zip(hb, hi):
+            _, va, sa = a.state()
+            _, vc, sc = c.state()
+            assert np.array_equal(sa, sc) and np.array_equal(va, vc)
+            ea, wa = a.energies()
+            ec, wc = c.energies()
+            assert ea == ec and wa == wc
+            if nvt:
+                assert a.thermostat() == c.thermostat()
     for h in hb + hi:
         h.close()
 
@@ -85,6 +125,7 @@ def test_batch_mixed_traversals_equal_individual_steps():
     hb = [make(r, sy) for r, sy in reps]
     hi = [make(r, sy) for r, sy in reps]
     with binding.Batch(hb) as b:
+        assert b.info()[:2] == (0, 0)  # list and RBL replicas, and a lone cell replica
         b.step(4)
         torch.cuda.synchronize()
         for h in hi:
@@ -132,6 +173,8 @@ def test_full_size_batch96(orc):
     hb = [make(r, sy) for r, sy in enumerate(systems)]
     hi = [make(r, sy) for r, sy in enumerate(systems)]
     with binding.Batch(hb) as b:
+        ncls, nbat, _ = b.info()
+        assert nbat >= 80 and ncls <= 6
         b.step(2)
         torch.cuda.synchronize()
         for h in hi:
