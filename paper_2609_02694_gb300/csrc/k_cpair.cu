@@ -940,14 +940,18 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
 #undef RBE_CP_LAUNCH
   if (e != cudaSuccess) return e;
   const int64_t n3 = 3 * c.N;
+  // (per replica in a batch too: it joins the pair kernel and the Coulomb pass in one run of
+  // per-replica launches, one fork and join per step instead of two)
   const dim3 fg((unsigned)(((n3 + 3) / 4 + 255) / 256)), fb(256);
   if (fp64) {
     const FinishArgs f{c.facc, c.Fd, n3, 0.f, 0.f, 1.0 / kFixScale64};
-    return dispatch(c, cpair_finalize_kernel<double>, cpair_finalize_kernel_b<double>, fg, fb, 0, f);
+    return dispatch(c, cpair_finalize_kernel<double>, cpair_finalize_kernel_b<double>, fg, fb, 0, f,
+                    true);
   }
   const FinishArgs f{c.facc, c.F, n3, (float)(4294967296.0 / kFixScale32),
                      (float)(1.0 / kFixScale32), 0.0};
-  return dispatch(c, cpair_finalize_kernel<float>, cpair_finalize_kernel_b<float>, fg, fb, 0, f);
+  return dispatch(c, cpair_finalize_kernel<float>, cpair_finalize_kernel_b<float>, fg, fb, 0, f,
+                  true);
 }
 
 }  // namespace rbe
