@@ -68,6 +68,8 @@ __device__ __forceinline__ void coul_body(const CoulArgs a, int bx, int) {
     const int R1 = a.grid.R[1], R2 = a.grid.R[2];
     const int cy = cell_of(pi.y, n1), cz = cell_of(pi.z, n2);
     const int ny = 2 * R1 + 1, nrows = ny * (2 * R2 + 1);
+    // t / ny as (t m) >> 8, m = ceil(256 / ny): exact for t < 64 and ny in {1, 3, 5, 7}
+    const int mny = (256 + ny - 1) / ny;
     // i's y and z in cell units, and the cell widths
     const float fyc = (float)pi.y * ((float)n1 * 2.3283064365386963e-10f);
     const float fzc = (float)pi.z * ((float)n2 * 2.3283064365386963e-10f);
@@ -77,7 +79,8 @@ __device__ __forceinline__ void coul_body(const CoulArgs a, int bx, int) {
       const int t = rb + lane;
       int b0 = 0, l0 = 0, b1 = 0, l1 = 0;
       if (t < nrows) {
-        const int dz = t / ny - R2, dy = t % ny - R1;
+        const int tq = (t * mny) >> 8;
+        const int dz = tq - R2, dy = t - tq * ny - R1;
         // distance of i from the row's cells in y and z, in cell widths (i's position in cell
         // units is within about 1e-5 cells in FP32; the distance is shrunk by 1e-3 cells)
         const float ey = fmaxf(0.f, fmaxf((float)(cy + dy) - fyc, fyc - (float)(cy + dy + 1)) - 1e-3f);
@@ -85,7 +88,12 @@ __device__ __forceinline__ void coul_body(const CoulArgs a, int bx, int) {
         const float dyl = ey * wy, dzl = ez * wz;
         const float rx2 = mad(-dzl, dzl, mad(-dyl, dyl, a.reach2));
         if (rx2 > 0.f) {
-          const int ryw = ((cy + dy) % n1 + n1) % n1, rzw = ((cz + dz) % n2 + n2) % n2;
+          // periodic row indices (|dy| <= R1 < n1, |dz| <= R2 < n2)
+          int ryw = cy + dy, rzw = cz + dz;
+          ryw += ryw < 0 ? n1 : 0;
+          ryw -= ryw >= n1 ? n1 : 0;
+          rzw += rzw < 0 ? n2 : 0;
+          rzw -= rzw >= n2 ? n2 : 0;
           const int64_t rowbase = (int64_t)n0 * (ryw + (int64_t)n1 * rzw);
           // x-cells within reach (unwrapped floor division by the cell width)
           const int64_t reach = (int64_t)(sqrtf(rx2) * (1.0f + 1e-5f) / pc.h[0]) + 4;

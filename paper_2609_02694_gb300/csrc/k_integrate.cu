@@ -203,8 +203,10 @@ struct TotalsArgs {
 
 // Fixed-order reduction of every partial into the scalars (ACC = float for the plain
 // FP32 form, double otherwise). One block of kTotalsThreads: strided per-thread sums (four
-// partials in flight per thread), then warp shuffles, then the warp sums in order.
-constexpr int kTotalsThreads = 1024;
+// partials in flight per thread), then warp shuffles, then the warp sums in order. Four
+// warps: the warp reductions of seven FP64 sums dominate on one SM (FP64 runs at 1/64 of the
+// FP32 rate), and they scale with the warps, the strided sums do not.
+constexpr int kTotalsThreads = 128;
 
 template <typename ACC>
 __device__ __forceinline__ void totals_body(const TotalsArgs &a, int, int) {
