@@ -227,8 +227,8 @@ constexpr int kCellsPerWarp = 4;
 
 // One warp per kCellsPerWarp consecutive cells: rank members by their key (and charged
 // members among themselves), then move every field to the final slot. When no cell of the four
-// holds more than 8 particles (dilute systems), each cell gets 8 lanes; otherwise the warp
-// takes the cells one after another, 32 members at a time.
+// holds more than 8 (16) particles, each cell gets 8 (16) lanes; otherwise the warp takes the
+// cells one after another, 32 members at a time.
 __device__ __forceinline__ void bin_rank_permute_body(const PermuteArgs &a, int bx, int) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -237,25 +237,32 @@ __device__ __forceinline__ void bin_rank_permute_body(const PermuteArgs &a, int 
   int cnt4 = 0;
   if (lane < kCellsPerWarp && c0 + lane < a.ncell)
     cnt4 = a.cell_start[c0 + lane + 1] - a.cell_start[c0 + lane];
-  if (__all_sync(FULL, cnt4 <= 8)) {
-    const int64_t c = c0 + (lane >> 3);
-    const int k = lane & 7;
-    const bool cell_ok = c < a.ncell;
-    const int32_t beg = cell_ok ? a.cell_start[c] : 0;
-    const int32_t cnt = cell_ok ? a.cell_start[c + 1] - beg : 0;
-    const bool valid = k < cnt;
-    const int32_t o = valid ? a.tmp[beg + k] : 0;
-    const int32_t myid = valid ? a.id0[o] : INT_MAX;
-    const uint64_t mykey = valid ? member_key(a, o, myid) : ~0ull;
-    const int mych = (valid && a.qf0[o] != 0.0f) ? 1 : 0;
-    int rank = 0, crank = 0;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {  // 8-lane segments: lanes past the count hold the maximum
-      const uint64_t x = __shfl_sync(FULL, mykey, t, 8);
-      const int xc = __shfl_sync(FULL, mych, t, 8);
-      if (x < mykey) { ++rank; crank += xc; }
+  // Cells of at most 8 (16) members: 8-lane (16-lane) segments, one cell each, in one (two)
+  // rounds; lanes past a cell's count hold the largest key. Larger cells: one cell after
+  // another, 32 members at a time (below).
+  const int mx = __reduce_max_sync(FULL, cnt4);
+  if (mx <= 16) {
+    const int W = mx <= 8 ? 8 : 16;
+    const int lw = W == 8 ? 3 : 4;
+    for (int r = 0; r < W / 8; ++r) {
+      const int64_t c = c0 + r * (32 / W) + (lane >> lw);
+      const int k = lane & (W - 1);
+      const bool cell_ok = c < a.ncell;
+      const int32_t beg = cell_ok ? a.cell_start[c] : 0;
+      const int32_t cnt = cell_ok ? a.cell_start[c + 1] - beg : 0;
+      const bool valid = k < cnt;
+      const int32_t o = valid ? a.tmp[beg + k] : 0;
+      const int32_t myid = valid ? a.id0[o] : INT_MAX;
+      const uint64_t mykey = valid ? member_key(a, o, myid) : ~0ull;
+      const int mych = (valid && a.qf0[o] != 0.0f) ? 1 : 0;
+      int rank = 0, crank = 0;
+      for (int t = 0; t < mx; ++t) {
+        const uint64_t x = __shfl_sync(FULL, mykey, t, W);
+        const int xc = __shfl_sync(FULL, mych, t, W);
+        if (x < mykey) { ++rank; crank += xc; }
+      }
+      if (valid) move_particle(a, o, beg + rank, myid, mych != 0, a.ccell_start[c] + crank);
     }
-    if (valid) move_particle(a, o, beg + rank, myid, mych != 0, a.ccell_start[c] + crank);
     return;
   }
   for (int q = 0; q < kCellsPerWarp; ++q) {
