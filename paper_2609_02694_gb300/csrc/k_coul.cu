@@ -179,14 +179,19 @@ __device__ __forceinline__ void coul_body(const CoulArgs a, int bx, int) {
       }
     };
     int nb = 0;  // buffered hits (warp-uniform)
-    int sg = 0;
+    const int nseg = 2 * nrows;
     for (int base = 0; base < T; base += 32) {
       const int cc = base + lane;
-      int s = sg;
       bool hit = false;
       int4 rec = make_int4(0, 0, 0, 0);
       if (cc < T) {
-        while (seg_pre[wid][s + 1] <= cc) ++s;
+        // candidate cc's run: the last of the (possibly empty) runs starting at or before cc,
+        // by a binary search over the run offsets (the same steps on every lane)
+        int s = 0, hi = nseg;
+        while (hi - s > 1) {
+          const int mid = (s + hi) >> 1;
+          if (seg_pre[wid][mid] <= cc) s = mid; else hi = mid;
+        }
         const int64_t j = seg_beg[wid][s] + (cc - seg_pre[wid][s]);
         if (j != i) {
           const uint4 pj = a.s4[j];
@@ -203,7 +208,6 @@ __device__ __forceinline__ void coul_body(const CoulArgs a, int bx, int) {
           rec = make_int4(dsx, dsy, dsz, F64 ? (int)j : (int)pj.w);
         }
       }
-      sg = __shfl_sync(FULL, s, 31);
       const unsigned hm = __ballot_sync(FULL, hit);
       if (hit) buf[wid][nb + __popc(hm & ((1u << lane) - 1u))] = rec;
       nb += __popc(hm);
