@@ -367,7 +367,7 @@ cudaError_t launch_bin_sort(Ctx &c) {
     a.ty0 = c.type[b0]; a.ty1 = c.type[b1];
     a.im0 = c.invm[b0]; a.im1 = c.invm[b1];
     a.cs = c.cs; a.cqf = c.cqf; a.cqd = c.cqd; a.cmap = c.cmap;
-    a.s4 = c.vl_on ? c.s4 : c.cp4;  // list gathers, or the cluster kernel's j loads
+    a.s4 = c.vl_on ? c.s4 : nullptr;  // the list gathers
     a.cs4 = c.vl_on ? c.cs4 : c.cq4;  // list gathers, or the Coulomb pass
     a.gate = gate;
     const int64_t threads = (nc + kCellsPerWarp - 1) / kCellsPerWarp * 32;

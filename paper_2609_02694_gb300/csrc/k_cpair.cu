@@ -25,7 +25,11 @@
 // floating point. Energies and virials are per-block partial sums, as in the other kernels.
 //
 // Frame. A super-cluster's coordinates are the exact integer offsets of its particles from
-// the centre of its bounding box, converted to FP32 (kept as integers in the FP64 form).
+// the centre of its bounding box, converted to FP32 (kept as integers in the FP64 form). A
+// visited j particle's x is converted the same way; its y and z are the frame coordinates of
+// its cluster's box corner plus its FP32 offsets from that corner, stored per step in the
+// cluster's eight record slots (a cluster lies in one cell in y and z, so the offsets are
+// small and never wrap; the one extra rounding widens the band below).
 // The difference of two offsets is the minimum-image displacement of a pair within r_c as
 // long as the super-cluster's extent plus 2 r_c stays below L on every axis: the host
 // checks y and z (a cell width), the kernel splits a super-cluster whose x extent is
@@ -54,7 +58,8 @@ struct ClusterArgs {
   const int32_t *cl_base;      // nrows + 1: first global cluster of each row
   const int32_t *sc_base;      // nrows + 1: first super-cluster of each row
   const uint4 *cl_lo, *cl_hi;  // per cluster: (min s_x, s_y, s_z, first particle), (max..., count)
-  const uint4 *s4;             // FP32 forms: packed (s_x, s_y, s_z, q bits) of every particle
+  const uint4 *jrec;           // FP32 forms: 8 slots per cluster (s_x, y and z offsets from the
+                               // box corner as FP32 bits, q bits); empty slots y = -3e18
   int nrows;
   long long *facc;             // 3 x N fixed-point forces (x block, y, z)
   int64_t N;
@@ -79,11 +84,14 @@ struct RowsArgs {
 };
 struct BoundsArgs {
   const uint32_t *sx, *sy, *sz;
+  const float *qf;
   const int32_t *cell_start;
   int n0, nrows;
   const int32_t *cl_base;
   int64_t cap;
   uint4 *lo, *hi;
+  uint4 *jrec;                 // nullable (FP64 form)
+  float hy, hz;                // length of one fractional unit in y and z
 };
 struct FinishArgs {
   long long *facc;
@@ -157,30 +165,49 @@ __device__ __forceinline__ int row_of(const int32_t *__restrict__ base, int nrow
   return lo;
 }
 
-// Bounding box (integer fractional coordinates), first particle and count of every cluster.
+// Bounding box (integer fractional coordinates), first particle and count of every cluster,
+// and its j records: slot k holds particle k's s_x, its y and z offsets from the box's low
+// corner in length units (FP32 bits) and its charge bits; a slot past the cluster's count
+// holds y = -3e18, beyond the reach of any i particle. Eight threads per cluster, one per
+// slot, with the box reduced over the eight by shuffles.
+static_assert(kClSize == 8, "eight threads per cluster");
 __device__ __forceinline__ void cluster_bounds_body(const BoundsArgs &a, int bx, int) {
-  const uint32_t *__restrict__ sx = a.sx;
-  const uint32_t *__restrict__ sy = a.sy;
-  const uint32_t *__restrict__ sz = a.sz;
   const int32_t *__restrict__ cell_start = a.cell_start;
   const int32_t *__restrict__ cl_base = a.cl_base;
   const int n0 = a.n0, nrows = a.nrows;
-  const int64_t cap = a.cap;
-  const int64_t g = (int64_t)bx * blockDim.x + threadIdx.x;
-  if (g >= cap || g >= cl_base[nrows]) return;
+  const int64_t t = (int64_t)bx * blockDim.x + threadIdx.x;
+  const int64_t g = t >> 3;
+  const int k = (int)(t & 7);
+  // (the same for the eight threads of a cluster, which exit together)
+  if (g >= a.cap || g >= cl_base[nrows]) return;
+  const unsigned gm = 0xffu << (threadIdx.x & 24);
   const int r = row_of(cl_base, nrows, (int)g);
   const int ps = cell_start[(int64_t)r * n0], pe = cell_start[(int64_t)(r + 1) * n0];
   const int b = ps + (int)(g - cl_base[r]) * kClSize;
   const int n = min(kClSize, pe - b);
-  uint32_t x0 = 0xffffffffu, y0 = 0xffffffffu, z0 = 0xffffffffu, x1 = 0u, y1 = 0u, z1 = 0u;
-  for (int k = 0; k < n; ++k) {
-    const uint32_t x = sx[b + k], y = sy[b + k], z = sz[b + k];
-    x0 = min(x0, x); x1 = max(x1, x);
-    y0 = min(y0, y); y1 = max(y1, y);
-    z0 = min(z0, z); z1 = max(z1, z);
+  const bool v = k < n;
+  uint32_t x = 0u, y = 0u, z = 0u;
+  float q = 0.f;
+  if (v) {
+    x = a.sx[b + k]; y = a.sy[b + k]; z = a.sz[b + k];
+    q = a.qf[b + k];
   }
-  a.lo[g] = make_uint4(x0, y0, z0, (uint32_t)b);
-  a.hi[g] = make_uint4(x1, y1, z1, (uint32_t)n);
+  uint32_t x0 = v ? x : 0xffffffffu, y0 = v ? y : 0xffffffffu, z0 = v ? z : 0xffffffffu;
+  uint32_t x1 = x, y1 = y, z1 = z;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    x0 = min(x0, __shfl_xor_sync(gm, x0, o)); x1 = max(x1, __shfl_xor_sync(gm, x1, o));
+    y0 = min(y0, __shfl_xor_sync(gm, y0, o)); y1 = max(y1, __shfl_xor_sync(gm, y1, o));
+    z0 = min(z0, __shfl_xor_sync(gm, z0, o)); z1 = max(z1, __shfl_xor_sync(gm, z1, o));
+  }
+  if (k == 0) {
+    a.lo[g] = make_uint4(x0, y0, z0, (uint32_t)b);
+    a.hi[g] = make_uint4(x1, y1, z1, (uint32_t)n);
+  }
+  if (a.jrec)
+    a.jrec[t] = v ? make_uint4(x, __float_as_uint((float)(int)(y - y0) * a.hy),
+                               __float_as_uint((float)(int)(z - z0) * a.hz), __float_as_uint(q))
+                  : make_uint4(0u, __float_as_uint(-3e18f), 0u, 0u);
 }
 RBE_BATCHED_KERNEL(__launch_bounds__(256), cluster_bounds_kernel, BoundsArgs, cluster_bounds_body)
 
@@ -534,6 +561,7 @@ __device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
         const int cc = base + lane;
         int s = sg, J = 0, jb = 0, jn = 0;
         uint32_t msk = 0u;
+        float jy0 = 0.f, jz0 = 0.f;  // the candidate box's low corner in y and z (frame)
         if (cc < T) {
           while (seg_pre[s + 1] <= cc) ++s;
           J = seg_beg[s] + (cc - seg_pre[s]);
@@ -541,8 +569,8 @@ __device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
           jb = (int)l.w;
           jn = (int)u.w;
           const float jx0 = (float)(int)(l.x - rx) * pc.h[0];
-          const float jy0 = (float)(int)(l.y - ry) * pc.h[1];
-          const float jz0 = (float)(int)(l.z - rz) * pc.h[2];
+          jy0 = (float)(int)(l.y - ry) * pc.h[1];
+          jz0 = (float)(int)(l.z - rz) * pc.h[2];
           const float jx1 = (float)(int)(u.x - rx) * pc.h[0];
           const float jy1 = (float)(int)(u.y - ry) * pc.h[1];
           const float jz1 = (float)(int)(u.z - rz) * pc.h[2];
@@ -571,9 +599,12 @@ __device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
           const int Jv = __shfl_sync(FULL, J, t0);
           const uint32_t M = __shfl_sync(FULL, msk, t0);
           const int vb = __shfl_sync(FULL, jb, t0), vn = __shfl_sync(FULL, jn, t0);
+          const float cyj = F64 ? 0.f : __shfl_sync(FULL, jy0, t0);
+          const float czj = F64 ? 0.f : __shfl_sync(FULL, jz0, t0);
           const int cdiag = Jv - g0;  // the visited cluster's place in the super-cluster
-          // This lane's j particles, h and h + 4 of the cluster: exact integer offsets from the
-          // frame centre, converted to FP32 (kept as integers in the FP64 form).
+          // This lane's j particles, h and h + 4 of the cluster: x from the exact integer
+          // offset from the frame centre, y and z from the cluster's corner plus the record's
+          // offsets, in FP32 (exact integer offsets in the FP64 form).
           real xj[2], yj[2], zj[2], qj[2], fxj[2], fyj[2], fzj[2];
           int oxj[2], oyj[2], ozj[2], tj[2], cntj[2];
           bool vj[2];
@@ -585,10 +616,11 @@ __device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
             oxj[k] = oyj[k] = ozj[k] = 0;
             qj[k] = (real)0;
             if (!F64) {
-              const uint4 pj = __ldg(&a.s4[p]);
-              xj[k] = vj[k] ? (real)((float)(int)(pj.x - rx) * pc.h[0]) : (real)-3e18f;
-              yj[k] = vj[k] ? (real)((float)(int)(pj.y - ry) * pc.h[1]) : (real)-3e18f;
-              zj[k] = vj[k] ? (real)((float)(int)(pj.z - rz) * pc.h[2]) : (real)-3e18f;
+              // (an empty slot's y of -3e18 puts it out of reach)
+              const uint4 pj = __ldg(&a.jrec[((int64_t)Jv << 3) + t]);
+              xj[k] = (real)((float)(int)(pj.x - rx) * pc.h[0]);
+              yj[k] = (real)(cyj + __uint_as_float(pj.y));
+              zj[k] = (real)(czj + __uint_as_float(pj.z));
               if (COUL) qj[k] = (real)__uint_as_float(pj.w);
             } else {
               oxj[k] = (int)(a.set.sx[p] - rx);
@@ -873,9 +905,10 @@ cudaError_t launch_cluster_tables(Ctx &c) {
                            ra);
   if (e != cudaSuccess) return e;
   const int64_t ccap = cpair_clusters_bound(c);
-  const BoundsArgs ba{c.s[b], c.s[b] + c.N, c.s[b] + 2 * c.N, c.cell_start, c.grid.n[0], nrows,
-                      c.cl_base, ccap, c.cl_lo, c.cl_hi};
-  return dispatch(c, cluster_bounds_kernel, cluster_bounds_kernel_b, dim3((unsigned)((ccap + 255) / 256)), dim3(256), 0, ba);
+  const BoundsArgs ba{c.s[b], c.s[b] + c.N, c.s[b] + 2 * c.N, c.qf[b], c.cell_start, c.grid.n[0],
+                      nrows, c.cl_base, ccap, c.cl_lo, c.cl_hi, c.cjrec, c.pc.h[1], c.pc.h[2]};
+  return dispatch(c, cluster_bounds_kernel, cluster_bounds_kernel_b,
+                  dim3((unsigned)((kClSize * ccap + 255) / 256)), dim3(256), 0, ba);
 }
 
 // The pair pass itself (the tables of launch_cluster_tables must be current), then the
@@ -893,7 +926,7 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
   a.ljAd = c.lj.Ad[0]; a.ljBd = c.lj.Bd[0]; a.ljA12d = c.lj.A12d[0]; a.ljB6d = c.lj.B6d[0];
   a.table = reinterpret_cast<const LJTable *>(c.lj_dev);
   a.cl_base = c.cl_base; a.sc_base = c.sc_base; a.cl_lo = c.cl_lo; a.cl_hi = c.cl_hi;
-  a.s4 = c.cp4;
+  a.jrec = c.cjrec;
   a.nrows = nrows;
   a.facc = c.facc;
   a.N = c.N;
@@ -906,9 +939,13 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
     // x extent of a group: (extent + 2 r_c) < L, in fractional units, with margin
     const double lim = (c.box[0] - 2.0 * c.rc) / c.box[0] * kTwo32 * (1.0 - 1e-7) - 16.0;
     a.xlim = (uint32_t)std::max(0.0, std::min(lim, 4294967295.0));
-    // frame coordinates within L/2 on every axis: the exact-decision band for that extent
+    // frame coordinates within L/2 on every axis: the exact-decision band for that extent.
+    // A j particle's y and z add one more rounding (corner plus offset: within 3u |y| + 4u w
+    // for a cell width w, against the 2u |y| the band assumes per coordinate); extents
+    // raised by 2 r_c + 2 w cover it, as |y| <= L/2.
     double X[3];
     for (int d = 0; d < 3; ++d) X[d] = 0.5 * c.box[d];
+    for (int d = 1; d < 3; ++d) X[d] += 2.0 * c.rc + 2.0 * c.box[d] / c.grid.n[d];
     const double band = frame_band(X, c.rc, c.box, false);
     a.pc.rc2_lo = (float)(c.rc * c.rc * (1.0 - band));
     a.pc.rc2_hi = (float)(c.rc * c.rc * (1.0 + band));

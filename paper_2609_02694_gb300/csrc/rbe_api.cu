@@ -121,7 +121,7 @@ int free_all(Ctx &c) {
     c.graph[b] = nullptr;
   }
   dfree(c.F); dfree(c.Fd); dfree(c.facc); dfree(c.cl_base); dfree(c.sc_base); dfree(c.cl_lo);
-  dfree(c.cl_hi); dfree(c.cp4); dfree(c.cq4); dfree(c.cs); dfree(c.cqf); dfree(c.cqd); dfree(c.cmap);
+  dfree(c.cl_hi); dfree(c.cjrec); dfree(c.cq4); dfree(c.cs); dfree(c.cqf); dfree(c.cqd); dfree(c.cmap);
   dfree(c.cell_count); dfree(c.cell_start); dfree(c.key); dfree(c.off); dfree(c.tmp);
   dfree(c.scan_blk);
   for (int d = 0; d < 3; ++d) dfree(c.T[d]);
@@ -473,7 +473,7 @@ int rbe_init(rbe_handle *hout, const rbe_params *p, int64_t N, const double box[
     rc |= dalloc(c, &c.sc_base, nrows + 1);
     rc |= dalloc(c, &c.cl_lo, cpair_clusters_bound(c));
     rc |= dalloc(c, &c.cl_hi, cpair_clusters_bound(c));
-    if (!fp64) rc |= dalloc(c, &c.cp4, N);
+    if (!fp64) rc |= dalloc(c, &c.cjrec, 8 * cpair_clusters_bound(c));  // 8 slots per cluster
     rc |= dalloc(c, &c.cq4, Nq);
   }
   rc |= dalloc(c, &c.cs, 3 * Nq);

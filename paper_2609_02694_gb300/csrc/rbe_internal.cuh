@@ -111,8 +111,8 @@ struct Ctx {
   long long *facc = nullptr;
   int32_t *cl_base = nullptr, *sc_base = nullptr;
   uint4 *cl_lo = nullptr, *cl_hi = nullptr;
-  uint4 *cp4 = nullptr;        // packed (s_x, s_y, s_z, q bits), sorted order, written by the
-                               // binning for the cluster kernel's j loads (FP32 forms)
+  uint4 *cjrec = nullptr;      // the cluster kernel's j records, 8 slots per cluster, written
+                               // with the cluster boxes (FP32 forms)
   uint4 *cq4 = nullptr;        // the same for the charged subset (its Coulomb pass)
   // charged subset
   uint32_t *cs = nullptr;
