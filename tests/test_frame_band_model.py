@@ -88,6 +88,49 @@ def test_frame_r2_error_within_band_bound():
         assert obs <= band_bound(X, r, (L, L, L)), (label, obs)
 
 
+def observed_error_corner(L, X, w, r, n=300000, seed=1):
+    """As observed_error, with the cluster kernel's j coordinates: x converted from the
+    particle's own integer offset, y and z as the FP32 frame coordinate of its cluster's box
+    corner plus its FP32 offset from that corner (an integer within one cell width w),
+    added in FP32."""
+    rng = np.random.default_rng(seed)
+    hd = L / TWO32
+    h32 = np.float32(hd)
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    rr = r * (1 + 0.002 * (rng.random(n) - 0.5))
+    d = np.round(v * (rr / hd)[:, None]).astype(np.int64)
+    lim = (np.asarray(X) / hd).astype(np.int64)
+    di = np.stack([rng.integers(-lim[k], lim[k] + 1, n) for k in range(3)], 1)
+    dj = di - d
+    off = rng.integers(0, int(w / hd) + 1, size=(n, 3))
+    off[:, 0] = 0
+    corner = dj - off
+    keep = (np.abs(dj) <= lim).all(1) & (np.abs(corner) <= lim).all(1)
+    di, dj, off, corner = di[keep], dj[keep], off[keep], corner[keep]
+    xi = di.astype(np.float32) * h32
+    xj = dj.astype(np.float32) * h32
+    yz = corner[:, 1:].astype(np.float32) * h32 + off[:, 1:].astype(np.float32) * h32
+    xj[:, 1:] = yz                    # corner + offset, one more FP32 rounding
+    dd = xi - xj
+    z2 = (dd[:, 2].astype(np.float64) ** 2).astype(np.float32)
+    r2 = _fma_f32(dd[:, 0], dd[:, 0], _fma_f32(dd[:, 1], dd[:, 1], z2)).astype(np.float64)
+    ex = (di - dj) * hd
+    return (np.abs(r2 - (ex * ex).sum(1)) / (r * r)).max()
+
+
+def test_cluster_corner_offsets_within_widened_band():
+    """The cluster kernel's band takes X = L/2 on every axis, raised by 2 r_c + 2 w in y and
+    z for the corner-plus-offset j coordinates; the observed error stays within that bound,
+    in the 1,048,576-particle box and in the tightest box the kernel takes (w + 2 r_c just
+    below L)."""
+    for L, w, r in ((218.877, 218.877 / 43, 10.0), (26.0, 5.2, 10.0), (551.535, 551.535 / 110, 10.0)):
+        X = (L / 2, L / 2, L / 2)
+        obs = observed_error_corner(L, X, w, r)
+        Xb = (L / 2, L / 2 + 2 * r + 2 * w, L / 2 + 2 * r + 2 * w)
+        assert obs <= band_bound(Xb, r, (L, L, L)), (L, obs)
+
+
 def test_fixed_band_too_narrow_for_half_box_groups():
     """A group spanning half of a 1103 A box (the 2^27-particle system): the FP32 error
     exceeds a fixed 1e-5 band, so the band must follow the bound."""
