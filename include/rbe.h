@@ -196,12 +196,16 @@ enum {
   RBE_PH_PAIR = 5,       /* main real-space kernel (cell list or Verlet list LJ[+Coulomb], or RBL) */
   RBE_PH_PAIR2 = 6,      /* charged-subset Coulomb pass, or the RBL mean-force correction */
   RBE_PH_GATHER = 7,     /* k-space force gather */
-  RBE_PH_TAIL = 8,       /* second half-kick, kinetic energy and totals */
+  RBE_PH_TAIL = 8,       /* second half-kick, kinetic energy and totals (with the cluster
+                            kernel, first its fixed-point finish) */
   RBE_N_PHASE = 9
 };
 
 /* Turn per-phase event timing on or off (off by default). Toggling it discards the
- * captured step graph, which is captured again on the next rbe_step. */
+ * captured step graph, which is captured again on the next rbe_step. With timing on, a step
+ * runs its phases one after another; with it off, the captured step of the cluster-pair
+ * kernel runs the k-space chain and the charged subset's Coulomb pass as a second graph
+ * branch beside the pair pass (the same forces and energies bit for bit). */
 int rbe_set_profiling(rbe_handle h, int enable);
 
 /* Per-phase device times (ms, RBE_N_PHASE doubles) of the most recent force evaluation

@@ -16,9 +16,11 @@
 //     form). Hits are compacted (ballot) into a small per-warp buffer in shared memory.
 //  3. Evaluate: whenever 32 hits are buffered (and once at the end) every lane evaluates one
 //     of them (erfc, exp and a reciprocal square root), so the expensive terms run on full
-//     warps. A warp sum gives F_i, added to the force of i's slot in the full set.
-// Each pair is evaluated from both sides with no atomics, so the forces are reproducible run
-// to run; the energy and virial partials take half of the per-i sums.
+//     warps. A warp sum gives F_i, added to the force of i's slot in the full set: to F after
+//     a pass that wrote F, or to the cluster kernel's 64-bit fixed-point sums (three integer
+//     atomics per particle, whose sums do not depend on their order).
+// Each pair is evaluated from both sides, so the forces are reproducible run to run; the
+// energy and virial partials take half of the per-i sums.
 #include <climits>
 #include <cmath>
 
@@ -44,6 +46,10 @@ struct CoulArgs {
   double *epart;              // per-block partials (NQ_PAIR doubles)
   int comp;                   // Kahan-compensated energy and virial sums
   float reach2;               // r_c^2 widened: rows and cells farther than this are skipped
+  long long *facc;            // nullable: 3 x N fixed-point force sums of the full set (then
+  float fscale;               //   F is not written), their scale (FP32 forms)
+  double fscale_d;            //   (FP64 form)
+  int *err;                   //   (a sum out of range sets ERRBIT_NONFINITE)
 };
 
 int64_t coul_blocks(int64_t nq) { return (nq + kCoulWarps - 1) / kCoulWarps; }
@@ -223,11 +229,20 @@ __device__ __forceinline__ void coul_body(const CoulArgs a, int bx, int) {
     }
     evaluate(nb);
     fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-    if (lane == 0) {
+    if (a.facc) {  // one component per lane (every lane holds the sums)
+      if (lane < 3) {
+        const real sc = F64 ? (real)a.fscale_d : (real)a.fscale;
+        fx_add_i32(a.facc + lane * a.Fstride + a.map[i], lane == 0 ? fx : (lane == 1 ? fy : fz),
+                   sc, a.err);
+      }
+    } else if (lane == 0) {
       const int64_t o = a.map[i];
       const int64_t S = a.Fstride;
-      if (F64) { a.Fd[o] += (double)fx; a.Fd[S + o] += (double)fy; a.Fd[2 * S + o] += (double)fz; }
-      else { a.F[o] += (float)fx; a.F[S + o] += (float)fy; a.F[2 * S + o] += (float)fz; }
+      if (F64) {
+        a.Fd[o] += (double)fx; a.Fd[S + o] += (double)fy; a.Fd[2 * S + o] += (double)fz;
+      } else {
+        a.F[o] += (float)fx; a.F[S + o] += (float)fy; a.F[2 * S + o] += (float)fz;
+      }
     }
   }
   // block partials of the Coulomb energy and virial (halves of the per-i sums)
@@ -252,7 +267,7 @@ __global__ void __launch_bounds__(kCoulWarps * 32, sizeof(real) == 8 ? 8 : 16)
 }
 
 
-cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4) {
+cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4, bool into_facc) {
   CoulArgs a;
   a.s4 = s4;
   a.qd = c.cqd;
@@ -266,6 +281,10 @@ cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4) {
   a.comp = c.precision == RBE_FP32_COMP;
   const double rr = c.rc * (1.0 + 1e-5) + 8.0 * std::ldexp(1.0, -24) * std::max(c.box[0], std::max(c.box[1], c.box[2]));
   a.reach2 = (float)(rr * rr);
+  a.facc = into_facc ? c.facc : nullptr;
+  a.fscale = (float)kFixScale32;
+  a.fscale_d = kFixScale64;
+  a.err = c.err;
   const dim3 g((unsigned)c.n_coul_blk), b(kCoulWarps * 32);  // every slot of the partial range
   // (per replica in a batch, like the other pair kernels)
   if (c.precision == RBE_FP64)

@@ -274,21 +274,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Add v * scale to a fixed-point sum (round to nearest); an out-of-range value sets the
-// non-finite flag instead (its sum would wrap).
-__device__ __forceinline__ void fx_add(long long *p, float v, float scale, int *err) {
-  const float s = v * scale;
-  if (fabsf(s) < 4.0e18f) atomicAdd(reinterpret_cast<unsigned long long *>(p),
-                                    (unsigned long long)__float2ll_rn(s));
-  else atomicOr(err, ERRBIT_NONFINITE);
-}
-__device__ __forceinline__ void fx_add(long long *p, double v, double scale, int *err) {
-  const double s = v * scale;
-  if (fabs(s) < 4.0e18) atomicAdd(reinterpret_cast<unsigned long long *>(p),
-                                  (unsigned long long)__double2ll_rn(s));
-  else atomicOr(err, ERRBIT_NONFINITE);
-}
-
 template <typename real>
 struct CpAcc {
   real u0, u1;   // single type: sum r^-12, sum r^-6; several types: U_LJ, W_LJ
@@ -911,8 +896,9 @@ cudaError_t launch_cluster_tables(Ctx &c) {
                   dim3((unsigned)((kClSize * ccap + 255) / 256)), dim3(256), 0, ba);
 }
 
-// The pair pass itself (the tables of launch_cluster_tables must be current), then the
-// fixed-point finish.
+// The pair pass itself (the tables of launch_cluster_tables must be current); its forces stay
+// in the fixed-point sums, which the Coulomb pass and the k-space gather add to before
+// launch_cluster_finish converts them.
 cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts) {
   const int b = c.cur;
   const int nrows = c.grid.n[1] * c.grid.n[2];
@@ -983,10 +969,15 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
     else { if (multi) RBE_CP_LAUNCH(float, false, true); else RBE_CP_LAUNCH(float, false, false); }
   }
 #undef RBE_CP_LAUNCH
-  if (e != cudaSuccess) return e;
+  return e;
+}
+
+// F = the fixed-point sums / scale, and the sums cleared for the next step.
+cudaError_t launch_cluster_finish(Ctx &c) {
+  const bool fp64 = c.precision == RBE_FP64;
   const int64_t n3 = 3 * c.N;
-  // (per replica in a batch too: it joins the pair kernel and the Coulomb pass in one run of
-  // per-replica launches, one fork and join per step instead of two)
+  // (per replica in a batch too: it joins the pair kernel, the Coulomb pass and the gather in
+  // one run of per-replica launches, one fork and join per step)
   const dim3 fg((unsigned)(((n3 + 3) / 4 + 255) / 256)), fb(256);
   if (fp64) {
     const FinishArgs f{c.facc, c.Fd, n3, 0.f, 0.f, 1.0 / kFixScale64};

@@ -54,6 +54,10 @@ struct GatherArgs {
   float *F;
   double *Fd;
   int64_t N;
+  long long *facc;         // nullable: add to these 3 x N fixed-point sums instead of F
+  float fscale;            // (their scale in the FP32 forms,
+  double fscale_d;         //  and in the FP64 form)
+  int *err;
 };
 
 // Solo and batched kernels of a body templated on MODE.
@@ -244,7 +248,19 @@ __device__ __forceinline__ void gather_body(const GatherArgs &a, int bx, int) {
   }
   if (!valid) return;
   const int64_t p = a.cmap[i];
-  if (MODE == 2) {
+  if (a.facc) {  // into the cluster kernel's fixed-point sums (integer atomics)
+    if (MODE == 2) {
+      const double q = a.cqd[i];
+      fx_add(a.facc + p, -q * dx, a.fscale_d, a.err);
+      fx_add(a.facc + N + p, -q * dy, a.fscale_d, a.err);
+      fx_add(a.facc + 2 * N + p, -q * dz, a.fscale_d, a.err);
+    } else {
+      const float q = a.cqf[i];
+      fx_add_i32(a.facc + p, -q * fx, a.fscale, a.err);
+      fx_add_i32(a.facc + N + p, -q * fy, a.fscale, a.err);
+      fx_add_i32(a.facc + 2 * N + p, -q * fz, a.fscale, a.err);
+    }
+  } else if (MODE == 2) {
     double *__restrict__ Fd = a.Fd;
     const double q = a.cqd[i];
     Fd[p] = mad(-q, dx, Fd[p]);
@@ -281,16 +297,18 @@ cudaError_t launch_structure_factor(Ctx &c) {
   }
 }
 
-cudaError_t launch_kspace_gather(Ctx &c) {
+cudaError_t launch_kspace_gather(Ctx &c, bool into_facc) {
   if (c.Nq == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((c.Nq + kGatherThreads - 1) / kGatherThreads);
   const GatherArgs a{c.cs, c.cqf, c.cqd, c.Nq, c.m, c.kcf, c.kcd, c.abf, c.abd, c.P, c.cmap,
-                     c.F, c.Fd, c.N};
+                     c.F, c.Fd, c.N, into_facc ? c.facc : nullptr, (float)kFixScale32,
+                     kFixScale64, c.err};
+  // (into the fixed-point sums it runs per replica in a batch, within the pair pass's run)
   if (c.precision == RBE_FP64)
     return dispatch(c, gather_kernel<2>, gather_kernel_b<2>, dim3(blocks), dim3(kGatherThreads),
-                    0, a);
+                    0, a, into_facc);
   return dispatch(c, gather_kernel<0>, gather_kernel_b<0>, dim3(blocks), dim3(kGatherThreads), 0,
-                  a);
+                  a, into_facc);
 }
 
 }  // namespace rbe

@@ -596,25 +596,31 @@ cudaError_t launch_pair(Ctx &c, bool want_counts) {
   }
   set_pretest_band(c, a, c.rc, wrap);
   const bool fp64 = c.precision == RBE_FP64;
-  if (cpair_usable(c)) {
-    // each pair once over clusters (k_cpair.cu); it writes F, the Coulomb pass adds to it
-    const cudaError_t e = launch_cluster_pair(c, fused, multi, want_counts);
+  if (fused) {
+    const cudaError_t e = fp64 ? launch_one<double, true, true>(c, a, c.N, multi, wrap)
+                               : launch_one<float, true, true>(c, a, c.N, multi, wrap);
     if (e != cudaSuccess) return e;
   } else {
-    if (fused) {
-      const cudaError_t e = fp64 ? launch_one<double, true, true>(c, a, c.N, multi, wrap)
-                                 : launch_one<float, true, true>(c, a, c.N, multi, wrap);
-      if (e != cudaSuccess) return e;
-    } else {
-      const cudaError_t e = fp64 ? launch_one<double, true, false>(c, a, c.N, multi, wrap)
-                                 : launch_one<float, true, false>(c, a, c.N, multi, wrap);
-      if (e != cudaSuccess) return e;
-    }
-    zero_partials_tail(c, c.off_pair, pair_blocks(c.N), c.n_pair_blk);
+    const cudaError_t e = fp64 ? launch_one<double, true, false>(c, a, c.N, multi, wrap)
+                               : launch_one<float, true, false>(c, a, c.N, multi, wrap);
+    if (e != cudaSuccess) return e;
   }
+  zero_partials_tail(c, c.off_pair, pair_blocks(c.N), c.n_pair_blk);
   mark(c, RBE_PH_PAIR2);
   // the charged subset's Coulomb pass (k_coul.cu), added to the forces the main pass wrote
-  if (!fused && c.Nq > 0) return launch_coulomb_subset(c, c.cq4);
+  if (!fused && c.Nq > 0) return launch_coulomb_subset(c, c.cq4, false);
+  return cudaGetLastError();
+}
+
+// The cluster kernel's pass (k_cpair.cu): each pair once, into the 64-bit fixed-point sums;
+// then, when most particles carry no charge, the charged subset's Coulomb pass into the same
+// sums. The k-space gather adds to them too, and launch_cluster_finish turns them into F.
+cudaError_t launch_pair_cluster(Ctx &c, bool want_counts) {
+  const bool fused = c.Nq * 2 > c.N;
+  cudaError_t e = launch_cluster_pair(c, fused, c.nt > 1, want_counts);
+  if (e != cudaSuccess) return e;
+  mark(c, RBE_PH_PAIR2);
+  if (!fused && c.Nq > 0) return launch_coulomb_subset(c, c.cq4, true);
   return cudaGetLastError();
 }
 

@@ -185,6 +185,8 @@ struct Ctx {
   // graph
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per starting buffer parity
   cudaStream_t cap_stream = nullptr;  // internal non-blocking stream used only for capture
+  cudaStream_t aux_stream = nullptr;  // second capture stream: the k-space branch of a step
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // (fork and join of that branch)
   // profiling: ev[k] is recorded before phase k, ev[RBE_N_PHASE] after the last one
   bool timing = false;
   cudaEvent_t ev[RBE_N_PHASE + 1] = {};
@@ -229,6 +231,44 @@ __device__ __forceinline__ float phase_to_radians(uint32_t ph) {
 
 __device__ __forceinline__ double phase_to_radians_d(uint32_t ph) {
   return (double)(int)ph * (2.0 * kPi / kTwo32);
+}
+
+// Add v * scale to a 64-bit fixed-point force sum (round to nearest); an out-of-range value
+// sets the non-finite flag instead (its sum would wrap). Integer sums do not depend on the
+// order of their terms, so passes that add to the same sums may run in any order.
+__device__ __forceinline__ void fx_add(long long *p, float v, float scale, int *err) {
+  const float s = v * scale;
+  if (fabsf(s) < 4.0e18f) atomicAdd(reinterpret_cast<unsigned long long *>(p),
+                                    (unsigned long long)__float2ll_rn(s));
+  else atomicOr(err, ERRBIT_NONFINITE);
+}
+__device__ __forceinline__ void fx_add(long long *p, double v, double scale, int *err) {
+  const double s = v * scale;
+  if (fabs(s) < 4.0e18) atomicAdd(reinterpret_cast<unsigned long long *>(p),
+                                  (unsigned long long)__double2ll_rn(s));
+  else atomicOr(err, ERRBIT_NONFINITE);
+}
+// The same sum for an FP32 v, with the integer nearest s = v * scale built from 32-bit
+// conversions: a 64-bit conversion issues to the FP64 pipe, at 1/64 of the FP32 rate, which
+// matters in a pass that keeps that pipe busy. |s| < 2^31 converts directly. A larger s is
+// an integer (its ulp is at least 2^8) and splits exactly into s = h 2^32 + l with
+// h = floor(s 2^-32) and l = s - h 2^32 in [0, 2^32): l is a multiple of s's ulp below 2^32,
+// so it has at most 24 significant bits and the FP32 subtraction is exact. The result equals
+// the 64-bit conversion's for every |s| < 4e18.
+__device__ __forceinline__ void fx_add_i32(long long *p, float v, float scale, int *err) {
+  const float s = v * scale;
+  if (fabsf(s) < 4.0e18f) {
+    const float h = floorf(s * 2.3283064365386963e-10f);
+    const unsigned l = __float2uint_rn(s - h * 4294967296.0f);
+    const unsigned long long big = ((unsigned long long)(unsigned)__float2int_rn(h) << 32) | l;
+    const unsigned long long small = (unsigned long long)(long long)__float2int_rn(s);
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), fabsf(s) < 2147483648.0f ? small : big);
+  } else {
+    atomicOr(err, ERRBIT_NONFINITE);
+  }
+}
+__device__ __forceinline__ void fx_add_i32(long long *p, double v, double scale, int *err) {
+  fx_add(p, v, scale, err);
 }
 
 // Fused multiply-add a * b + c (one rounding) in either precision. The library is compiled
@@ -351,8 +391,8 @@ cudaError_t fill_zero(Ctx &c, void *p, int64_t words);
 cudaError_t launch_sample_k(Ctx &c);
 cudaError_t launch_bin_sort(Ctx &c);
 cudaError_t launch_structure_factor(Ctx &c);
-cudaError_t launch_kspace_gather(Ctx &c);
-cudaError_t launch_pair(Ctx &c, bool want_counts);   // main pass, then mark, then Coulomb pass
+cudaError_t launch_kspace_gather(Ctx &c, bool into_facc);
+cudaError_t launch_pair(Ctx &c, bool want_counts);   // per-particle pass, then mark, then Coulomb pass
 // Cluster-pair kernel (k_cpair.cu): whether it applies to the handle's box and tuning, the
 // launch bounds of its super-clusters and clusters, and the launch (tables, pairs, finish).
 bool cpair_usable(const Ctx &c);
@@ -360,10 +400,12 @@ int64_t cpair_blocks_bound(const Ctx &c);
 int64_t cpair_clusters_bound(const Ctx &c);
 cudaError_t launch_cluster_tables(Ctx &c);  // per-row offsets and per-cluster bounds
 cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts);
+cudaError_t launch_cluster_finish(Ctx &c);
+cudaError_t launch_pair_cluster(Ctx &c, bool want_counts);
 // Coulomb pass over the charged subset (k_coul.cu): one warp per charged particle; its grid
 // (the partial slots of the pass) for nq charged particles.
 int64_t coul_blocks(int64_t nq);
-cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4);
+cudaError_t launch_coulomb_subset(Ctx &c, const uint4 *s4, bool into_facc);
 void mark(Ctx &c, int k);  // record the profiling event k (no-op when profiling is off)
 cudaError_t launch_rbl(Ctx &c, bool want_debug);
 cudaError_t launch_list_check(Ctx &c);    // rebuild flag from the displacements

@@ -186,3 +186,28 @@ def test_switching_passes_keeps_energies(orc):
     ref = orc.total_forces(sy.s, sy.q, sy.types, sy.box, ALPHA, RC, C, sy.eps, sy.sig, m, S)
     assert E1["lj"] == pytest.approx(ref["U_lj"], rel=2e-6)
     assert E1["real"] == pytest.approx(ref["U_real"], rel=1e-5)
+
+
+@pytest.mark.parametrize("precision,frac", [("fp32_comp", 0.1), ("fp64", 0.1), ("fp32_comp", 0.8)])
+def test_two_branch_step_graph_equals_sequential(precision, frac):
+    """With profiling off, a captured step of the cluster kernel runs the k-space chain and the
+    charged subset's Coulomb pass as a second graph branch beside the pair pass, all adding to
+    the same integer fixed-point sums; with profiling on, the phases run one after another.
+    Both give the same state and energies bit for bit after several steps (frac 0.8: the
+    fused LJ + Coulomb pass, with only the k-space chain beside it)."""
+    sy = synth.make_system(15000, density=0.1, frac_charged=frac, seed=43)
+    out = []
+    for prof in (False, True):
+        with binding.from_system(sy, P=64, alpha=ALPHA, r_c=RC, coulomb_C=C, dt=1.0,
+                                 kappa=synth.ACCEL_KAPPA, precision=precision, seed=9) as h:
+            h.set_tuning("pair_cluster", 1)
+            h.set_profiling(prof)
+            h.step(6)
+            s, v, _ = h.state()
+            out.append((s, v, h.energies()))
+            if prof:
+                ph = h.profile()[0]
+                assert ph["pair"] > 0 and ph["tail"] > 0  # (the tail holds the finish)
+    (s0, v0, e0), (s1, v1, e1) = out
+    assert np.array_equal(s0, s1) and np.array_equal(v0, v1)
+    assert e0 == e1
