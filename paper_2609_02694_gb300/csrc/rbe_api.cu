@@ -119,6 +119,8 @@ int free_all(Ctx &c) {
     dfree(c.qd[b]); dfree(c.type[b]); dfree(c.invm[b]);
     if (c.graph[b]) cudaGraphExecDestroy(c.graph[b]);
     c.graph[b] = nullptr;
+    if (c.fgraph[b]) cudaGraphExecDestroy(c.fgraph[b]);
+    c.fgraph[b] = nullptr;
   }
   dfree(c.F); dfree(c.Fd); dfree(c.facc); dfree(c.cl_base); dfree(c.sc_base); dfree(c.cl_lo);
   dfree(c.cl_hi); dfree(c.cjrec); dfree(c.cq4); dfree(c.cs); dfree(c.cqf); dfree(c.cqd); dfree(c.cmap);
@@ -264,7 +266,9 @@ int copy_scalars(Ctx &c, double *energies, double *virial) {
 
 // Capture one Verlet step into a graph. Capture runs on an internal non-blocking stream
 // (the legacy default stream cannot be captured); the graph is replayed on c.stream.
-int capture_step_graph(Ctx &c, int parity, cudaGraphExec_t *out) {
+// One Verlet step (or, forces_only, one force evaluation with the kinetic energy and the
+// totals, as rbe_forces runs it) captured from buffer parity `parity`.
+int capture_step_graph(Ctx &c, int parity, cudaGraphExec_t *out, bool forces_only = false) {
   if (!c.cap_stream) RBE_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
   if (!c.aux_stream) RBE_CUDA_TRY(cudaStreamCreateWithFlags(&c.aux_stream, cudaStreamNonBlocking));
   if (!c.ev_fork) RBE_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
@@ -282,6 +286,13 @@ int capture_step_graph(Ctx &c, int parity, cudaGraphExec_t *out) {
   }
   int rc = RBE_OK;
   do {
+    if (forces_only) {  // (the step number is set on the device before each launch)
+      rc = force_pipeline(c, false);
+      if (rc != RBE_OK) break;
+      if (launch_kinetic(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      if (launch_totals(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }
+      break;
+    }
     mark(c, RBE_PH_KICK_DRIFT);
     if (launch_kick_drift(c) != cudaSuccess) { rc = RBE_ERR_CUDA; break; }  // + step counter
     rc = force_pipeline(c, false);
@@ -668,6 +679,17 @@ int rbe_set_positions(rbe_handle h, const double *pos, int on_device) {
 static int forces_common(rbe_handle h, uint64_t step, bool debug) {
   Ctx &c = *h;
   RBE_CUDA_TRY(launch_set_step(c, step));
+  if (!debug && !c.timing) {
+    // replay a captured evaluation (one graph per buffer parity, as for rbe_step)
+    if (!c.fgraph[c.cur]) {
+      const int rc = capture_step_graph(c, c.cur, &c.fgraph[c.cur], true);
+      if (rc != RBE_OK) return rc;
+    }
+    RBE_CUDA_TRY(cudaGraphLaunch(c.fgraph[c.cur], c.stream));
+    c.cur = 1 - c.cur;
+    c.have_forces = (step == c.step);
+    return RBE_OK;
+  }
   mark(c, RBE_PH_KICK_DRIFT);
   int rc = force_pipeline(c, debug);
   if (rc != RBE_OK) return rc;
@@ -927,11 +949,16 @@ int rbe_get_profile(rbe_handle h, double *phase_ms, int64_t *kps) {
 }
 
 static void drop_graphs(Ctx &c) {
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
     if (c.graph[b]) {
       cudaGraphExecDestroy(c.graph[b]);
       c.graph[b] = nullptr;
     }
+    if (c.fgraph[b]) {
+      cudaGraphExecDestroy(c.fgraph[b]);
+      c.fgraph[b] = nullptr;
+    }
+  }
 }
 
 // Structure-factor launch shape for a tile of `tile` particles per block.

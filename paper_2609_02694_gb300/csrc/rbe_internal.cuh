@@ -184,6 +184,7 @@ struct Ctx {
   struct Recorder *rec = nullptr;
   // graph
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per starting buffer parity
+  cudaGraphExec_t fgraph[2] = {nullptr, nullptr}; // force evaluations (rbe_forces), the same
   cudaStream_t cap_stream = nullptr;  // internal non-blocking stream used only for capture
   cudaStream_t aux_stream = nullptr;  // second capture stream: the k-space branch of a step
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // (fork and join of that branch)

@@ -193,8 +193,9 @@ def test_two_branch_step_graph_equals_sequential(precision, frac):
     """With profiling off, a captured step of the cluster kernel runs the k-space chain and the
     charged subset's Coulomb pass as a second graph branch beside the pair pass, all adding to
     the same integer fixed-point sums; with profiling on, the phases run one after another.
-    Both give the same state and energies bit for bit after several steps (frac 0.8: the
-    fused LJ + Coulomb pass, with only the k-space chain beside it)."""
+    Both give the same state and energies bit for bit after several steps, and so do a
+    captured and an uncaptured force evaluation (frac 0.8: the fused LJ + Coulomb pass, with
+    only the k-space chain beside it)."""
     sy = synth.make_system(15000, density=0.1, frac_charged=frac, seed=43)
     out = []
     for prof in (False, True):
@@ -202,12 +203,14 @@ def test_two_branch_step_graph_equals_sequential(precision, frac):
                                  kappa=synth.ACCEL_KAPPA, precision=precision, seed=9) as h:
             h.set_tuning("pair_cluster", 1)
             h.set_profiling(prof)
+            F0, E0, W0 = h.forces(0)  # a force evaluation alone (a captured one, unprofiled)
             h.step(6)
             s, v, _ = h.state()
-            out.append((s, v, h.energies()))
+            out.append((s, v, h.energies(), F0, E0, W0))
             if prof:
                 ph = h.profile()[0]
                 assert ph["pair"] > 0 and ph["tail"] > 0  # (the tail holds the finish)
-    (s0, v0, e0), (s1, v1, e1) = out
+    (s0, v0, e0, F0, E0, W0), (s1, v1, e1, F1, E1, W1) = out
     assert np.array_equal(s0, s1) and np.array_equal(v0, v1)
     assert e0 == e1
+    assert np.array_equal(F0, F1) and E0 == E1 and W0 == W1
