@@ -747,14 +747,14 @@ __device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
           }
           // Reaction on the visited cluster, reduce-scattered over the 8 lanes sharing h: of
           // the slots (fx, fy, fz of particle h, then of particle h + 4, then two zeros) lane
-          // a8 ends with the sum of slot a8 over the 8 lanes and adds it (slots 0-5). Round
-          // m = 1, 2, 4 pairs the slots that differ in bit m: a lane keeps the one whose bit
-          // matches its own and adds its partner's copy of it, so each sum is formed as the
-          // tree ((v_a + v_a^1) + (v_a^2 + v_a^3)) + (...) of a full butterfly, with a third
-          // of its shuffles.
+          // a8 ends with the sum of slot a8 over the 8 lanes and adds it (slots 0-5). The
+          // exchange with lane a8 xor m (m = 1, 2, 4) pairs the slots that differ in bit m: a
+          // lane keeps the one whose bit matches its own and adds its partner's copy of it,
+          // so each sum is formed as the tree ((v_a + v_a^1) + (v_a^2 + v_a^3)) + (...) of a
+          // full butterfly, with a third of its shuffles.
           {
             const bool b0 = a8 & 1, b1 = a8 & 2, b2 = a8 & 4;
-            // round 1: slot pairs (0, 1), (2, 3), (4, 5); w[p] holds slot 2p + b0 ((6, 7): zero)
+            // xor 1: slot pairs (0, 1), (2, 3), (4, 5); w[p] holds slot 2p + b0 ((6, 7): zero)
             real w[3];
             {
               const real s0[3] = {fxj[0], fzj[0], fyj[1]}, s1[3] = {fyj[0], fxj[1], fzj[1]};
@@ -762,10 +762,10 @@ __device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
               for (int p = 0; p < 3; ++p)
                 w[p] = (b0 ? s1[p] : s0[p]) + __shfl_xor_sync(FULL, b0 ? s0[p] : s1[p], 1);
             }
-            // round 2: (w0, w1) and (w2, 0); u[q] holds slot 4q + 2 b1 + b0
+            // xor 2: (w0, w1) and (w2, 0); u[q] holds slot 4q + 2 b1 + b0
             const real u0 = (b1 ? w[1] : w[0]) + __shfl_xor_sync(FULL, b1 ? w[0] : w[1], 2);
             const real u1 = (b1 ? (real)0 : w[2]) + __shfl_xor_sync(FULL, b1 ? w[2] : (real)0, 2);
-            // round 3: slot a8
+            // xor 4: slot a8
             const real v = (b2 ? u1 : u0) + __shfl_xor_sync(FULL, b2 ? u0 : u1, 4);
             if (a8 < 6) {
               const int k = a8 / 3, d = a8 - 3 * k;
