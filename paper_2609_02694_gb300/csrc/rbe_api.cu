@@ -913,11 +913,7 @@ int rbe_set_profiling(rbe_handle h, int enable) {
   const bool on = enable != 0;
   if (on == c.timing) return RBE_OK;
   RBE_CUDA_TRY(cudaStreamSynchronize(c.stream));
-  for (int b = 0; b < 2; ++b)
-    if (c.graph[b]) {
-      cudaGraphExecDestroy(c.graph[b]);
-      c.graph[b] = nullptr;
-    }
+  drop_graphs(c);  // (steps and force evaluations are captured again, with or without events)
   if (on)
     for (int k = 0; k <= RBE_N_PHASE; ++k)
       if (!c.ev[k]) RBE_CUDA_TRY(cudaEventCreate(&c.ev[k]));
