@@ -214,3 +214,32 @@ def test_two_branch_step_graph_equals_sequential(precision, frac):
     assert np.array_equal(s0, s1) and np.array_equal(v0, v1)
     assert e0 == e1
     assert np.array_equal(F0, F1) and E0 == E1 and W0 == W1
+
+
+def test_replayed_force_evaluations_follow_new_positions():
+    """rbe_forces replays a captured evaluation (one graph per buffer parity). Fed a sequence
+    of new positions through rbe_set_positions, it gives the same forces and energies bit for
+    bit as the uncaptured evaluation (profiling on) on a second handle, at both parities."""
+    sy = synth.make_system(15000, density=0.1, frac_charged=0.1, seed=47)
+    rng = np.random.default_rng(5)
+    x0 = sy.positions()
+    moves = [x0 + rng.normal(scale=s, size=x0.shape) for s in (0.0, 0.02, 0.1, 0.05, 0.15)]
+    res = []
+    for prof in (False, True):
+        with binding.from_system(sy, P=64, alpha=ALPHA, r_c=RC, coulomb_C=C, seed=3) as h:
+            h.set_tuning("pair_cluster", 1)
+            h.set_profiling(prof)
+            out = []
+            for k, x in enumerate(moves):
+                h.set_positions(x)
+                out.append(h.forces(10 + k))
+            res.append(out)
+    for (F0, E0, W0), (F1, E1, W1) in zip(*res):
+        assert np.array_equal(F0, F1) and E0 == E1 and W0 == W1
+    # and they are forces of those positions: the last evaluation against a fresh handle
+    sy2 = synth.make_system(15000, density=0.1, frac_charged=0.1, seed=47)
+    with binding.from_system(sy2, P=64, alpha=ALPHA, r_c=RC, coulomb_C=C, seed=3) as h:
+        h.set_tuning("pair_cluster", 1)
+        h.set_positions(moves[-1])
+        F2, E2, _ = h.forces(10 + len(moves) - 1)
+    assert np.array_equal(F2, res[0][-1][0]) and E2 == res[0][-1][1]
