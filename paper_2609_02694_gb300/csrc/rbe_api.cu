@@ -264,10 +264,11 @@ int copy_scalars(Ctx &c, double *energies, double *virial) {
   return RBE_OK;
 }
 
-// Capture one Verlet step into a graph. Capture runs on an internal non-blocking stream
-// (the legacy default stream cannot be captured); the graph is replayed on c.stream.
-// One Verlet step (or, forces_only, one force evaluation with the kinetic energy and the
-// totals, as rbe_forces runs it) captured from buffer parity `parity`.
+// Capture one Verlet step from buffer parity `parity` into a graph (or, forces_only, one
+// force evaluation with the kinetic energy and the totals, as rbe_forces runs it). Capture
+// runs on an internal non-blocking stream (the legacy default stream cannot be captured),
+// with a second one for the cluster pipeline's other branch; the graph is replayed on
+// c.stream.
 int capture_step_graph(Ctx &c, int parity, cudaGraphExec_t *out, bool forces_only = false) {
   if (!c.cap_stream) RBE_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
   if (!c.aux_stream) RBE_CUDA_TRY(cudaStreamCreateWithFlags(&c.aux_stream, cudaStreamNonBlocking));
