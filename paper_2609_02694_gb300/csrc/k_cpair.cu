@@ -72,6 +72,7 @@ struct ClusterArgs {
   float bb2;                   // bounding-box test: squared gap <= bb2 (r_c^2, widened)
   float rc2_mid, rc2_half;     // band test: |r^2 - rc2_mid| <= rc2_half covers [rc2_lo, rc2_hi]
   int *err;
+  int64_t nslots;              // the pass's energy partial slots (at least the grid)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -342,7 +343,7 @@ __device__ __forceinline__ real cp_terms(const ClusterArgs &a, bool in, real r2,
 // The kernel: one warp per super-cluster.
 
 template <typename real, bool COUL, bool MULTI, bool COUNT>
-__device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
+__device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int nbx) {
   constexpr bool F64 = sizeof(real) == 8;
   constexpr int NC = F64 ? 4 : 8;          // clusters per super-cluster
   constexpr int NP = NC * kClSize;         // particles per super-cluster
@@ -838,6 +839,10 @@ __device__ __forceinline__ void cpair_body(const ClusterArgs &a, int bx, int) {
     const double s = warp_sum(v[k]);
     if (lane == 0) a.epart[(int64_t)bx * NQ_PAIR + k] = s;
   }
+  // the pass's partial slots past the grid (the range is sized for the per-particle kernel,
+  // the grid for the super-clusters) hold zeros
+  for (int64_t z = (int64_t)bx + nbx; z < a.nslots; z += nbx)
+    if (lane < NQ_PAIR) a.epart[z * NQ_PAIR + lane] = 0.0;
 }
 
 // (occupancy: 24 warps per SM for the FP32 LJ pass, fewer for the register-heavy Coulomb and
@@ -953,8 +958,10 @@ cudaError_t launch_cluster_pair(Ctx &c, bool coul, bool multi, bool want_counts)
     const cudaError_t e = fill_zero(c, c.nbr, c.N);
     if (e != cudaSuccess) return e;
   }
-  // every slot of the pass's partial range (blocks past the last super-cluster write zeros)
-  const dim3 g((unsigned)c.n_pair_blk), bl(32);
+  // a block per possible super-cluster (blocks past the last one, and each block for the
+  // slots past the grid, write zeros to the pass's partial range)
+  a.nslots = c.n_pair_blk;
+  const dim3 g((unsigned)std::min<int64_t>(c.n_pair_blk, cpair_blocks_bound(c))), bl(32);
   const bool fp64 = c.precision == RBE_FP64;
   cudaError_t e;
   // (per replica in a batch)
