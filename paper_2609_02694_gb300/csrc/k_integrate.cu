@@ -168,6 +168,54 @@ __device__ __forceinline__ void kick_body(const KickArgs<V, FT> &a, int bx, int)
 }
 RBE_VF_KERNELS(__launch_bounds__(256), kick_kernel, KickArgs, kick_body)
 
+// The FP32 forms with N a multiple of 4: blocks of 64 threads over the same 256 particles as
+// kick_body's blocks, four consecutive particles a thread in 16-byte accesses. Each particle's
+// arithmetic, its term's shared-memory slot and the reduction tree are kick_body's, so the
+// kinetic energy partials are the same bit for bit.
+__device__ __forceinline__ void kick4_body(const KickArgs<float, float> &a, int bx, int) {
+  __shared__ double sh[256];
+  const int64_t N = a.N;
+  const int t = threadIdx.x;
+  const int64_t i = (int64_t)bx * 256 + 4 * t;
+  const float hdk = (float)a.hdk, ik = (float)a.inv_kappa;
+  double ke[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < N) {  // (all four, N being a multiple of 4)
+    const float4 im = *reinterpret_cast<const float4 *>(a.invm + i);
+    float v2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float4 *vp = reinterpret_cast<float4 *>(a.v + d * N + i);
+      float4 vv = *vp;
+      if (a.do_kick) {
+        const float4 f = *reinterpret_cast<const float4 *>(a.F + d * N + i);
+        vv.x += f.x * im.x * hdk;
+        vv.y += f.y * im.y * hdk;
+        vv.z += f.z * im.z * hdk;
+        vv.w += f.w * im.w * hdk;
+        *vp = vv;
+      }
+      v2[0] += vv.x * vv.x;
+      v2[1] += vv.y * vv.y;
+      v2[2] += vv.z * vv.z;
+      v2[3] += vv.w * vv.w;
+    }
+    ke[0] = (double)(0.5f * v2[0] * __frcp_rn(im.x) * ik);
+    ke[1] = (double)(0.5f * v2[1] * __frcp_rn(im.y) * ik);
+    ke[2] = (double)(0.5f * v2[2] * __frcp_rn(im.z) * ik);
+    ke[3] = (double)(0.5f * v2[3] * __frcp_rn(im.w) * ik);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sh[4 * t + j] = ke[j];
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    for (int k = t; k < st; k += 64) sh[k] += sh[k + st];
+    __syncthreads();
+  }
+  if (t == 0) a.ke_part[bx] = sh[0];
+}
+using KickArgsF = KickArgs<float, float>;
+RBE_BATCHED_KERNEL(__launch_bounds__(64), kick4_kernel, KickArgsF, kick4_body)
+
 // Nose-Hoover half steps (chain of one): from 2K = 2 sum(kinetic partials) the end-of-step
 // half (mode 0) gives the velocity scale s_end and the start-of-next-step half gives
 // s_start, applied by the next kick-drift; mode 1 only does the start half (first step).
@@ -436,6 +484,9 @@ static cudaError_t kick_impl(Ctx &c, int do_kick) {
   }
   const KickArgs<float, float> a{c.vf[b], c.F, c.invm[b], c.N, hdk, 1.0 / c.kappa, do_kick,
                                  c.epart + c.off_ke};
+  // (a batch keeps the one-particle kernel: the same results, and replicas of any N share a
+  //  class)
+  if (c.N % 4 == 0 && !c.rec) return dispatch(c, kick4_kernel, kick4_kernel_b, g, dim3(64), 0, a);
   return dispatch(c, kick_kernel<float, float>, kick_kernel_b<float, float>, g, t, 0, a);
 }
 
