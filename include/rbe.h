@@ -123,13 +123,18 @@ int rbe_set_positions(rbe_handle h, const double *pos, int on_device);
  *            device memory
  *  energies  RBE_N_ENERGY doubles (nullable, host)
  *  virial    RBE_N_VIRIAL doubles (nullable, host)
- * The call synchronises when any host output is requested. */
+ * The call synchronises when any host output is requested. With profiling off, the stages
+ * run as a CUDA graph captured at the first call on each of the two buffer parities (an
+ * internal stream is captured; make those first calls outside any stream capture of the
+ * caller's own) and replayed afterwards; the step number is written to the device before
+ * each replay. The graphs are captured again after a change of tuning, profiling, neighbour
+ * list or thermostat, or a checkpoint load. */
 int rbe_forces(rbe_handle h, uint64_t step, float *F_out, int F_on_device, double *energies,
                double *virial);
 
 /* Same as rbe_forces, with FP64 forces written to host memory (for parity checks); it also
  * records the neighbour counts and RBL draws that rbe_get_neighbor_counts and
- * rbe_get_rbl_partners return. */
+ * rbe_get_rbl_partners return. It always launches its stages one by one (no graph). */
 int rbe_forces_f64(rbe_handle h, uint64_t step, double *F_out, double *energies,
                    double *virial);
 
